@@ -1,0 +1,233 @@
+"""FP64 CPU oracle for synchronous parallel simulated annealing -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It shares no code with the CUDA library: the C source
+``sa_oracle.c`` is compiled on its own with gcc (``-ffp-contract=off``) and loaded
+through ctypes.  Every function follows the paper's algorithm step by step
+(Sec. 2.1 Steps 1-5, Sec. 3.2.2, Listings 3-4); see the header of ``sa_oracle.c``
+for the readings taken where the paper is silent.
+
+Pins: the tests under ``tests/test_oracle_*.py`` check this oracle against
+published Philox4x32-10 known-answer vectors, the closed-form normalised
+Schwefel minimum, brute-force grids, schedule/evaluation-count identities
+printed with Table 1, and Metropolis invariants (acceptance 1 on a constant
+cost, zero uphill moves as T -> 0, Boltzmann histogram at fixed T).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sa_oracle.c")
+_LIB = os.path.join(_HERE, "libsaoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3,
+         "rot_rastrigin": 4, "rot_schwefel": 5}
+TAG_SWEEP, TAG_INIT, TAG_DA = 0, 1, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's shared library with gcc (OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_int32), ("n", ctypes.c_int32), ("chains", ctypes.c_int64),
+                ("L", ctypes.c_int32), ("K", ctypes.c_int32), ("level0", ctypes.c_int32),
+                ("boundary", ctypes.c_int32), ("mode", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("problem", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("T0", ctypes.c_double),
+                ("rho", ctypes.c_double), ("sigma_frac", ctypes.c_double),
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p)]
+
+
+class Out(ctypes.Structure):
+    _fields_ = [("x_best", ctypes.c_void_p), ("f_best", ctypes.c_void_p), ("x_inc", ctypes.c_void_p),
+                ("f_inc", ctypes.c_void_p), ("argmin", ctypes.c_void_p), ("f_level", ctypes.c_void_p),
+                ("accepts", ctypes.c_void_p), ("bits", ctypes.c_void_p), ("trace_levels", ctypes.c_int32),
+                ("F_final", ctypes.c_void_p), ("X_final", ctypes.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            vp, i32, i64, u32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+            L.sao_philox4x32_10.argtypes = [vp, vp, vp]
+            L.sao_uniform.argtypes = [u32]
+            L.sao_uniform.restype = f64
+            L.sao_coord.argtypes = [u32, i32]
+            L.sao_coord.restype = u32
+            L.sao_cost.argtypes = [i32, i32, vp, vp]
+            L.sao_cost.restype = f64
+            L.sao_grad.argtypes = [i32, i32, vp, vp, vp]
+            L.sao_temperature.argtypes = [f64, f64, i32]
+            L.sao_temperature.restype = f64
+            L.sao_levels_for.argtypes = [f64, f64, f64]
+            L.sao_levels_for.restype = i32
+            L.sao_init_point.argtypes = [ctypes.POINTER(Cfg), i64, vp]
+            L.sao_chain_level.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, vp, vp]
+            L.sao_chain_level.restype = f64
+            L.sao_run.argtypes = [ctypes.POINTER(Cfg), ctypes.POINTER(Out)]
+            L.sao_run.restype = ctypes.c_int
+            L.sao_level_chains.argtypes = [ctypes.POINTER(Cfg), i32, vp, i64, i64, vp, vp, vp, vp]
+            L.sao_level_chains.restype = ctypes.c_int
+            L.sao_pgd.argtypes = [i32, i32, vp, vp, vp, vp, i32, f64, f64, i32, vp, vp]
+            L.sao_pgd.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for a 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().sao_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def stream_key(seed: int, tag: int):
+    return [seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ tag]
+
+
+def uniform(w: int) -> float:
+    return lib().sao_uniform(int(w))
+
+
+def coord(w: int, n: int) -> int:
+    return lib().sao_coord(int(w), int(n))
+
+
+def cost(name_or_id, x, Q=None) -> float:
+    cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    return lib().sao_cost(cid, x.size, _p(x), _p(Qa))
+
+
+def grad(name_or_id, x, Q=None) -> np.ndarray:
+    cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    g = np.zeros_like(x)
+    lib().sao_grad(cid, x.size, _p(x), _p(Qa), _p(g))
+    return g
+
+
+def temperature(T0: float, rho: float, level: int) -> float:
+    return lib().sao_temperature(T0, rho, level)
+
+
+def levels_for(T0: float, rho: float, T_min: float) -> int:
+    return lib().sao_levels_for(T0, rho, T_min)
+
+
+class Problem:
+    """A box-constrained problem plus the schedule of one synchronous SA run."""
+
+    def __init__(self, cost, n, lo, hi, chains, L, T0=100.0, rho=0.9, sigma_frac=0.1,
+                 boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0):
+        self.cost = COSTS[cost] if isinstance(cost, str) else int(cost)
+        self.n = int(n)
+        self.lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.n,)))
+        self.hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (self.n,)))
+        self.Q = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+        self.chains, self.L = int(chains), int(L)
+        self.T0, self.rho, self.sigma_frac = float(T0), float(rho), float(sigma_frac)
+        self.boundary = {"reflect": 0, "clip": 1}[boundary] if isinstance(boundary, str) else int(boundary)
+        self.seed, self.problem, self.mode, self.threads = int(seed), int(problem), int(mode), int(threads)
+
+    def cfg(self, K=0, level0=0) -> Cfg:
+        return Cfg(self.cost, self.n, self.chains, self.L, K, level0, self.boundary, self.mode,
+                   self.threads, self.problem, self.seed, self.T0, self.rho, self.sigma_frac,
+                   _p(self.lo), _p(self.hi), _p(self.Q))
+
+    def init_point(self, c: int) -> np.ndarray:
+        x = np.zeros(self.n)
+        cfg = self.cfg()
+        lib().sao_init_point(ctypes.byref(cfg), c, _p(x))
+        return x
+
+    def chain_level(self, level, c, x_start=None, trace=False):
+        """One chain for one level; returns (F_end, x_end, accepts, bits)."""
+        cfg = self.cfg()
+        x = self.init_point(c) if x_start is None else np.array(x_start, np.float64)
+        words = (self.L + 31) // 32
+        bits = np.zeros(words, np.uint32) if trace else None
+        acc = np.zeros(1, np.int64)
+        F = lib().sao_chain_level(ctypes.byref(cfg), level, c, _p(x), _p(bits), _p(acc))
+        return F, x, int(acc[0]), bits
+
+    def level_chains(self, level, c0, c1, x_start=None, want_x=False, trace=False):
+        """One level for chains [c0, c1); returns dict of per-chain results."""
+        cfg = self.cfg()
+        m = c1 - c0
+        F = np.zeros(m)
+        X = np.zeros((m, self.n)) if want_x else None
+        words = (self.L + 31) // 32
+        bits = np.zeros((m, words), np.uint32) if trace else None
+        acc = np.zeros(m, np.int64)
+        xs = None if x_start is None else np.ascontiguousarray(x_start, np.float64)
+        rc = lib().sao_level_chains(ctypes.byref(cfg), level, _p(xs), c0, c1, _p(F), _p(X), _p(bits), _p(acc))
+        if rc != 0:
+            raise ValueError("sao_level_chains failed")
+        return {"F": F, "X": X, "bits": bits, "accepts": acc}
+
+    def run(self, K, level0=0, x_best=None, f_best=None, x_inc=None, f_inc=None,
+            trace_levels=0, want_final=False):
+        """Run K levels; returns a dict with the incumbent, per-level argmins and optional traces."""
+        n, C = self.n, self.chains
+        xb = np.zeros(n) if x_best is None else np.array(x_best, np.float64)
+        fb = np.array([np.inf if f_best is None else f_best], np.float64)
+        xi = np.zeros(n) if x_inc is None else np.array(x_inc, np.float64)
+        fi = np.array([np.inf if f_inc is None else f_inc], np.float64)
+        am = np.zeros(max(K, 1), np.int64)
+        fl = np.zeros(max(K, 1))
+        ac = np.zeros(max(K, 1), np.int64)
+        words = (self.L + 31) // 32
+        tl = min(trace_levels, K)
+        bits = np.zeros((max(tl, 1), C, words), np.uint32) if tl > 0 else None
+        Ff = np.zeros(C) if want_final else None
+        Xf = np.zeros((C, n)) if want_final else None
+        out = Out(_p(xb), _p(fb), _p(xi), _p(fi), _p(am), _p(fl), _p(ac), _p(bits), tl, _p(Ff), _p(Xf))
+        cfg = self.cfg(K, level0)
+        rc = lib().sao_run(ctypes.byref(cfg), ctypes.byref(out))
+        if rc != 0:
+            raise ValueError(f"sao_run failed ({rc})")
+        return {"x_best": xb, "f_best": float(fb[0]), "x_inc": xi, "f_inc": float(fi[0]),
+                "argmin": am[:K], "f_level": fl[:K], "accepts": ac[:K], "bits": bits,
+                "F_final": Ff, "X_final": Xf}
+
+
+def pgd(name_or_id, x0, lo, hi, Q=None, max_iter=1000, tol=1e-10, armijo_c=1e-4, max_halvings=30):
+    """Box-projected gradient descent with Armijo backtracking from x0."""
+    cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
+    x = np.array(x0, np.float64)
+    n = x.size
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (n,)))
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    f = np.zeros(1)
+    it = np.zeros(1, np.int32)
+    rc = lib().sao_pgd(cid, n, _p(lo), _p(hi), _p(Qa), _p(x), max_iter, tol, armijo_c, max_halvings, _p(f), _p(it))
+    if rc != 0:
+        raise ValueError("sao_pgd failed")
+    return x, float(f[0]), int(it[0])

@@ -1,0 +1,494 @@
+/*
+ * sa_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, FP64 CPU reference of synchronous parallel simulated annealing
+ * (Ferreiro, Garcia, Lopez-Salas, Vazquez: "An efficient implementation of
+ * parallel simulated annealing algorithm in GPUs").  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load this file's
+ * library.  It shares no code, header or constant table with the CUDA path.
+ *
+ * What it computes, in the paper's order:
+ *   - the box-constrained problem  min_{x in I} f(x),  I = prod [l_k, u_k]   (Eq. 1)
+ *   - per chain and per temperature level, N (here: L) Metropolis steps:
+ *     pick a coordinate, perturb it, evaluate f, accept by the Boltzmann rule
+ *     (Sec. 2.1 Steps 2-3, Eq. "proba", k_b = 1)
+ *   - at the end of every level a reduction picks the chain with the lowest
+ *     final f; all chains restart from it and T is cooled geometrically
+ *     T <- rho T  (Sec. 3.2.2 synchronous approach; Listings 3-4; Sec. 2.1 Step 5)
+ *
+ * Readings where the paper is silent (each one is also a pinned test):
+ *   - randomness: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), one
+ *     128-bit block per (step, level, chain, problem); key = (seed_lo,
+ *     seed_hi ^ tag).  Uniforms u(w) = ((w >> 9) + 0.5) * 2^-23, in (0,1).
+ *   - neighbour: coordinate d = (w0 * n) >> 32, Gaussian step via the cosine
+ *     branch of Box-Muller, sigma = sigma_frac * (u_d - l_d) * sqrt(T / T0).
+ *   - box: reflect once then clip (or clip only).
+ *   - acceptance: dF <= 0 or u3 < exp(-dF / T).
+ *   - tie-break of the reduction: lowest chain index.
+ *   - the answer returned is the incumbent: the best level minimum seen.
+ *
+ * Compiled with -ffp-contract=off so that every product and sum is rounded
+ * exactly as written, on every host architecture.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define SAO_TAG_SWEEP 0u
+#define SAO_TAG_INIT 1u
+#define SAO_TAG_DA 3u
+
+enum { SAO_SCHWEFEL = 0, SAO_RASTRIGIN = 1, SAO_ACKLEY = 2, SAO_ROSENBROCK = 3,
+       SAO_ROT_RASTRIGIN = 4, SAO_ROT_SCHWEFEL = 5 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, written from its definition (Salmon et al. 2011, Sec. 4):   */
+/* each round multiplies counter words 0 and 2 by two fixed odd constants,     */
+/* swaps the halves and xors in the key; the key is bumped by two Weyl        */
+/* constants between rounds.                                                   */
+/* ------------------------------------------------------------------------ */
+void sao_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static inline void sao_block(uint64_t seed, uint32_t tag, uint32_t c0, uint32_t c1,
+                             uint32_t c2, uint32_t c3, uint32_t w[4]) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ tag};
+    sao_philox4x32_10(ctr, key, w);
+}
+
+/* Uniform in (0,1) from the top 23 bits of a word: exact in FP32 and FP64. */
+double sao_uniform(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+uint32_t sao_coord(uint32_t w, int32_t n) { return (uint32_t)(((uint64_t)w * (uint64_t)n) >> 32); }
+
+/* ------------------------------------------------------------------------ */
+/* Cost functions, each written as the formula the paper prints (Appendix    */
+/* and Sec. 4.1), summed in index order.                                      */
+/* ------------------------------------------------------------------------ */
+static double h_schwefel(double t) { return t * sin(sqrt(fabs(t))); }
+static double g_rastrigin(double t) { return t * t - 10.0 * cos(2.0 * M_PI * t); }
+
+/* Normalised Schwefel (Sec. 4.1): f = -(1/n) sum x_i sin(sqrt|x_i|). */
+static double f_schwefel(int n, const double* x) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += h_schwefel(x[i]);
+    return -(s / (double)n);
+}
+/* Rastrigin (Appendix, Test 13): 10 n + sum (x_i^2 - 10 cos 2 pi x_i). */
+static double f_rastrigin(int n, const double* x) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += g_rastrigin(x[i]);
+    return 10.0 * (double)n + s;
+}
+static double ackley_from_sums(int n, double s1, double s2) {
+    return -20.0 * exp(-0.2 * sqrt(s1 / (double)n)) - exp(s2 / (double)n) + 20.0 + M_E;
+}
+/* Ackley (Appendix, Test 1). */
+static double f_ackley(int n, const double* x) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < n; ++i) { s1 += x[i] * x[i]; s2 += cos(2.0 * M_PI * x[i]); }
+    return ackley_from_sums(n, s1, s2);
+}
+/* Generalised Rosenbrock (Appendix, Test 14), standard form
+ * sum_{i<n-1} 100 (x_{i+1} - x_i^2)^2 + (1 - x_i)^2 (the printed x_i is read as x_i^2). */
+static double rosen_term(double a, double b) {
+    double t = b - a * a, u = 1.0 - a;
+    return 100.0 * t * t + u * u;
+}
+static double f_rosenbrock(int n, const double* x) {
+    double s = 0.0;
+    for (int i = 0; i + 1 < n; ++i) s += rosen_term(x[i], x[i + 1]);
+    return s;
+}
+/* y = Q x for a row-major n x n Q, each row summed in index order. */
+static void rotate(int n, const double* Q, const double* x, double* y) {
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        const double* q = Q + (size_t)i * n;
+        for (int j = 0; j < n; ++j) s += q[j] * x[j];
+        y[i] = s;
+    }
+}
+
+/* Full definition of f at x (ywork: n doubles of scratch for rotated costs). */
+double sao_cost_ws(int32_t cost, int32_t n, const double* x, const double* Q, double* ywork) {
+    switch (cost) {
+    case SAO_SCHWEFEL: return f_schwefel(n, x);
+    case SAO_RASTRIGIN: return f_rastrigin(n, x);
+    case SAO_ACKLEY: return f_ackley(n, x);
+    case SAO_ROSENBROCK: return f_rosenbrock(n, x);
+    case SAO_ROT_RASTRIGIN: rotate(n, Q, x, ywork); return f_rastrigin(n, ywork);
+    case SAO_ROT_SCHWEFEL: rotate(n, Q, x, ywork); return f_schwefel(n, ywork);
+    default: return NAN;
+    }
+}
+double sao_cost(int32_t cost, int32_t n, const double* x, const double* Q) {
+    double* y = (cost >= SAO_ROT_RASTRIGIN) ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+    double f = sao_cost_ws(cost, n, x, Q, y);
+    free(y);
+    return f;
+}
+
+/* Gradient of f (used by the box-projected local minimiser). */
+static double dh_schwefel(double t) {
+    double r = sqrt(fabs(t));
+    return sin(r) + 0.5 * r * cos(r);
+}
+static double dg_rastrigin(double t) { return 2.0 * t + 20.0 * M_PI * sin(2.0 * M_PI * t); }
+void sao_grad(int32_t cost, int32_t n, const double* x, const double* Q, double* g) {
+    if (cost == SAO_SCHWEFEL) {
+        for (int i = 0; i < n; ++i) g[i] = -dh_schwefel(x[i]) / (double)n;
+    } else if (cost == SAO_RASTRIGIN) {
+        for (int i = 0; i < n; ++i) g[i] = dg_rastrigin(x[i]);
+    } else if (cost == SAO_ACKLEY) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = 0; i < n; ++i) { s1 += x[i] * x[i]; s2 += cos(2.0 * M_PI * x[i]); }
+        double r = sqrt(s1 / (double)n);
+        double e1 = exp(-0.2 * r), e2 = exp(s2 / (double)n);
+        for (int i = 0; i < n; ++i) {
+            double a = (r > 0.0) ? 4.0 * e1 * x[i] / ((double)n * r) : 0.0;
+            g[i] = a + 2.0 * M_PI * sin(2.0 * M_PI * x[i]) * e2 / (double)n;
+        }
+    } else if (cost == SAO_ROSENBROCK) {
+        for (int i = 0; i < n; ++i) {
+            double gi = 0.0;
+            if (i + 1 < n) gi += -400.0 * x[i] * (x[i + 1] - x[i] * x[i]) - 2.0 * (1.0 - x[i]);
+            if (i > 0) gi += 200.0 * (x[i] - x[i - 1] * x[i - 1]);
+            g[i] = gi;
+        }
+    } else { /* rotated: grad_x = Q^T g'(y) */
+        double* y = (double*)malloc(sizeof(double) * (size_t)n);
+        double* gy = (double*)malloc(sizeof(double) * (size_t)n);
+        rotate(n, Q, x, y);
+        for (int i = 0; i < n; ++i)
+            gy[i] = (cost == SAO_ROT_RASTRIGIN) ? dg_rastrigin(y[i]) : -dh_schwefel(y[i]) / (double)n;
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += Q[(size_t)i * n + j] * gy[i];
+            g[j] = s;
+        }
+        free(y);
+        free(gy);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Synchronous parallel SA                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t cost;
+    int32_t n;
+    int64_t chains;
+    int32_t L;        /* Metropolis steps per chain and level (the paper's N) */
+    int32_t K;        /* levels to run in this call */
+    int32_t level0;   /* absolute index of the first level (resume) */
+    int32_t boundary; /* 0: reflect once then clip; 1: clip */
+    int32_t mode;     /* 0: full recompute of f(x'); 1: local difference */
+    int32_t threads;  /* OpenMP threads, 0 = runtime default */
+    uint32_t problem; /* counter word 3 (problem index in a batch) */
+    uint64_t seed;
+    double T0, rho, sigma_frac;
+    const double* lo;
+    const double* hi;
+    const double* Q; /* row-major n x n, rotated costs only */
+} sao_cfg;
+
+typedef struct {
+    double* x_best;      /* [n] in: restart point when level0 > 0; out: restart point after the last level */
+    double* f_best;      /* [1] F(x_best), in/out */
+    double* x_inc;       /* [n] incumbent, in/out */
+    double* f_inc;       /* [1] incumbent value, in/out (+inf before the first level) */
+    int64_t* argmin;     /* [K] p* per level, or NULL */
+    double* f_level;     /* [K] F_{p*} per level, or NULL */
+    int64_t* accepts;    /* [K] accepted moves per level, or NULL */
+    uint32_t* bits;      /* [trace_levels][chains][ceil(L/32)] accept bits, or NULL */
+    int32_t trace_levels;
+    double* F_final;     /* [chains] F at the end of the last level, or NULL */
+    double* X_final;     /* [chains * n] states at the end of the last level, or NULL */
+} sao_out;
+
+/* T_l = T0 rho^l by repeated multiplication (the host loop of Listing 3). */
+double sao_temperature(double T0, double rho, int32_t level) {
+    double T = T0;
+    for (int l = 0; l < level; ++l) T = T * rho;
+    return T;
+}
+
+/* Number of levels of the do-while of Listing 3: run, cool, stop once T <= T_min. */
+int32_t sao_levels_for(double T0, double rho, double T_min) {
+    double T = T0;
+    int32_t k = 0;
+    do { ++k; T = T * rho; } while (T > T_min && k < 100000000);
+    return k;
+}
+
+static double apply_box(double xp, double l, double u, int32_t boundary) {
+    if (boundary == 0) {
+        if (xp < l) xp = 2.0 * l - xp;
+        else if (xp > u) xp = 2.0 * u - xp;
+    }
+    if (xp < l) xp = l;
+    if (xp > u) xp = u;
+    return xp;
+}
+
+/* Initial point of a chain at level 0: x_k = l_k + u (u_k - l_k), coordinate
+ * k taking word k mod 4 of Philox block (k/4, 0, chain, problem), tag INIT. */
+void sao_init_point(const sao_cfg* cfg, int64_t c, double* x) {
+    for (int k = 0; k < cfg->n; k += 4) {
+        uint32_t w[4];
+        sao_block(cfg->seed, SAO_TAG_INIT, (uint32_t)(k / 4), 0u, (uint32_t)c, cfg->problem, w);
+        for (int j = 0; j < 4 && k + j < cfg->n; ++j)
+            x[k + j] = cfg->lo[k + j] + sao_uniform(w[j]) * (cfg->hi[k + j] - cfg->lo[k + j]);
+    }
+}
+
+/* Sum of g over the rotated coordinates y (rotated costs, mode 1). */
+static double gsum(int32_t cost, int n, const double* y) {
+    double s = 0.0;
+    if (cost == SAO_ROT_RASTRIGIN) for (int i = 0; i < n; ++i) s += g_rastrigin(y[i]);
+    else for (int i = 0; i < n; ++i) s += h_schwefel(y[i]);
+    return s;
+}
+static double f_from_gsum(int32_t cost, int n, double s) {
+    return (cost == SAO_ROT_RASTRIGIN) ? 10.0 * (double)n + s : -(s / (double)n);
+}
+
+/*
+ * One chain for one level: L Metropolis steps at temperature T starting from
+ * x (level 0: its own random point; later: the common restart point).
+ * On return x holds the final state and the function returns f(x) recomputed
+ * from the definition.  bits (may be NULL) receives the accept decisions.
+ */
+double sao_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
+                       uint32_t* bits, int64_t* n_accept) {
+    const int n = cfg->n;
+    const double T = sao_temperature(cfg->T0, cfg->rho, level);
+    const double s_l = sqrt(T / cfg->T0);
+    const int rot = cfg->cost >= SAO_ROT_RASTRIGIN;
+    double* y = rot ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+    double* yp = rot ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+    double F = sao_cost_ws(cfg->cost, n, x, cfg->Q, y);
+    double S1 = 0.0, S2 = 0.0, G = 0.0;
+    if (cfg->mode == 1 && cfg->cost == SAO_ACKLEY)
+        for (int i = 0; i < n; ++i) { S1 += x[i] * x[i]; S2 += cos(2.0 * M_PI * x[i]); }
+    if (cfg->mode == 1 && rot) G = gsum(cfg->cost, n, y); /* y = Q x from the call above */
+    int64_t acc = 0;
+    const int words = (cfg->L + 31) / 32;
+    if (bits) memset(bits, 0, sizeof(uint32_t) * (size_t)words);
+
+    for (int s = 0; s < cfg->L; ++s) {
+        uint32_t w[4];
+        sao_block(cfg->seed, SAO_TAG_SWEEP, (uint32_t)s, (uint32_t)level, (uint32_t)c, cfg->problem, w);
+        const int d = (int)sao_coord(w[0], n);
+        const double u1 = sao_uniform(w[1]), u2 = sao_uniform(w[2]), u3 = sao_uniform(w[3]);
+        /* Step 2: Gaussian move of coordinate d (Box-Muller, cosine branch). */
+        const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+        const double sigma = cfg->sigma_frac * (cfg->hi[d] - cfg->lo[d]) * s_l;
+        const double xd = x[d];
+        const double xp = apply_box(xd + sigma * z, cfg->lo[d], cfg->hi[d], cfg->boundary);
+
+        /* Step 3: energy difference. */
+        double dF, Fp = 0.0, S1p = 0.0, S2p = 0.0, Gp = 0.0;
+        if (cfg->mode == 0) {
+            x[d] = xp;
+            Fp = sao_cost_ws(cfg->cost, n, x, cfg->Q, y);
+            x[d] = xd;
+            dF = Fp - F;
+        } else if (cfg->cost == SAO_SCHWEFEL) {
+            dF = -((h_schwefel(xp) - h_schwefel(xd)) / (double)n);
+        } else if (cfg->cost == SAO_RASTRIGIN) {
+            dF = g_rastrigin(xp) - g_rastrigin(xd);
+        } else if (cfg->cost == SAO_ACKLEY) {
+            S1p = S1 - xd * xd + xp * xp;
+            S2p = S2 - cos(2.0 * M_PI * xd) + cos(2.0 * M_PI * xp);
+            dF = ackley_from_sums(n, S1p, S2p) - ackley_from_sums(n, S1, S2);
+        } else if (cfg->cost == SAO_ROSENBROCK) {
+            double before = 0.0, after = 0.0;
+            if (d > 0) { before += rosen_term(x[d - 1], xd); after += rosen_term(x[d - 1], xp); }
+            if (d + 1 < n) { before += rosen_term(xd, x[d + 1]); after += rosen_term(xp, x[d + 1]); }
+            dF = after - before;
+        } else { /* rotated: y' = y + (x'_d - x_d) Q[:, d] */
+            const double delta = xp - xd;
+            for (int i = 0; i < n; ++i) yp[i] = y[i] + delta * cfg->Q[(size_t)i * n + d];
+            Gp = gsum(cfg->cost, n, yp);
+            dF = f_from_gsum(cfg->cost, n, Gp) - f_from_gsum(cfg->cost, n, G);
+        }
+
+        /* Metropolis criterion, Eq. "proba" with k_b = 1. */
+        const int accept = (dF <= 0.0) || (u3 < exp(-dF / T));
+        if (accept) {
+            x[d] = xp;
+            ++acc;
+            if (bits) bits[s >> 5] |= 1u << (s & 31);
+            if (cfg->mode == 0) {
+                F = Fp;
+            } else {
+                F = F + dF;
+                if (cfg->cost == SAO_ACKLEY) { S1 = S1p; S2 = S2p; }
+                if (rot) { double* t = y; y = yp; yp = t; G = Gp; }
+            }
+        }
+    }
+    double Fend = sao_cost_ws(cfg->cost, n, x, cfg->Q, yp ? yp : y);
+    free(y);
+    free(yp);
+    if (n_accept) *n_accept = acc;
+    return Fend;
+}
+
+/*
+ * Run levels level0 .. level0+K-1 of synchronous parallel SA (Listings 3-4).
+ * Returns 0 on success, -1 on a bad argument, -2 on allocation failure.
+ */
+int sao_run(const sao_cfg* cfg, sao_out* out) {
+    if (!cfg || !out || cfg->n < 1 || cfg->chains < 1 || cfg->L < 0 || cfg->K < 0 ||
+        !cfg->lo || !cfg->hi || !out->x_best || !out->f_best || !out->x_inc || !out->f_inc)
+        return -1;
+    if (cfg->cost >= SAO_ROT_RASTRIGIN && !cfg->Q) return -1;
+    const int n = cfg->n;
+    const int64_t C = cfg->chains;
+    const int words = (cfg->L + 31) / 32;
+    double* X = (double*)malloc(sizeof(double) * (size_t)C * (size_t)n);
+    double* F = (double*)malloc(sizeof(double) * (size_t)C);
+    int64_t* A = (int64_t*)malloc(sizeof(int64_t) * (size_t)C);
+    if (!X || !F || !A) { free(X); free(F); free(A); return -2; }
+#ifdef _OPENMP
+    int nthreads = cfg->threads > 0 ? cfg->threads : omp_get_max_threads();
+#endif
+    for (int k = 0; k < cfg->K; ++k) {
+        const int32_t level = cfg->level0 + k;
+        uint32_t* bits = (out->bits && k < out->trace_levels)
+                             ? out->bits + (size_t)k * (size_t)C * (size_t)words : NULL;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+        for (int64_t c = 0; c < C; ++c) {
+            double* x = X + (size_t)c * n;
+            if (level == 0) sao_init_point(cfg, c, x);
+            else memcpy(x, out->x_best, sizeof(double) * (size_t)n);
+            F[c] = sao_chain_level(cfg, level, c, x, bits ? bits + (size_t)c * words : NULL, &A[c]);
+        }
+        /* Reduction over the chains' final values, lowest index on ties (Sec. 3.2.2). */
+        int64_t p = 0;
+        int64_t acc = 0;
+        for (int64_t c = 0; c < C; ++c) {
+            if (F[c] < F[p]) p = c;
+            acc += A[c];
+        }
+        memcpy(out->x_best, X + (size_t)p * n, sizeof(double) * (size_t)n);
+        out->f_best[0] = F[p];
+        if (F[p] < out->f_inc[0]) {
+            out->f_inc[0] = F[p];
+            memcpy(out->x_inc, X + (size_t)p * n, sizeof(double) * (size_t)n);
+        }
+        if (out->argmin) out->argmin[k] = p;
+        if (out->f_level) out->f_level[k] = F[p];
+        if (out->accepts) out->accepts[k] = acc;
+        if (k == cfg->K - 1) {
+            if (out->F_final) memcpy(out->F_final, F, sizeof(double) * (size_t)C);
+            if (out->X_final) memcpy(out->X_final, X, sizeof(double) * (size_t)C * (size_t)n);
+        }
+    }
+    free(X);
+    free(F);
+    free(A);
+    return 0;
+}
+
+/*
+ * One level for a subset of chains [c0, c1): used to check single chains of a
+ * large run one by one.  x_start = NULL means level 0 (own random start).
+ */
+int sao_level_chains(const sao_cfg* cfg, int32_t level, const double* x_start, int64_t c0,
+                     int64_t c1, double* F_out, double* X_out, uint32_t* bits_out,
+                     int64_t* acc_out) {
+    if (!cfg || c1 < c0 || (level > 0 && !x_start)) return -1;
+    const int n = cfg->n;
+    const int words = (cfg->L + 31) / 32;
+#ifdef _OPENMP
+    int nthreads = cfg->threads > 0 ? cfg->threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+#endif
+    for (int64_t c = c0; c < c1; ++c) {
+        double* x = (double*)malloc(sizeof(double) * (size_t)n);
+        if (x_start) memcpy(x, x_start, sizeof(double) * (size_t)n);
+        else sao_init_point(cfg, c, x);
+        int64_t a = 0;
+        double Fc = sao_chain_level(cfg, level, c, x, bits_out ? bits_out + (size_t)(c - c0) * words : NULL, &a);
+        if (F_out) F_out[c - c0] = Fc;
+        if (X_out) memcpy(X_out + (size_t)(c - c0) * n, x, sizeof(double) * (size_t)n);
+        if (acc_out) acc_out[c - c0] = a;
+        free(x);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Box-projected gradient descent with Armijo backtracking: the local       */
+/* minimiser of the hybrid SA (the paper hands the SA point to Nelder-Mead, */
+/* Sec. 4.2 / Table 10; here a projected gradient method takes that role).  */
+/* ------------------------------------------------------------------------ */
+int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
+            double* x, int32_t max_iter, double tol, double armijo_c, int32_t max_halvings,
+            double* f_out, int32_t* iters_out) {
+    double* g = (double*)malloc(sizeof(double) * (size_t)n);
+    double* xn = (double*)malloc(sizeof(double) * (size_t)n);
+    double* yw = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!g || !xn || !yw) { free(g); free(xn); free(yw); return -2; }
+    for (int i = 0; i < n; ++i) x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
+    double f = sao_cost_ws(cost, n, x, Q, yw);
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        sao_grad(cost, n, x, Q, g);
+        double pg = 0.0; /* infinity norm of the projected gradient P(x - g) - x */
+        for (int i = 0; i < n; ++i) {
+            double v = fmin(fmax(x[i] - g[i], lo[i]), hi[i]) - x[i];
+            if (fabs(v) > pg) pg = fabs(v);
+        }
+        if (pg < tol) break;
+        double alpha = 1.0;
+        int ok = 0;
+        double fn = f;
+        for (int h = 0; h < max_halvings; ++h) {
+            double slope = 0.0;
+            for (int i = 0; i < n; ++i) {
+                xn[i] = fmin(fmax(x[i] - alpha * g[i], lo[i]), hi[i]);
+                slope += g[i] * (xn[i] - x[i]);
+            }
+            fn = sao_cost_ws(cost, n, xn, Q, yw);
+            if (fn <= f + armijo_c * slope) { ok = 1; break; }
+            alpha = 0.5 * alpha;
+        }
+        if (!ok) break;
+        memcpy(x, xn, sizeof(double) * (size_t)n);
+        f = fn;
+    }
+    free(g);
+    free(xn);
+    free(yw);
+    if (f_out) *f_out = f;
+    if (iters_out) *iters_out = it;
+    return 0;
+}
