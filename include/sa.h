@@ -1,0 +1,223 @@
+/*
+ * sa.h -- C ABI of a GB300 (sm_103a) library for synchronous parallel
+ * simulated annealing (Ferreiro, Garcia, Lopez-Salas, Vazquez, "An efficient
+ * implementation of parallel simulated annealing algorithm in GPUs").
+ *
+ * The problem (Eq. 1):  minimise f(x) over the box I = prod_k [l_k, u_k].
+ * The method (Sec. 3.2.2, Listings 3-4): C Markov chains each run L
+ * Metropolis steps at the temperature of the current level; a reduction then
+ * finds the chain with the lowest f, every chain restarts from it, and the
+ * temperature is cooled geometrically, T <- rho T (Sec. 2.1, Step 5).
+ *
+ * Conventions for every entry point below
+ *   - Host pointers are plain host memory owned by the caller; the library
+ *     copies what it needs before returning (or, for outputs, writes into them
+ *     before returning).  Device pointers are named d_* and are caller-owned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a handle is enqueued on its stream.
+ *   - Every call returns sa_status.  After SA_ECUDA, SA_ETIMEOUT or
+ *     SA_ENUMERIC a handle only accepts sa_destroy (further calls give
+ *     SA_ESTATE).  Handles are not thread-safe.
+ *   - Layouts: vectors of length n are contiguous doubles; matrices are
+ *     row-major.
+ */
+#ifndef SA_GB300_H
+#define SA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SA_OK = 0,
+    SA_EINVAL = 1,   /* an argument is out of range (see each call) */
+    SA_ENOMEM = 2,   /* a device or host allocation failed */
+    SA_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    SA_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    SA_ENUMERIC = 5, /* the best state of a level is not finite */
+    SA_ESTATE = 6    /* the handle is in an error state or the call is out of order */
+} sa_status;
+
+/* Cost functions.  Schwefel is the paper's normalised form (Sec. 4.1,
+ * f = -(1/n) sum x_i sin sqrt|x_i|); Ackley, Rastrigin and Rosenbrock are the
+ * Appendix tests 1, 13 and 14 (Rosenbrock in its standard x_{i+1} - x_i^2
+ * form).  The rotated variants evaluate the same formula at y = Q x for an
+ * orthogonal Q (an extension: the paper has no rotated costs). */
+typedef enum {
+    SA_SCHWEFEL = 0,
+    SA_RASTRIGIN = 1,
+    SA_ACKLEY = 2,
+    SA_ROSENBROCK = 3,
+    SA_ROT_RASTRIGIN = 4,
+    SA_ROT_SCHWEFEL = 5
+} sa_cost;
+
+enum { SA_REFLECT = 0, SA_CLIP = 1 };                 /* box handling of a move */
+enum { SA_FP64 = 0, SA_FP32 = 1, SA_MIXED_BF16 = 2 }; /* arithmetic of the sweep */
+
+typedef struct {
+    int32_t cost;    /* sa_cost */
+    const double* Q; /* host, n x n row-major, orthogonal; NULL unless rotated */
+} sa_problem;
+
+typedef struct {
+    const double* lo; /* host, [n]: l_k */
+    const double* hi; /* host, [n]: u_k, hi[k] >= lo[k] */
+} sa_box;
+
+/* Annealing schedule (Sec. 2.1 Step 5; Listing 3 host loop). */
+typedef struct {
+    double T0;          /* initial temperature, > 0 */
+    double rho;         /* cooling factor, 0 < rho < 1 */
+    double T_min;       /* stop temperature (used when levels == 0), 0 < T_min < T0 */
+    int32_t levels;     /* > 0: run exactly this many levels; 0: the do-while of Listing 3 */
+    double sigma_frac;  /* Gaussian step sigma = sigma_frac (u_d - l_d) sqrt(T / T0), > 0 */
+    int32_t boundary;   /* SA_REFLECT (reflect once, then clip) or SA_CLIP */
+    int32_t precision;  /* SA_FP64 or SA_FP32 (state in FP32, argmin in FP64) */
+    int32_t surrogate;  /* reserved, must be 0 */
+    int32_t polish_k;   /* reserved, must be 0 */
+    int32_t trace_levels; /* record accept bits of the first trace_levels levels (0 = off) */
+} sa_schedule;
+
+typedef struct {
+    int64_t steps;        /* Metropolis steps run so far: chains * L * levels_done */
+    int64_t accepts;      /* accepted moves so far */
+    int32_t levels_done;  /* levels completed */
+    int32_t levels_total; /* levels of the schedule */
+    double f_level;       /* F of the restart point chosen by the last level */
+    int64_t argmin;       /* chain index p* chosen by the last level */
+    int64_t h2d_bytes;    /* bytes this handle copied host -> device so far */
+    int64_t d2h_bytes;    /* bytes this handle copied device -> host so far */
+    int64_t t_start_ns;   /* device clock (ns) when level 0 of the current run started */
+} sa_stats;
+
+typedef struct sa_handle sa_handle;
+
+/* Fill *s with the defaults: T0 = 100, rho = 0.9, T_min = 0, levels = 50,
+ * sigma_frac = 0.1, SA_REFLECT, SA_FP64, no tracing. */
+void sa_default_schedule(sa_schedule* s);
+
+/* Levels run by the do-while of Listing 3: the smallest K >= 1 with
+ * T0 rho^K <= T_min (temperatures by repeated multiplication).  Returns -1 on
+ * a bad argument.  T0 = 1000, rho = 0.99, T_min = 0.01 gives 1146 (Table 1). */
+int32_t sa_levels_for(double T0, double rho, double T_min);
+
+/*
+ * Create a solver for one problem (Eq. 1) with `chains` Markov chains of `L`
+ * steps per level.  Copies box, Q and the schedule to device memory that the
+ * handle owns (stream-ordered allocation on `stream`).  Launches nothing.
+ * Errors: SA_EINVAL if n < 1, chains < 1, L < 1, lo[k] > hi[k] or not finite,
+ * T0 <= 0, rho not in (0,1), levels < 0, levels == 0 and T_min not in
+ * (0, T0), sigma_frac <= 0, unknown cost/boundary/precision, a rotated cost
+ * without Q, surrogate or polish_k != 0, or chains > 2^31 - 1;
+ * SA_ENOMEM / SA_ECUDA on allocation or copy failure.  *out is NULL on error.
+ */
+sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains,
+                    int32_t L, const sa_schedule* schedule, uint64_t seed, void* stream,
+                    sa_handle** out);
+
+/*
+ * Run up to `levels` further temperature levels (-1 = all remaining).  Each
+ * level is: Metropolis sweep of every chain (Listing 4), reduction to the
+ * lowest-f chain with lowest-index tie-break, restart and cooling (Listing 3).
+ * Asynchronous: the work is enqueued on the handle's stream and the call
+ * returns; errors raised on the device surface at the next sa_best.
+ * Errors: SA_ESTATE on a failed handle or when no level remains,
+ * SA_EINVAL if levels == 0 or < -1, SA_ECUDA on a launch failure.
+ */
+sa_status sa_run(sa_handle* h, int32_t levels);
+
+/*
+ * Rewind the handle to level 0 (same problem, schedule and seed), so that the
+ * next sa_run repeats the run from its random initial points.  Asynchronous
+ * (stream-ordered device writes only).  Errors: SA_ESTATE on a failed handle.
+ */
+sa_status sa_reset(sa_handle* h);
+
+/*
+ * Run up to `levels` further levels like sa_run, but launch the kernels one
+ * by one (no graph) with CUDA events around them on the handle's stream, and
+ * return per level the sweep kernel's time (sweep_ms[l]) and the whole level's
+ * time (level_ms[l]) in milliseconds; arrays host [levels], may be NULL.
+ * Synchronises.  Errors as sa_run.
+ */
+sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* level_ms);
+
+/*
+ * Synchronise the handle's stream and return the incumbent: the best restart
+ * point over all levels run so far (x_out: host [n], f_out: host scalar, both
+ * may be NULL) and statistics (st may be NULL).  f is evaluated in FP64.
+ * `problem` must be 0 for a single-problem handle.
+ * Errors: SA_ESTATE before the first level or on a failed handle, SA_EINVAL
+ * on a bad problem index, SA_ECUDA / SA_ETIMEOUT / SA_ENUMERIC from the device.
+ */
+sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, sa_stats* st);
+
+/*
+ * Per-level log of one problem (synchronises): for each completed level l <
+ * cap, argmin[l] = p*, f_level[l] = F(x_{p*}) in FP64, f_inc[l] = the
+ * incumbent after level l, t_ns[l] = device clock (ns) when level l ended.
+ * Any output may be NULL.  *count = levels written.
+ */
+sa_status sa_level_log(sa_handle* h, int32_t problem, int64_t* argmin, double* f_level,
+                       double* f_inc, int64_t* t_ns, int32_t cap, int32_t* count);
+
+/*
+ * Accept bits recorded for traced level `level` (< trace_levels, completed):
+ * bits_out[c * words + s / 32] bit (s % 32) = 1 iff step s of chain c was
+ * accepted, words = ceil(L / 32).  `nwords` must be >= chains * words.
+ */
+sa_status sa_trace(sa_handle* h, int32_t level, uint32_t* bits_out, size_t nwords);
+
+/*
+ * Final states of the last completed traced level (synchronises): X_out
+ * host [chains * n] (chain-major), F_out host [chains] f in FP64.  Only
+ * available when that level was traced.
+ */
+sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_out);
+
+/*
+ * Serialise the state between levels (restart point, incumbent, level index,
+ * counters) into buf.  With buf == NULL, *len receives the size needed.
+ * Errors: SA_EINVAL if *len is too small.  Synchronises.
+ */
+sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len);
+
+/* Restore a checkpoint taken from a handle created with identical arguments.
+ * Continuing reproduces the uninterrupted run bit for bit (the random streams
+ * are counter-based on (step, level, chain)).  Errors: SA_EINVAL on a size,
+ * version or fingerprint mismatch. */
+sa_status sa_restore(sa_handle* h, const void* buf, size_t len);
+
+/* Release the handle and its device memory (stream-ordered).  NULL is a no-op. */
+void sa_destroy(sa_handle* h);
+
+const char* sa_strerror(sa_status s);
+
+/*
+ * Kernel-level entry point: Philox4x32-10 (Salmon et al., SC'11) blocks for
+ * counters (c0 + i, c1, c2, c3), i = 0..count-1, with key (key0, key1);
+ * block i goes to d_out[4 i .. 4 i + 3].  d_out: device, >= 4 count uint32.
+ * Errors: SA_EINVAL if count < 0 or d_out == NULL with count > 0.
+ */
+sa_status sa_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t key0,
+                         uint32_t key1, int64_t count, uint32_t* d_out, void* stream);
+
+/*
+ * Kernel-level entry point: the reduction of Sec. 3.2.2 on its own.  Finds
+ * p = argmin_c d_F[c] over c < count (lowest index among equal values; NaN
+ * never wins) and writes it to *d_index and d_F[p] to *d_value (device).
+ * d_scratch: device, >= sa_argmin_scratch_bytes(count) bytes, caller-owned.
+ * Errors: SA_EINVAL if count < 1 or a pointer is NULL.
+ */
+size_t sa_argmin_scratch_bytes(int64_t count);
+sa_status sa_argmin_f64(const double* d_F, int64_t count, int64_t* d_index, double* d_value,
+                        void* d_scratch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SA_GB300_H */

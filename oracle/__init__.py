@@ -81,6 +81,8 @@ def lib():
             L.sao_init_point.argtypes = [ctypes.POINTER(Cfg), i64, vp]
             L.sao_chain_level.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, vp, vp]
             L.sao_chain_level.restype = f64
+            L.sao_chain_level_steps.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, vp, vp, vp, vp]
+            L.sao_chain_level_steps.restype = f64
             L.sao_run.argtypes = [ctypes.POINTER(Cfg), ctypes.POINTER(Out)]
             L.sao_run.restype = ctypes.c_int
             L.sao_level_chains.argtypes = [ctypes.POINTER(Cfg), i32, vp, i64, i64, vp, vp, vp, vp]
@@ -175,6 +177,17 @@ class Problem:
         acc = np.zeros(1, np.int64)
         F = lib().sao_chain_level(ctypes.byref(cfg), level, c, _p(x), _p(bits), _p(acc))
         return F, x, int(acc[0]), bits
+
+    def chain_steps(self, level, c, x_start=None):
+        """One chain for one level with per-step diagnostics: (F_end, x_end, bits, dF[L], tau[L])."""
+        cfg = self.cfg()
+        x = self.init_point(c) if x_start is None else np.array(x_start, np.float64)
+        bits = np.zeros((self.L + 31) // 32, np.uint32)
+        acc = np.zeros(1, np.int64)
+        dF = np.zeros(self.L)
+        tau = np.zeros(self.L)
+        F = lib().sao_chain_level_steps(ctypes.byref(cfg), level, c, _p(x), _p(bits), _p(acc), _p(dF), _p(tau))
+        return F, x, bits, dF, tau
 
     def level_chains(self, level, c0, c1, x_start=None, want_x=False, trace=False):
         """One level for chains [c0, c1); returns dict of per-chain results."""

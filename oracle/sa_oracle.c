@@ -281,8 +281,8 @@ static double f_from_gsum(int32_t cost, int n, double s) {
  * On return x holds the final state and the function returns f(x) recomputed
  * from the definition.  bits (may be NULL) receives the accept decisions.
  */
-double sao_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
-                       uint32_t* bits, int64_t* n_accept) {
+static double chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
+                          uint32_t* bits, int64_t* n_accept, double* dF_out, double* tau_out) {
     const int n = cfg->n;
     const double T = sao_temperature(cfg->T0, cfg->rho, level);
     const double s_l = sqrt(T / cfg->T0);
@@ -338,6 +338,8 @@ double sao_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
 
         /* Metropolis criterion, Eq. "proba" with k_b = 1. */
         const int accept = (dF <= 0.0) || (u3 < exp(-dF / T));
+        if (dF_out) dF_out[s] = dF;
+        if (tau_out) tau_out[s] = -T * log(u3); /* the same test written as dF < tau */
         if (accept) {
             x[d] = xp;
             ++acc;
@@ -356,6 +358,18 @@ double sao_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
     free(yp);
     if (n_accept) *n_accept = acc;
     return Fend;
+}
+
+double sao_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
+                       uint32_t* bits, int64_t* n_accept) {
+    return chain_level(cfg, level, c, x, bits, n_accept, NULL, NULL);
+}
+
+/* The same, also returning every step's dF and threshold tau = -T ln u3
+ * (diagnostics for judging near-ties of reduced-precision decisions). */
+double sao_chain_level_steps(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
+                             uint32_t* bits, int64_t* n_accept, double* dF_out, double* tau_out) {
+    return chain_level(cfg, level, c, x, bits, n_accept, dF_out, tau_out);
 }
 
 /*

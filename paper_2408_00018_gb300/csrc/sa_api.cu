@@ -1,0 +1,717 @@
+// sa_api.cu -- the C ABI of include/sa.h: handle life cycle, level loop
+// (captured once as CUDA graphs and replayed), results, log, checkpoints.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sa.h"
+#include "sa_internal.h"
+
+namespace sa {
+size_t sweep_f32_smem_bytes(int n, int block);
+size_t sweep_f64_smem_bytes(int n, int block);
+cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                               int64_t count, uint32_t* out, cudaStream_t s);
+int64_t argmin_num_parts(int64_t count);
+cudaError_t launch_argmin_f64(const double* F, int64_t count, int64_t* idx, double* val, void* scratch, cudaStream_t s);
+}  // namespace sa
+
+using namespace sa;
+
+namespace {
+
+constexpr uint32_t kCkptMagic = 0x42475341u;  // "ASGB"
+constexpr uint32_t kCkptVersion = 1u;
+constexpr int kGraphLevels = 8;
+
+struct HostProb {
+    int32_t cost, n;
+    int64_t chains, chain_base, x_base;
+    std::vector<double> lo, hi, Q;
+    ProbDev dev;  // with device pointers
+};
+
+}  // namespace
+
+struct sa_handle {
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    sa_schedule sch{};
+    uint64_t seed = 0;
+    int32_t L = 0;
+    int32_t levels_total = 0;
+    int32_t levels_done = 0;
+    int32_t words = 0;
+    int precision = 0;
+    int64_t total_chains = 0;
+    int64_t total_x = 0;
+    std::vector<HostProb> probs;
+    std::vector<WorkItem> items;
+    int block = 0;
+    size_t smem = 0;
+    int max_argmin_blocks = 0;
+    uint64_t fingerprint = 0;
+    sa_status failed = SA_OK;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+    // device
+    std::vector<void*> allocs;
+    ProbDev* d_probs = nullptr;
+    WorkItem* d_items = nullptr;
+    RunDev* d_run = nullptr;
+    double* d_T = nullptr;
+    double* d_s = nullptr;
+    double* d_F = nullptr;
+    float* d_X32 = nullptr;
+    double* d_X64 = nullptr;
+    uint32_t* d_bits = nullptr;
+    SweepArgs args{};
+    cudaGraphExec_t g1 = nullptr, gN = nullptr;
+};
+
+namespace {
+
+sa_status fail(sa_handle* h, sa_status s) {
+    if (h && h->failed == SA_OK) h->failed = s;
+    return s;
+}
+
+template <class T>
+sa_status dalloc(sa_handle* h, T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMallocAsync(&q, count * sizeof(T), h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SA_ENOMEM;
+    }
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return SA_OK;
+}
+
+template <class T>
+sa_status h2d(sa_handle* h, T* dst, const T* src, size_t count) {
+    if (count == 0) return SA_OK;
+    h->h2d_bytes += (int64_t)(count * sizeof(T));
+    return cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream) == cudaSuccess ? SA_OK : SA_ECUDA;
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t len) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < len; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+float round_up_f(double v) {
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafterf(f, INFINITY);
+    return f;
+}
+float round_down_f(double v) {
+    float f = (float)v;
+    if ((double)f > v) f = std::nextafterf(f, -INFINITY);
+    return f;
+}
+
+sa_status check_schedule(const sa_schedule* s) {
+    if (!s) return SA_EINVAL;
+    if (!(s->T0 > 0.0) || !std::isfinite(s->T0)) return SA_EINVAL;
+    if (!(s->rho > 0.0 && s->rho < 1.0)) return SA_EINVAL;
+    if (s->levels < 0) return SA_EINVAL;
+    if (s->levels == 0 && !(s->T_min > 0.0 && s->T_min < s->T0)) return SA_EINVAL;
+    if (!(s->sigma_frac > 0.0) || !std::isfinite(s->sigma_frac)) return SA_EINVAL;
+    if (s->boundary != SA_REFLECT && s->boundary != SA_CLIP) return SA_EINVAL;
+    if (s->precision != SA_FP64 && s->precision != SA_FP32) return SA_EINVAL;
+    if (s->surrogate != 0 || s->polish_k != 0) return SA_EINVAL;
+    if (s->trace_levels < 0) return SA_EINVAL;
+    return SA_OK;
+}
+
+int pick_block(int precision, int n_max) {
+    // FP64 arithmetic is a small fraction of the FP32 rate on this GPU, so the
+    // FP64 sweep uses one warp per block: chains spread over as many SMs as
+    // possible.
+    if (precision == SA_FP64) return 32;
+    // ~64 KB of chain state per block: several blocks per SM, so that one
+    // block's end-of-level work overlaps the others' sweeps.
+    const int bytes = 4;
+    int b = 65536 / (bytes * n_max);
+    b = (b / 32) * 32;
+    if (b > 256) b = 256;
+    if (b < 32) b = 32;
+    return b;
+}
+
+cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
+    if (h->precision == SA_FP64) return launch_sweep_f64(h->args, (int)h->items.size(), h->block, h->smem, s);
+    return launch_sweep_f32(h->args, (int)h->items.size(), h->block, h->smem, s);
+}
+
+cudaError_t launch_level_tail(sa_handle* h, cudaStream_t s) {
+    cudaError_t e = launch_argmin_restart(h->args, h->d_probs, (int)h->probs.size(), h->max_argmin_blocks,
+                                          h->precision == SA_FP64 ? 0 : 1, s);
+    if (e == cudaSuccess) e = launch_level_end(h->d_run, s);
+    return e;
+}
+
+sa_status capture_levels(sa_handle* h, int levels, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SA_ECUDA;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < levels && e == cudaSuccess; ++k) {
+        e = launch_sweep(h, h->cap_stream);
+        if (e == cudaSuccess) e = launch_level_tail(h, h->cap_stream);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return SA_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? SA_OK : SA_ECUDA;
+}
+
+sa_status device_status(sa_handle* h) {
+    int32_t st = 0;
+    if (cudaMemcpyAsync(&st, &h->d_run->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return fail(h, SA_ECUDA);
+    if (st == 5) return fail(h, SA_ENUMERIC);
+    if (st == 4) return fail(h, SA_ETIMEOUT);
+    if (st != 0) return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
+sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, const int32_t* ns,
+                const int64_t* chains, int32_t num) {
+    sa_status st;
+    const int P = num;
+    int n_max = 1;
+    h->total_chains = 0;
+    h->total_x = 0;
+    h->probs.resize(P);
+    for (int p = 0; p < P; ++p) {
+        HostProb& hp = h->probs[p];
+        hp.cost = problems[p].cost;
+        hp.n = ns[p];
+        hp.chains = chains[p];
+        hp.chain_base = h->total_chains;
+        hp.x_base = h->total_x;
+        h->total_chains += hp.chains;
+        h->total_x += (int64_t)hp.n * hp.chains;
+        hp.lo.assign(boxes[p].lo, boxes[p].lo + hp.n);
+        hp.hi.assign(boxes[p].hi, boxes[p].hi + hp.n);
+        if (hp.n > n_max) n_max = hp.n;
+    }
+    h->words = (h->L + 31) / 32;
+    h->levels_total = h->sch.levels > 0 ? h->sch.levels : sa_levels_for(h->sch.T0, h->sch.rho, h->sch.T_min);
+    if (h->levels_total < 1) return SA_EINVAL;
+
+    // launch shape
+    h->block = pick_block(h->precision, n_max);
+    h->smem = h->precision == SA_FP64 ? sweep_f64_smem_bytes(n_max, h->block) : sweep_f32_smem_bytes(n_max, h->block);
+    int dev = 0, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((int)h->smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
+    if ((h->precision == SA_FP64 ? sweep_f64_set_smem(h->smem) : sweep_f32_set_smem(h->smem)) != cudaSuccess)
+        return SA_ECUDA;
+    for (int p = 0; p < P; ++p)
+        for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += h->block) {
+            const int64_t cnt = h->probs[p].chains - c0 < h->block ? h->probs[p].chains - c0 : h->block;
+            h->items.push_back(WorkItem{p, (int32_t)cnt, c0});
+        }
+    h->max_argmin_blocks = 1;
+
+    // device memory
+    if ((st = dalloc(h, &h->d_probs, P)) || (st = dalloc(h, &h->d_items, h->items.size())) ||
+        (st = dalloc(h, &h->d_run, 1)) || (st = dalloc(h, &h->d_T, h->levels_total)) ||
+        (st = dalloc(h, &h->d_s, h->levels_total)) || (st = dalloc(h, &h->d_F, h->total_chains)))
+        return st;
+    if (h->precision == SA_FP64) { if ((st = dalloc(h, &h->d_X64, h->total_x))) return st; }
+    else if ((st = dalloc(h, &h->d_X32, h->total_x))) return st;
+    const int tl = h->sch.trace_levels < h->levels_total ? h->sch.trace_levels : h->levels_total;
+    if (tl > 0 && (st = dalloc(h, &h->d_bits, (size_t)tl * h->total_chains * h->words))) return st;
+
+    std::vector<ProbDev> pd(P);
+    for (int p = 0; p < P; ++p) {
+        HostProb& hp = h->probs[p];
+        const int n = hp.n;
+        ProbDev d{};
+        d.cost = hp.cost;
+        d.n = n;
+        d.chains = hp.chains;
+        d.chain_base = hp.chain_base;
+        d.x_base = hp.x_base;
+        d.pid = (uint32_t)p;
+        const int64_t span = (int64_t)kArgminThreads * kArgminPerThread;
+        d.nblk_argmin = (int32_t)((hp.chains + span - 1) / span);
+        if (d.nblk_argmin > h->max_argmin_blocks) h->max_argmin_blocks = d.nblk_argmin;
+        std::vector<double> sig(n);
+        std::vector<float> lo32(n), hi32(n), sig32(n);
+        for (int k = 0; k < n; ++k) {
+            sig[k] = h->sch.sigma_frac * (hp.hi[k] - hp.lo[k]);
+            lo32[k] = round_up_f(hp.lo[k]);
+            hi32[k] = round_down_f(hp.hi[k]);
+            if (lo32[k] > hi32[k]) lo32[k] = hi32[k] = (float)hp.lo[k];
+            sig32[k] = (float)sig[k];
+        }
+        double *dlo, *dhi, *dsig, *xb64, *xinc, *scal, *pval, *lf, *lfi;
+        float *dlo32, *dhi32, *dsig32, *xb32;
+        unsigned long long *lmin, *acc;
+        unsigned int* done;
+        int64_t *pidx, *la;
+        long long* lt;
+        if ((st = dalloc(h, &dlo, n)) || (st = dalloc(h, &dhi, n)) || (st = dalloc(h, &dsig, n)) ||
+            (st = dalloc(h, &dlo32, n)) || (st = dalloc(h, &dhi32, n)) || (st = dalloc(h, &dsig32, n)) ||
+            (st = dalloc(h, &xb64, n)) || (st = dalloc(h, &xb32, n)) || (st = dalloc(h, &xinc, n)) ||
+            (st = dalloc(h, &scal, kNumScalars)) || (st = dalloc(h, &lmin, 1)) || (st = dalloc(h, &done, 1)) ||
+            (st = dalloc(h, &pval, d.nblk_argmin)) || (st = dalloc(h, &pidx, d.nblk_argmin)) ||
+            (st = dalloc(h, &la, h->levels_total)) || (st = dalloc(h, &lf, h->levels_total)) ||
+            (st = dalloc(h, &lfi, h->levels_total)) || (st = dalloc(h, &lt, h->levels_total)) ||
+            (st = dalloc(h, &acc, 1)))
+            return st;
+        d.lo = dlo; d.hi = dhi; d.sig = dsig; d.lo32 = dlo32; d.hi32 = dhi32; d.sig32 = dsig32;
+        d.x_best64 = xb64; d.x_best32 = xb32; d.x_inc = xinc; d.scal = scal; d.level_min = lmin; d.done = done;
+        d.part_val = pval; d.part_idx = pidx; d.log_argmin = la; d.log_f = lf; d.log_finc = lfi; d.log_t = lt;
+        d.accepts = acc;
+        hp.dev = d;
+        pd[p] = d;
+        std::vector<double> sc(kNumScalars, 0.0);
+        sc[kFBest] = INFINITY;
+        sc[kFInc] = INFINITY;
+        const unsigned long long inf_key = 0xFFF0000000000000ull;
+        const unsigned int zero = 0;
+        const unsigned long long zero64 = 0;
+        std::vector<double> zeros(n, 0.0);
+        std::vector<float> zf(n, 0.0f);
+        if ((st = h2d(h, dlo, hp.lo.data(), n)) || (st = h2d(h, dhi, hp.hi.data(), n)) ||
+            (st = h2d(h, dsig, sig.data(), n)) || (st = h2d(h, dlo32, lo32.data(), n)) ||
+            (st = h2d(h, dhi32, hi32.data(), n)) || (st = h2d(h, dsig32, sig32.data(), n)) ||
+            (st = h2d(h, scal, sc.data(), kNumScalars)) || (st = h2d(h, lmin, &inf_key, 1)) ||
+            (st = h2d(h, done, &zero, 1)) || (st = h2d(h, acc, &zero64, 1)) || (st = h2d(h, xinc, zeros.data(), n)) ||
+            (st = h2d(h, xb64, zeros.data(), n)) || (st = h2d(h, xb32, zf.data(), n)))
+            return st;
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SA_ECUDA;  // host temporaries die here
+    }
+    std::vector<double> T(h->levels_total), s(h->levels_total);
+    double Tl = h->sch.T0;
+    for (int l = 0; l < h->levels_total; ++l) {
+        T[l] = Tl;
+        s[l] = std::sqrt(Tl / h->sch.T0);
+        Tl = Tl * h->sch.rho;
+    }
+    RunDev run{0, 0, 0};
+    if ((st = h2d(h, h->d_probs, pd.data(), P)) || (st = h2d(h, h->d_items, h->items.data(), h->items.size())) ||
+        (st = h2d(h, h->d_run, &run, 1)) || (st = h2d(h, h->d_T, T.data(), T.size())) ||
+        (st = h2d(h, h->d_s, s.data(), s.size())))
+        return st;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SA_ECUDA;
+
+    SweepArgs& a = h->args;
+    a.probs = h->d_probs;
+    a.items = h->d_items;
+    a.run = h->d_run;
+    a.T_tab = h->d_T;
+    a.s_tab = h->d_s;
+    a.F = h->d_F;
+    a.X32 = h->d_X32;
+    a.X64 = h->d_X64;
+    a.bits = h->d_bits;
+    a.total_chains = h->total_chains;
+    a.L = h->L;
+    a.words = h->words;
+    a.trace_levels = tl;
+    a.boundary = h->sch.boundary;
+    a.key0 = (uint32_t)h->seed;
+    a.key1 = (uint32_t)(h->seed >> 32) ^ kTagSweep;
+    a.ikey0 = (uint32_t)h->seed;
+    a.ikey1 = (uint32_t)(h->seed >> 32) ^ kTagInit;
+
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return SA_ECUDA;
+    if ((st = capture_levels(h, 1, &h->g1))) return st;
+    if (h->levels_total >= kGraphLevels && (st = capture_levels(h, kGraphLevels, &h->gN))) return st;
+
+    uint64_t fp = 1469598103934665603ull;
+    fp = fnv(fp, &h->sch, sizeof(h->sch));
+    fp = fnv(fp, &h->seed, sizeof(h->seed));
+    fp = fnv(fp, &h->L, sizeof(h->L));
+    for (auto& hp : h->probs) {
+        fp = fnv(fp, &hp.cost, sizeof(hp.cost));
+        fp = fnv(fp, &hp.n, sizeof(hp.n));
+        fp = fnv(fp, &hp.chains, sizeof(hp.chains));
+        fp = fnv(fp, hp.lo.data(), hp.lo.size() * sizeof(double));
+        fp = fnv(fp, hp.hi.data(), hp.hi.size() * sizeof(double));
+    }
+    h->fingerprint = fp;
+    return SA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sa_default_schedule(sa_schedule* s) {
+    if (!s) return;
+    std::memset(s, 0, sizeof(*s));
+    s->T0 = 100.0;
+    s->rho = 0.9;
+    s->T_min = 0.0;
+    s->levels = 50;
+    s->sigma_frac = 0.1;
+    s->boundary = SA_REFLECT;
+    s->precision = SA_FP64;
+}
+
+int32_t sa_levels_for(double T0, double rho, double T_min) {
+    if (!(T0 > 0.0) || !(rho > 0.0 && rho < 1.0) || !(T_min > 0.0)) return -1;
+    double T = T0;
+    int32_t k = 0;
+    do {
+        ++k;
+        T = T * rho;
+    } while (T > T_min && k < 100000000);
+    return k;
+}
+
+const char* sa_strerror(sa_status s) {
+    switch (s) {
+    case SA_OK: return "ok";
+    case SA_EINVAL: return "invalid argument";
+    case SA_ENOMEM: return "out of memory";
+    case SA_ECUDA: return "CUDA error";
+    case SA_ETIMEOUT: return "bounded device wait timed out";
+    case SA_ENUMERIC: return "non-finite best state";
+    case SA_ESTATE: return "handle in error state or call out of order";
+    }
+    return "unknown status";
+}
+
+sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains, int32_t L,
+                    const sa_schedule* schedule, uint64_t seed, void* stream, sa_handle** out) {
+    if (out) *out = nullptr;
+    if (!problem || !box || !out || !box->lo || !box->hi || n < 1 || chains < 1 || chains > 2147483647LL || L < 1)
+        return SA_EINVAL;
+    if (check_schedule(schedule) != SA_OK) return SA_EINVAL;
+    if (problem->cost < SA_SCHWEFEL || problem->cost > SA_ROSENBROCK) return SA_EINVAL;  // rotated: not in this build yet
+    for (int k = 0; k < n; ++k)
+        if (!std::isfinite(box->lo[k]) || !std::isfinite(box->hi[k]) || box->lo[k] > box->hi[k]) return SA_EINVAL;
+    sa_handle* h = new (std::nothrow) sa_handle();
+    if (!h) return SA_ENOMEM;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->sch = *schedule;
+    h->seed = seed;
+    h->L = L;
+    h->precision = schedule->precision;
+    sa_status st = build(h, problem, box, &n, &chains, 1);
+    if (st != SA_OK) {
+        sa_destroy(h);
+        return st;
+    }
+    *out = h;
+    return SA_OK;
+}
+
+sa_status sa_run(sa_handle* h, int32_t levels) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (levels == 0 || levels < -1) return SA_EINVAL;
+    const int remaining = h->levels_total - h->levels_done;
+    if (remaining <= 0) return SA_ESTATE;
+    int k = (levels == -1 || levels > remaining) ? remaining : levels;
+    if (h->levels_done == 0 && launch_stamp_start(h->d_run, h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    while (k > 0) {
+        cudaError_t e;
+        int step;
+        if (h->gN && k >= kGraphLevels) { e = cudaGraphLaunch(h->gN, h->stream); step = kGraphLevels; }
+        else { e = cudaGraphLaunch(h->g1, h->stream); step = 1; }
+        if (e != cudaSuccess) return fail(h, SA_ECUDA);
+        h->levels_done += step;
+        k -= step;
+    }
+    return SA_OK;
+}
+
+sa_status sa_reset(sa_handle* h) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (launch_reset(h->d_probs, (int)h->probs.size(), h->d_run, h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    h->levels_done = 0;
+    return SA_OK;
+}
+
+sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* level_ms) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (levels == 0 || levels < -1) return SA_EINVAL;
+    const int remaining = h->levels_total - h->levels_done;
+    if (remaining <= 0) return SA_ESTATE;
+    const int k = (levels == -1 || levels > remaining) ? remaining : levels;
+    std::vector<cudaEvent_t> ev(3 * (size_t)k, nullptr);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto& f : ev) if (f) cudaEventDestroy(f);
+            return fail(h, SA_ECUDA);
+        }
+    sa_status st = SA_OK;
+    if (h->levels_done == 0 && launch_stamp_start(h->d_run, h->stream) != cudaSuccess) st = SA_ECUDA;
+    for (int l = 0; l < k && st == SA_OK; ++l) {
+        if (cudaEventRecord(ev[3 * l], h->stream) != cudaSuccess || launch_sweep(h, h->stream) != cudaSuccess ||
+            cudaEventRecord(ev[3 * l + 1], h->stream) != cudaSuccess || launch_level_tail(h, h->stream) != cudaSuccess ||
+            cudaEventRecord(ev[3 * l + 2], h->stream) != cudaSuccess)
+            st = SA_ECUDA;
+        else
+            h->levels_done += 1;
+    }
+    if (st == SA_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = SA_ECUDA;
+    for (int l = 0; l < k && st == SA_OK; ++l) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, ev[3 * l], ev[3 * l + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&b, ev[3 * l], ev[3 * l + 2]) != cudaSuccess) {
+            st = SA_ECUDA;
+            break;
+        }
+        if (sweep_ms) sweep_ms[l] = a;
+        if (level_ms) level_ms[l] = b;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return st == SA_OK ? SA_OK : fail(h, st);
+}
+
+sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, sa_stats* stt) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (problem < 0 || problem >= (int)h->probs.size()) return SA_EINVAL;
+    if (h->levels_done == 0) return SA_ESTATE;
+    sa_status st = device_status(h);
+    if (st != SA_OK) return st;
+    const HostProb& hp = h->probs[problem];
+    std::vector<double> sc(kNumScalars);
+    unsigned long long acc = 0;
+    int64_t am = -1;
+    long long t0 = 0;
+    h->d2h_bytes += (int64_t)(sizeof(double) * kNumScalars + sizeof(acc) + sizeof(am) + sizeof(t0) +
+                              (x_out ? sizeof(double) * hp.n : 0));
+    if (cudaMemcpyAsync(sc.data(), hp.dev.scal, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, h->stream) ||
+        cudaMemcpyAsync(&t0, &h->d_run->t_start, sizeof(t0), cudaMemcpyDeviceToHost, h->stream) ||
+        cudaMemcpyAsync(&acc, hp.dev.accepts, sizeof(acc), cudaMemcpyDeviceToHost, h->stream) ||
+        cudaMemcpyAsync(&am, hp.dev.log_argmin + (h->levels_done - 1), sizeof(am), cudaMemcpyDeviceToHost, h->stream) ||
+        (x_out && cudaMemcpyAsync(x_out, hp.dev.x_inc, sizeof(double) * hp.n, cudaMemcpyDeviceToHost, h->stream)) ||
+        cudaStreamSynchronize(h->stream))
+        return fail(h, SA_ECUDA);
+    if (f_out) *f_out = sc[kFInc];
+    if (stt) {
+        stt->steps = hp.chains * (int64_t)h->L * h->levels_done;
+        stt->accepts = (int64_t)acc;
+        stt->levels_done = h->levels_done;
+        stt->levels_total = h->levels_total;
+        stt->f_level = sc[kFBest];
+        stt->argmin = am;
+        stt->h2d_bytes = h->h2d_bytes;
+        stt->d2h_bytes = h->d2h_bytes;
+        stt->t_start_ns = t0;
+    }
+    return SA_OK;
+}
+
+sa_status sa_level_log(sa_handle* h, int32_t problem, int64_t* argmin, double* f_level, double* f_inc, int64_t* t_ns,
+                       int32_t cap, int32_t* count) {
+    if (!h || cap < 0) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (problem < 0 || problem >= (int)h->probs.size()) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    const ProbDev& d = h->probs[problem].dev;
+    const int m = cap < h->levels_done ? cap : h->levels_done;
+    if (m > 0) {
+        if ((argmin && cudaMemcpy(argmin, d.log_argmin, sizeof(int64_t) * m, cudaMemcpyDeviceToHost)) ||
+            (f_level && cudaMemcpy(f_level, d.log_f, sizeof(double) * m, cudaMemcpyDeviceToHost)) ||
+            (f_inc && cudaMemcpy(f_inc, d.log_finc, sizeof(double) * m, cudaMemcpyDeviceToHost)) ||
+            (t_ns && cudaMemcpy(t_ns, d.log_t, sizeof(int64_t) * m, cudaMemcpyDeviceToHost)))
+            return fail(h, SA_ECUDA);
+    }
+    if (count) *count = m;
+    return SA_OK;
+}
+
+sa_status sa_trace(sa_handle* h, int32_t level, uint32_t* bits_out, size_t nwords) {
+    if (!h || !bits_out) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (level < 0 || level >= h->args.trace_levels || level >= h->levels_done) return SA_EINVAL;
+    const size_t need = (size_t)h->total_chains * h->words;
+    if (nwords < need) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    if (cudaMemcpy(bits_out, h->d_bits + (size_t)level * need, need * sizeof(uint32_t), cudaMemcpyDeviceToHost))
+        return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
+sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_out) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (level < 0 || level != h->levels_done - 1 || level >= h->args.trace_levels) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    if (F_out && cudaMemcpy(F_out, h->d_F, sizeof(double) * h->total_chains, cudaMemcpyDeviceToHost))
+        return fail(h, SA_ECUDA);
+    if (X_out) {
+        for (const HostProb& hp : h->probs) {
+            const size_t cnt = (size_t)hp.n * hp.chains;
+            std::vector<double> tmp(cnt);
+            if (h->precision == SA_FP64) {
+                if (cudaMemcpy(tmp.data(), h->d_X64 + hp.x_base, cnt * sizeof(double), cudaMemcpyDeviceToHost))
+                    return fail(h, SA_ECUDA);
+            } else {
+                std::vector<float> tf(cnt);
+                if (cudaMemcpy(tf.data(), h->d_X32 + hp.x_base, cnt * sizeof(float), cudaMemcpyDeviceToHost))
+                    return fail(h, SA_ECUDA);
+                for (size_t i = 0; i < cnt; ++i) tmp[i] = tf[i];
+            }
+            double* dst = X_out + hp.x_base;
+            for (int64_t c = 0; c < hp.chains; ++c)
+                for (int k = 0; k < hp.n; ++k) dst[(size_t)c * hp.n + k] = tmp[(size_t)k * hp.chains + c];
+        }
+    }
+    return SA_OK;
+}
+
+sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len) {
+    if (!h || !len) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    size_t need = 4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(int32_t) * 2;
+    for (const HostProb& hp : h->probs)
+        need += sizeof(double) * (kNumScalars + 2 * (size_t)hp.n) + sizeof(uint64_t) +
+                (size_t)h->levels_done * (sizeof(int64_t) * 2 + sizeof(double) * 2);
+    if (!buf) { *len = need; return SA_OK; }
+    if (*len < need) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    auto put = [&p](const void* src, size_t n) { std::memcpy(p, src, n); p += n; };
+    const uint32_t hdr[4] = {kCkptMagic, kCkptVersion, (uint32_t)h->probs.size(), (uint32_t)h->precision};
+    put(hdr, sizeof(hdr));
+    put(&h->fingerprint, sizeof(uint64_t));
+    put(&h->levels_done, sizeof(int32_t));
+    put(&h->levels_total, sizeof(int32_t));
+    for (const HostProb& hp : h->probs) {
+        const ProbDev& d = hp.dev;
+        std::vector<double> sc(kNumScalars), xb(hp.n), xi(hp.n);
+        unsigned long long acc = 0;
+        const int m = h->levels_done;
+        std::vector<int64_t> la(m), lt(m);
+        std::vector<double> lf(m), lfi(m);
+        if (cudaMemcpy(sc.data(), d.scal, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost) ||
+            cudaMemcpy(xi.data(), d.x_inc, sizeof(double) * hp.n, cudaMemcpyDeviceToHost) ||
+            cudaMemcpy(&acc, d.accepts, sizeof(acc), cudaMemcpyDeviceToHost))
+            return fail(h, SA_ECUDA);
+        if (h->precision == SA_FP64) {
+            if (cudaMemcpy(xb.data(), d.x_best64, sizeof(double) * hp.n, cudaMemcpyDeviceToHost)) return fail(h, SA_ECUDA);
+        } else {
+            std::vector<float> xf(hp.n);
+            if (cudaMemcpy(xf.data(), d.x_best32, sizeof(float) * hp.n, cudaMemcpyDeviceToHost)) return fail(h, SA_ECUDA);
+            for (int k = 0; k < hp.n; ++k) xb[k] = xf[k];
+        }
+        if (m > 0 && (cudaMemcpy(la.data(), d.log_argmin, sizeof(int64_t) * m, cudaMemcpyDeviceToHost) ||
+                      cudaMemcpy(lf.data(), d.log_f, sizeof(double) * m, cudaMemcpyDeviceToHost) ||
+                      cudaMemcpy(lfi.data(), d.log_finc, sizeof(double) * m, cudaMemcpyDeviceToHost) ||
+                      cudaMemcpy(lt.data(), d.log_t, sizeof(int64_t) * m, cudaMemcpyDeviceToHost)))
+            return fail(h, SA_ECUDA);
+        put(sc.data(), sizeof(double) * kNumScalars);
+        put(xb.data(), sizeof(double) * hp.n);
+        put(xi.data(), sizeof(double) * hp.n);
+        put(&acc, sizeof(uint64_t));
+        put(la.data(), sizeof(int64_t) * m);
+        put(lf.data(), sizeof(double) * m);
+        put(lfi.data(), sizeof(double) * m);
+        put(lt.data(), sizeof(int64_t) * m);
+    }
+    *len = need;
+    return SA_OK;
+}
+
+sa_status sa_restore(sa_handle* h, const void* buf, size_t len) {
+    if (!h || !buf) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    const unsigned char* p = static_cast<const unsigned char*>(buf);
+    const unsigned char* end = p + len;
+    auto get = [&p, end](void* dst, size_t n) {
+        if ((size_t)(end - p) < n) return false;
+        std::memcpy(dst, p, n);
+        p += n;
+        return true;
+    };
+    uint32_t hdr[4];
+    uint64_t fp;
+    int32_t done, total;
+    if (!get(hdr, sizeof(hdr)) || !get(&fp, sizeof(fp)) || !get(&done, sizeof(done)) || !get(&total, sizeof(total)))
+        return SA_EINVAL;
+    if (hdr[0] != kCkptMagic || hdr[1] != kCkptVersion || hdr[2] != h->probs.size() || hdr[3] != (uint32_t)h->precision ||
+        fp != h->fingerprint || total != h->levels_total || done < 0 || done > total)
+        return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    for (const HostProb& hp : h->probs) {
+        const ProbDev& d = hp.dev;
+        std::vector<double> sc(kNumScalars), xb(hp.n), xi(hp.n);
+        uint64_t acc;
+        std::vector<int64_t> la(done), lt(done);
+        std::vector<double> lf(done), lfi(done);
+        if (!get(sc.data(), sizeof(double) * kNumScalars) || !get(xb.data(), sizeof(double) * hp.n) ||
+            !get(xi.data(), sizeof(double) * hp.n) || !get(&acc, sizeof(acc)) || !get(la.data(), sizeof(int64_t) * done) ||
+            !get(lf.data(), sizeof(double) * done) || !get(lfi.data(), sizeof(double) * done) ||
+            !get(lt.data(), sizeof(int64_t) * done))
+            return SA_EINVAL;
+        std::vector<float> xf(hp.n);
+        for (int k = 0; k < hp.n; ++k) xf[k] = (float)xb[k];
+        if (cudaMemcpy(d.scal, sc.data(), sizeof(double) * kNumScalars, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(d.x_inc, xi.data(), sizeof(double) * hp.n, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(d.x_best64, xb.data(), sizeof(double) * hp.n, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(d.x_best32, xf.data(), sizeof(float) * hp.n, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(d.accepts, &acc, sizeof(acc), cudaMemcpyHostToDevice))
+            return fail(h, SA_ECUDA);
+        if (done > 0 && (cudaMemcpy(d.log_argmin, la.data(), sizeof(int64_t) * done, cudaMemcpyHostToDevice) ||
+                         cudaMemcpy(d.log_f, lf.data(), sizeof(double) * done, cudaMemcpyHostToDevice) ||
+                         cudaMemcpy(d.log_finc, lfi.data(), sizeof(double) * done, cudaMemcpyHostToDevice) ||
+                         cudaMemcpy(d.log_t, lt.data(), sizeof(int64_t) * done, cudaMemcpyHostToDevice)))
+            return fail(h, SA_ECUDA);
+    }
+    RunDev run{done, 0};
+    if (cudaMemcpy(h->d_run, &run, sizeof(run), cudaMemcpyHostToDevice)) return fail(h, SA_ECUDA);
+    h->levels_done = done;
+    return SA_OK;
+}
+
+void sa_destroy(sa_handle* h) {
+    if (!h) return;
+    if (h->g1) cudaGraphExecDestroy(h->g1);
+    if (h->gN) cudaGraphExecDestroy(h->gN);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaGetLastError();
+    delete h;
+}
+
+sa_status sa_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t key0, uint32_t key1, int64_t count,
+                         uint32_t* d_out, void* stream) {
+    if (count < 0 || (count > 0 && !d_out)) return SA_EINVAL;
+    return launch_philox_fill(c0, c1, c2, c3, key0, key1, count, d_out, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? SA_OK : SA_ECUDA;
+}
+
+size_t sa_argmin_scratch_bytes(int64_t count) {
+    if (count < 1) return 0;
+    return (size_t)argmin_num_parts(count) * 16;
+}
+
+sa_status sa_argmin_f64(const double* d_F, int64_t count, int64_t* d_index, double* d_value, void* d_scratch,
+                        void* stream) {
+    if (count < 1 || !d_F || !d_index || !d_value || !d_scratch) return SA_EINVAL;
+    if (argmin_num_parts(count) > 2147483647LL) return SA_EINVAL;
+    return launch_argmin_f64(d_F, count, d_index, d_value, d_scratch, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? SA_OK : SA_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// sa_internal.h -- descriptors shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sa {
+
+// Philox stream tags: key = (seed_lo, seed_hi ^ tag).
+constexpr uint32_t kTagSweep = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+// Scalars kept per problem in device memory.
+enum ScalarSlot : int {
+    kFBest = 0,   // F(x_best) in FP64 (restart point of the next level)
+    kFInc = 1,    // incumbent value
+    kS1 = 2,      // Ackley: sum x_best^2 (FP64)
+    kS2 = 3,      // Ackley: sum cos(2 pi x_best) (FP64)
+    kNumScalars = 8
+};
+
+// One problem of a (possibly batched) run; lives in device memory.
+struct ProbDev {
+    int32_t cost, n;
+    int64_t chains;
+    int64_t chain_base;   // offset of this problem's chains in per-chain arrays
+    int64_t x_base;       // offset (elements) of this problem's [n][chains] state block
+    uint32_t pid;         // Philox counter word 3
+    int32_t nblk_argmin;  // blocks of the argmin kernel for this problem
+    const double* lo;     // [n]
+    const double* hi;     // [n]
+    const double* sig;    // [n] sigma_frac (hi - lo)
+    const float* lo32;    // [n] lo rounded up to FP32
+    const float* hi32;    // [n] hi rounded down to FP32
+    const float* sig32;   // [n]
+    double* x_best64;     // [n] restart point (FP64 path)
+    float* x_best32;      // [n] restart point (FP32 path)
+    double* x_inc;        // [n] incumbent
+    double* scal;         // [kNumScalars]
+    unsigned long long* level_min;  // candidate threshold of the current level (ordered key)
+    unsigned int* done;   // last-block-done counter of the argmin
+    double* part_val;     // [nblk_argmin] partial minima
+    int64_t* part_idx;    // [nblk_argmin]
+    int64_t* log_argmin;  // [levels]
+    double* log_f;        // [levels]
+    double* log_finc;     // [levels]
+    long long* log_t;     // [levels] device clock (ns) at the end of the level
+    unsigned long long* accepts;  // running count of accepted moves
+};
+
+// Device-resident run state shared by all problems of a handle.
+struct RunDev {
+    int32_t level;   // level index the next sweep runs
+    int32_t status;  // sa_status raised on the device (0 = ok)
+    long long t_start;  // device clock (ns) when the current run's level 0 started
+};
+
+struct WorkItem {
+    int32_t problem;
+    int32_t count;   // chains in this tile
+    int64_t c0;      // first chain (problem-local index)
+};
+
+struct SweepArgs {
+    const ProbDev* probs;
+    const WorkItem* items;
+    RunDev* run;
+    const double* T_tab;   // [levels] temperature of each level (repeated multiplication)
+    const double* s_tab;   // [levels] sqrt(T_l / T0)
+    double* F;             // [total chains] FP64 value of each chain's final state (+inf: not a candidate)
+    float* X32;            // state blocks, [n][chains] per problem (FP32 path)
+    double* X64;           // state blocks, [n][chains] per problem (FP64 path)
+    uint32_t* bits;        // [trace_levels][total chains][words] accept bits, or NULL
+    int64_t total_chains;
+    int32_t L;
+    int32_t words;         // ceil(L / 32)
+    int32_t trace_levels;
+    int32_t boundary;      // 0 reflect then clip, 1 clip
+    uint32_t key0, key1;   // Philox key of the sweep stream
+    uint32_t ikey0, ikey1; // Philox key of the initial-point stream
+};
+
+// Launch wrappers (one per translation unit).
+cudaError_t launch_sweep_f32(const SweepArgs& a, int num_items, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_sweep_f64(const SweepArgs& a, int num_items, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_argmin_restart(const SweepArgs& a, const ProbDev* probs, int num_probs, int max_blocks,
+                                  int precision, cudaStream_t s);
+cudaError_t launch_level_end(RunDev* run, cudaStream_t s);
+cudaError_t launch_reset(ProbDev* probs, int num_probs, RunDev* run, cudaStream_t s);
+cudaError_t launch_stamp_start(RunDev* run, cudaStream_t s);
+cudaError_t sweep_f32_set_smem(size_t bytes);
+cudaError_t sweep_f64_set_smem(size_t bytes);
+
+constexpr int kArgminThreads = 256;
+constexpr int kArgminPerThread = 8;
+
+}  // namespace sa

@@ -1,0 +1,340 @@
+// sweep_f32.cu -- Metropolis sweep of one temperature level, FP32 state.
+//
+// One thread runs one Markov chain for the L steps of a level (the kernel of
+// Listing 4): pick a coordinate, Gaussian move, reflect/clip into the box,
+// energy difference, Boltzmann acceptance (Eq. "proba", k_b = 1).  The
+// chain's state lives in shared memory as x[d][lane] (bank = lane, so the
+// random coordinate of each lane never conflicts).  Separable costs use the
+// O(1) difference of the terms that touch coordinate d instead of the
+// paper's full recompute of f(x1).
+//
+// At the end of the level every chain holds F_start + dS with a running
+// bound e on its FP32 error.  The block takes part in a device-wide
+// threshold M = min(F + e) (atomicMin on an ordered key); only chains with
+// F - e <= M can hold the level's minimum, and only those are re-evaluated
+// in FP64 and have their state written to global memory.  The FP64 argmin
+// over those candidates (reduce.cu) is therefore exact.
+#include <cmath>
+#include <cfloat>
+#include <math_constants.h>
+
+#include "sa_device.cuh"
+#include "sa_internal.h"
+
+namespace sa {
+namespace {
+
+constexpr int kMaxBlock = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sums of two doubles; every thread receives the totals.
+__device__ void block_sum2(double& a, double& b, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __syncthreads();
+    if (lane == 0) { red[wid] = a; red[32 + wid] = b; }
+    __syncthreads();
+    double sa_ = 0.0, sb = 0.0;
+    for (int i = 0; i < nw; ++i) { sa_ += red[i]; sb += red[32 + i]; }
+    a = sa_;
+    b = sb;
+}
+
+__device__ double block_min(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_min(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double m = red[0];
+    for (int i = 1; i < nw; ++i) m = fmin(m, red[i]);
+    return m;
+}
+
+// FP64 partial sums of the cost at x (coordinate k of column tc of xs), strided over the block.
+template <int COST>
+__device__ void partials64(const float* xs, int B, int n, int tc, double& p1, double& p2) {
+    p1 = 0.0;
+    p2 = 0.0;
+    for (int k = threadIdx.x; k < n; k += B) {
+        const double x = (double)xs[k * B + tc];
+        if (COST == kSchwefel) p1 += h64_schwefel(x);
+        else if (COST == kRastrigin) p1 += g64_rastrigin(x);
+        else if (COST == kAckley) { p1 += x * x; p2 += cos(6.283185307179586 * x); }
+        else if (COST == kRosenbrock) { if (k + 1 < n) p1 += rosen64(x, (double)xs[(k + 1) * B + tc]); }
+    }
+}
+template <int COST>
+__device__ __forceinline__ double assemble64(int n, double p1, double p2) {
+    if (COST == kSchwefel) return -(p1 / (double)n);
+    if (COST == kRastrigin) return 10.0 * (double)n + p1;
+    if (COST == kAckley) return ackley64(n, p1, p2);
+    return p1;
+}
+
+// FP32 value of the cost at the chain's own column, with an error bound (level 0 start).
+template <int COST>
+__device__ float start_value32(const float* xs, int B, int n, int t, float inv_n, float& eb, SepState& st) {
+    float s = 0.0f, sabs = 0.0f, e = 0.0f;
+    st.s1 = 0.0f;
+    st.s2 = 0.0f;
+    for (int k = 0; k < n; ++k) {
+        const float x = xs[k * B + t];
+        if (COST == kSchwefel) {
+            const float r = sqrt_approx(fabsf(x));
+            const float g = x * sin_reduced(r);
+            e += fabsf(x) * fmaf(r, 9.6e-7f, 2.6e-6f);
+            s += g;
+            sabs += fabsf(g);
+        } else if (COST == kRastrigin) {
+            const float g = g_rastrigin(x);
+            e += 2.4e-5f + fabsf(g) * 1.2e-7f;
+            s += g;
+            sabs += fabsf(g);
+        } else if (COST == kAckley) {
+            st.s1 = fmaf(x, x, st.s1);
+            st.s2 += cos2pi(x);
+        } else if (COST == kRosenbrock) {
+            if (k + 1 < n) {
+                const float g = rosen_term(x, xs[(k + 1) * B + t], e);
+                s += g;
+                sabs += g;
+            }
+        }
+    }
+    float F;
+    if (COST == kSchwefel) {
+        F = -s * inv_n;
+        eb = (e + sabs * 1.2e-7f * (float)n) * inv_n + fabsf(F) * 1.2e-7f;
+    } else if (COST == kRastrigin) {
+        F = 10.0f * (float)n + s;
+        eb = e + (sabs + 10.0f * n) * 1.2e-7f * (float)n;
+    } else if (COST == kAckley) {
+        st.a = ackley_value(st.s1, st.s2, inv_n);
+        F = st.a;
+        eb = 1e-4f + 2.4e-7f * (float)n * 50.0f;
+    } else {
+        F = s;
+        eb = e + sabs * 1.2e-7f * (float)n;
+    }
+    return F;
+}
+
+template <int COST>
+__device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
+                           float* xs, float* slo, float* shi, float* ssig, double* red, int* cand, int* ncand) {
+    const int t = threadIdx.x, B = blockDim.x, n = P.n;
+    const bool active = t < it.count;
+    const int64_t c = it.c0 + t;
+    const int64_t gc = P.chain_base + c;
+    const double T = A.T_tab[level];
+    const float Tf = (float)T;
+    const float sl = (float)A.s_tab[level];
+    const float inv_n = 1.0f / (float)n;
+
+    for (int k = t; k < n; k += B) { slo[k] = P.lo32[k]; shi[k] = P.hi32[k]; ssig[k] = P.sig32[k] * sl; }
+    if (level == 0) {
+        if (active) {
+            for (int k = 0; k < n; k += 4) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c, P.pid), A.ikey0, A.ikey1);
+                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (k + j < n) {
+                        const double lo = P.lo[k + j], hi = P.hi[k + j];
+                        float x = (float)(lo + u23d(ww[j]) * (hi - lo));
+                        x = fminf(fmaxf(x, P.lo32[k + j]), P.hi32[k + j]);
+                        xs[(k + j) * B + t] = x;
+                    }
+                }
+            }
+        }
+    } else {
+        for (int k = 0; k < n; ++k) xs[k * B + t] = P.x_best32[k];
+    }
+    __syncthreads();
+
+    double Fs = 0.0;
+    float es = 0.0f;
+    SepState st{0.0f, 0.0f, 0.0f};
+    if (level == 0) {
+        if (active) Fs = (double)start_value32<COST>(xs, B, n, t, inv_n, es, st);
+    } else {
+        Fs = P.scal[kFBest];
+        if (COST == kAckley) {
+            st.s1 = (float)P.scal[kS1];
+            st.s2 = (float)P.scal[kS2];
+            st.a = ackley_value(st.s1, st.s2, inv_n);
+            es = 1e-4f;
+        }
+    }
+
+    const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
+    uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
+    float dS = 0.0f, e = 0.0f;
+    uint32_t nacc = 0;
+    if (active) {
+        uint32_t bw = 0;
+        float* xcol = xs + t;
+        for (int s = 0; s < A.L; ++s) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), A.key0, A.key1);
+            const int d = coord_of(w.x, n);
+            const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
+            // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
+            const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
+            const float z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+            // Acceptance u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3  (tau > 0 covers dF <= 0).
+            const float tau = -Tf * 0.69314718055994531f * __log2f(u3);
+            const float xo = xcol[d * B];
+            const float lo = slo[d], hi = shi[d];
+            float xp = fmaf(ssig[d], z, xo);
+            if (A.boundary == 0) {
+                if (xp < lo) xp = 2.0f * lo - xp;
+                else if (xp > hi) xp = 2.0f * hi - xp;
+            }
+            xp = fminf(fmaxf(xp, lo), hi);
+
+            float dF, eb;
+            float s1p = 0.0f, s2p = 0.0f, ap = 0.0f;
+            if (COST == kSchwefel) {
+                const float ro = sqrt_approx(fabsf(xo)), rp = sqrt_approx(fabsf(xp));
+                const float ho = xo * sin_reduced(ro), hp = xp * sin_reduced(rp);
+                dF = (ho - hp) * inv_n;
+                eb = (fabsf(xo) * fmaf(ro, 9.6e-7f, 2.6e-6f) + fabsf(xp) * fmaf(rp, 9.6e-7f, 2.6e-6f)) * inv_n +
+                     fabsf(dF) * 2.4e-7f;
+            } else if (COST == kRastrigin) {
+                const float go = g_rastrigin(xo), gp = g_rastrigin(xp);
+                dF = gp - go;
+                eb = 4.8e-5f + (fabsf(go) + fabsf(gp) + fabsf(dF)) * 1.2e-7f;
+            } else if (COST == kAckley) {
+                s1p = st.s1 + (xp - xo) * (xp + xo);
+                s2p = st.s2 + (cos2pi(xp) - cos2pi(xo));
+                ap = ackley_value(s1p, s2p, inv_n);
+                dF = ap - st.a;
+                eb = 1e-4f + fabsf(dF) * 2.4e-7f;
+            } else {
+                eb = 0.0f;
+                float before = 0.0f, after = 0.0f;
+                if (d > 0) {
+                    const float xm = xcol[(d - 1) * B];
+                    before += rosen_term(xm, xo, eb);
+                    after += rosen_term(xm, xp, eb);
+                }
+                if (d + 1 < n) {
+                    const float xq = xcol[(d + 1) * B];
+                    before += rosen_term(xo, xq, eb);
+                    after += rosen_term(xp, xq, eb);
+                }
+                dF = after - before;
+                eb += (before + after + fabsf(dF)) * 1.2e-7f;
+            }
+            const bool acc = dF < tau;
+            if (acc) {
+                xcol[d * B] = xp;
+                dS += dF;
+                e += eb + fabsf(dS) * 1.2e-7f;
+                ++nacc;
+                if (COST == kAckley) { st.s1 = s1p; st.s2 = s2p; st.a = ap; }
+            }
+            if (tracing) {
+                bw |= (acc ? 1u : 0u) << (s & 31);
+                if ((s & 31) == 31 || s == A.L - 1) { mybits[s >> 5] = bw; bw = 0; }
+            }
+        }
+    }
+
+    // ---- candidates for the FP64 argmin -------------------------------------
+    const double Fa = Fs + (double)dS;
+    const double ec = (double)es + (double)e;
+    const bool finite = active && isfinite(Fa);
+    const double lo_c = finite ? Fa - ec : CUDART_INF;
+    const double hi_c = finite ? Fa + ec : CUDART_INF;
+    double bmin = block_min(hi_c, red);
+    if (t == 0) {
+        *ncand = 0;
+        double M = bmin;
+        if (bmin < CUDART_INF) {
+            const unsigned long long old = atomicMin(P.level_min, dbl_key(bmin));
+            M = fmin(M, key_dbl(old));
+        } else {
+            M = key_dbl(*(volatile unsigned long long*)P.level_min);
+        }
+        red[64] = M;
+    }
+    __syncthreads();
+    const double M = red[64];
+    const bool is_cand = finite && (tracing || lo_c <= M);
+    if (is_cand) cand[atomicAdd(ncand, 1)] = t;
+    else if (active) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+    __syncthreads();
+    const int nc = *ncand;
+    for (int j = 0; j < nc; ++j) {
+        const int tc = cand[j];
+        double p1, p2;
+        partials64<COST>(xs, B, n, tc, p1, p2);
+        block_sum2(p1, p2, red);
+        if (t == 0) A.F[P.chain_base + it.c0 + tc] = assemble64<COST>(n, p1, p2);
+        float* dst = A.X32 + P.x_base + it.c0 + tc;
+        for (int k = t; k < n; k += B) dst[(size_t)k * (size_t)P.chains] = xs[k * B + tc];
+    }
+    // accepted-move count of the tile
+    double a1 = (double)nacc, a2 = 0.0;
+    block_sum2(a1, a2, red);
+    if (t == 0) atomicAdd(P.accepts, (unsigned long long)a1);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) sweep_f32_kernel(SweepArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const WorkItem it = A.items[blockIdx.x];
+    const ProbDev P = A.probs[it.problem];
+    const int level = A.run->level;
+    const int n = P.n, B = blockDim.x;
+    double* red = reinterpret_cast<double*>(smem_raw);          // 72 doubles
+    int* cand = reinterpret_cast<int*>(smem_raw + 72 * sizeof(double));  // B ints
+    int* ncand = cand + kMaxBlock;
+    float* xs = reinterpret_cast<float*>(smem_raw + 72 * sizeof(double) + (kMaxBlock + 4) * sizeof(int));
+    float* slo = xs + (size_t)n * B;
+    float* shi = slo + n;
+    float* ssig = shi + n;
+    switch (P.cost) {
+    case kSchwefel: sweep_tile<kSchwefel>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kRastrigin: sweep_tile<kRastrigin>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kAckley: sweep_tile<kAckley>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kRosenbrock: sweep_tile<kRosenbrock>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    default: if (threadIdx.x == 0) A.run->status = 1; break;
+    }
+}
+
+}  // namespace
+
+size_t sweep_f32_smem_bytes(int n, int block) {
+    return 72 * sizeof(double) + (kMaxBlock + 4) * sizeof(int) + ((size_t)n * block + 3 * (size_t)n) * sizeof(float);
+}
+
+cudaError_t sweep_f32_set_smem(size_t bytes) {
+    // The limit only grows, so a later handle never invalidates an earlier handle's graphs.
+    static size_t current = 0;
+    if (bytes <= current) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(sweep_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) current = bytes;
+    return e;
+}
+
+cudaError_t launch_sweep_f32(const SweepArgs& a, int num_items, int block, size_t smem, cudaStream_t s) {
+    if (block > kMaxBlock) return cudaErrorInvalidValue;
+    sweep_f32_kernel<<<num_items, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sa

@@ -1,0 +1,262 @@
+"""Thin Python binding of the C ABI in include/sa.h (argument marshalling only).
+
+Every step of the annealing runs in the CUDA library ``libsa103.so``; this module
+only converts Python arguments to the C structs and back.  PyTorch supplies the
+CUDA stream (the current stream of the current device) and, for the
+kernel-level calls, device memory.  There is no CPU fallback: if the library is
+missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+SA_OK, SA_EINVAL, SA_ENOMEM, SA_ECUDA, SA_ETIMEOUT, SA_ENUMERIC, SA_ESTATE = range(7)
+COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "rot_rastrigin": 4, "rot_schwefel": 5}
+BOUNDARY = {"reflect": 0, "clip": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed_bf16": 2}
+
+
+class SAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_strerror(status)} (status {status})")
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_int32), ("Q", ctypes.c_void_p)]
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [("T0", ctypes.c_double), ("rho", ctypes.c_double), ("T_min", ctypes.c_double),
+                ("levels", ctypes.c_int32), ("sigma_frac", ctypes.c_double), ("boundary", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("surrogate", ctypes.c_int32), ("polish_k", ctypes.c_int32),
+                ("trace_levels", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("accepts", ctypes.c_int64), ("levels_done", ctypes.c_int32),
+                ("levels_total", ctypes.c_int32), ("f_level", ctypes.c_double), ("argmin", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("t_start_ns", ctypes.c_int64)]
+
+
+_lib = None
+
+# symbol -> (restype, argtypes)
+_V, _I32, _I64, _U32, _U64, _SZ, _D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                       ctypes.c_uint64, ctypes.c_size_t, ctypes.c_double)
+SIGNATURES = {
+    "sa_default_schedule": (None, [_V]),
+    "sa_levels_for": (_I32, [_D, _D, _D]),
+    "sa_create": (ctypes.c_int, [_V, _V, _I32, _I64, _I32, _V, _U64, _V, _V]),
+    "sa_run": (ctypes.c_int, [_V, _I32]),
+    "sa_reset": (ctypes.c_int, [_V]),
+    "sa_profile": (ctypes.c_int, [_V, _I32, _V, _V]),
+    "sa_best": (ctypes.c_int, [_V, _I32, _V, _V, _V]),
+    "sa_level_log": (ctypes.c_int, [_V, _I32, _V, _V, _V, _V, _I32, _V]),
+    "sa_trace": (ctypes.c_int, [_V, _I32, _V, _SZ]),
+    "sa_trace_states": (ctypes.c_int, [_V, _I32, _V, _V]),
+    "sa_checkpoint": (ctypes.c_int, [_V, _V, _V]),
+    "sa_restore": (ctypes.c_int, [_V, _V, _SZ]),
+    "sa_destroy": (None, [_V]),
+    "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
+    "sa_argmin_scratch_bytes": (_SZ, [_I64]),
+    "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsa103.so (raises if it is missing and build_if_missing is False)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library {_build.LIB} is not built; run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().sa_strerror(status).decode()
+    except Exception:  # the library itself failed to load
+        return "unknown"
+
+
+def _check(status: int, where: str):
+    if status != SA_OK:
+        raise SAError(status, where)
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Schedule:
+    T0: float = 100.0
+    rho: float = 0.9
+    T_min: float = 0.0
+    levels: int = 50
+    sigma_frac: float = 0.1
+    boundary: str = "reflect"
+    precision: str = "fp64"
+    trace_levels: int = 0
+
+    def _c(self) -> _Schedule:
+        return _Schedule(self.T0, self.rho, self.T_min, self.levels, self.sigma_frac, BOUNDARY[self.boundary],
+                         PRECISION[self.precision], 0, 0, self.trace_levels)
+
+
+def levels_for(T0: float, rho: float, T_min: float) -> int:
+    return load().sa_levels_for(T0, rho, T_min)
+
+
+class Handle:
+    """One solver (sa_create ... sa_destroy)."""
+
+    def __init__(self, ptr, n, chains, L, schedule):
+        self._ptr = ptr
+        self.n, self.chains, self.L, self.schedule = n, chains, L, schedule
+
+    def run(self, levels: int = -1):
+        _check(load().sa_run(self._ptr, levels), "sa_run")
+
+    def reset(self):
+        _check(load().sa_reset(self._ptr), "sa_reset")
+
+    def profile(self, levels: int = -1):
+        """Eager run with CUDA events: per-level (sweep_ms, level_ms)."""
+        n_levels = self.schedule.levels if self.schedule.levels > 0 else levels_for(
+            self.schedule.T0, self.schedule.rho, self.schedule.T_min)
+        m = n_levels if levels == -1 else levels
+        sw = np.zeros(m)
+        lv = np.zeros(m)
+        _check(load().sa_profile(self._ptr, levels, sw.ctypes.data, lv.ctypes.data), "sa_profile")
+        return sw, lv
+
+    def best(self, problem: int = 0):
+        x = np.zeros(self.n)
+        f = ctypes.c_double()
+        st = _Stats()
+        _check(load().sa_best(self._ptr, problem, x.ctypes.data, ctypes.byref(f), ctypes.byref(st)), "sa_best")
+        stats = {k: getattr(st, k) for k, _ in _Stats._fields_}
+        return x, f.value, stats
+
+    def level_log(self, problem: int = 0, cap: int = 1 << 20):
+        cap = min(cap, 1 << 20)
+        st = _Stats()
+        lib = load()
+        n_levels = self.schedule.levels if self.schedule.levels > 0 else levels_for(
+            self.schedule.T0, self.schedule.rho, self.schedule.T_min)
+        cap = min(cap, n_levels)
+        am = np.zeros(cap, np.int64)
+        fl = np.zeros(cap)
+        fi = np.zeros(cap)
+        tn = np.zeros(cap, np.int64)
+        cnt = ctypes.c_int32()
+        _check(lib.sa_level_log(self._ptr, problem, am.ctypes.data, fl.ctypes.data, fi.ctypes.data, tn.ctypes.data,
+                                cap, ctypes.byref(cnt)), "sa_level_log")
+        m = cnt.value
+        del st
+        return {"argmin": am[:m], "f_level": fl[:m], "f_inc": fi[:m], "t_ns": tn[:m]}
+
+    def trace(self, level: int, total_chains: int | None = None):
+        C = self.chains if total_chains is None else total_chains
+        words = (self.L + 31) // 32
+        bits = np.zeros((C, words), np.uint32)
+        _check(load().sa_trace(self._ptr, level, bits.ctypes.data, bits.size), "sa_trace")
+        return bits
+
+    def trace_states(self, level: int):
+        X = np.zeros((self.chains, self.n))
+        F = np.zeros(self.chains)
+        _check(load().sa_trace_states(self._ptr, level, X.ctypes.data, F.ctypes.data), "sa_trace_states")
+        return X, F
+
+    def checkpoint(self) -> bytes:
+        lib = load()
+        ln = ctypes.c_size_t()
+        _check(lib.sa_checkpoint(self._ptr, None, ctypes.byref(ln)), "sa_checkpoint")
+        buf = ctypes.create_string_buffer(ln.value)
+        _check(lib.sa_checkpoint(self._ptr, buf, ctypes.byref(ln)), "sa_checkpoint")
+        return buf.raw[:ln.value]
+
+    def restore(self, blob: bytes):
+        _check(load().sa_restore(self._ptr, blob, len(blob)), "sa_restore")
+
+    def destroy(self):
+        if self._ptr:
+            load().sa_destroy(self._ptr)
+            self._ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def create(cost, lo, hi, n, chains, L, schedule: Schedule | None = None, seed: int = 0, Q=None, stream=None) -> Handle:
+    """sa_create: one box-constrained problem (Eq. 1) with `chains` chains of L steps per level."""
+    lib = load()
+    schedule = schedule or Schedule()
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (n,)))
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    prob = _Problem(COSTS[cost] if isinstance(cost, str) else int(cost), None if Qa is None else Qa.ctypes.data)
+    box = _Box(lo.ctypes.data, hi.ctypes.data)
+    sch = schedule._c()
+    out = ctypes.c_void_p()
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check(lib.sa_create(ctypes.byref(prob), ctypes.byref(box), n, chains, L, ctypes.byref(sch), seed, s,
+                         ctypes.byref(out)), "sa_create")
+    return Handle(out, n, chains, L, schedule)
+
+
+def philox_fill(ctr, key, out) -> None:
+    """Philox4x32-10 blocks for counters (ctr0 + i, ctr1, ctr2, ctr3) into a uint32/int32 CUDA tensor of 4*count."""
+    count = out.numel() // 4
+    _check(load().sa_philox_fill(ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1], count,
+                                 ctypes.c_void_p(out.data_ptr()), _current_stream()), "sa_philox_fill")
+
+
+def argmin_f64(F):
+    """Lowest-index argmin of a float64 CUDA tensor; returns (index, value) as 0-d CUDA tensors."""
+    import torch
+    lib = load()
+    count = F.numel()
+    scratch = torch.empty(max(1, lib.sa_argmin_scratch_bytes(count)), dtype=torch.uint8, device=F.device)
+    idx = torch.empty((), dtype=torch.int64, device=F.device)
+    val = torch.empty((), dtype=torch.float64, device=F.device)
+    _check(lib.sa_argmin_f64(ctypes.c_void_p(F.data_ptr()), count, ctypes.c_void_p(idx.data_ptr()),
+                             ctypes.c_void_p(val.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
+                             _current_stream()), "sa_argmin_f64")
+    return idx, val
