@@ -217,6 +217,30 @@ size_t sa_argmin_scratch_bytes(int64_t count);
 sa_status sa_argmin_f64(const double* d_F, int64_t count, int64_t* d_index, double* d_value,
                         void* d_scratch, void* stream);
 
+/*
+ * sa_argmin_f64 for callers that cannot allocate device memory (the paper has
+ * no counterpart: this is a library convenience).  Some callers cannot hand
+ * over a scratch buffer -- code inside a host framework whose allocator owns
+ * the device's memory, latency-critical loops where cudaMalloc would
+ * synchronise the device, or code that must not run out of memory mid-run.
+ * This call allocates nothing: its scratch is a fixed array of
+ * SA_ARGMIN_STATIC_MAX_COUNT / 2048 * 16 bytes (1 MiB) inside the library,
+ * held by every GPU that loads the library until the process exits.
+ * Same inputs, outputs and result as sa_argmin_f64.
+ *   - count must be <= SA_ARGMIN_STATIC_MAX_COUNT; larger gives SA_EINVAL.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the array: calls whose kernels overlap on the GPU
+ *     (other streams, other host threads) race and may return wrong results.
+ *     Order such calls on one stream.
+ * Errors: SA_EINVAL on count < 1, count too large or a NULL pointer;
+ * SA_ECUDA if the address lookup or a launch fails.
+ */
+#define SA_ARGMIN_STATIC_MAX_COUNT ((int64_t)1 << 27)
+sa_status sa_argmin_f64_static(const double* d_F, int64_t count, int64_t* d_index, double* d_value,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ UNITS = {
     "sweep_f64.cu": ["-fmad=false"],
     "reduce.cu": [],
     "sa_api.cu": [],
+    "argmin_static.cu": [],
 }
 
 

@@ -72,7 +72,11 @@ SIGNATURES = {
     "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
+    "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
 }
+
+# Largest input of sa_argmin_f64_static (SA_ARGMIN_STATIC_MAX_COUNT in include/sa.h).
+ARGMIN_STATIC_MAX_COUNT = 1 << 27
 
 
 def library_path() -> str:
@@ -259,4 +263,16 @@ def argmin_f64(F):
     _check(lib.sa_argmin_f64(ctypes.c_void_p(F.data_ptr()), count, ctypes.c_void_p(idx.data_ptr()),
                              ctypes.c_void_p(val.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
                              _current_stream()), "sa_argmin_f64")
+    return idx, val
+
+
+def argmin_f64_static(F):
+    """Like argmin_f64 but without any scratch allocation: the library's fixed
+    1 MiB scratch is used instead (inputs up to ARGMIN_STATIC_MAX_COUNT values;
+    calls overlapping on the GPU race on that scratch)."""
+    import torch
+    idx = torch.empty((), dtype=torch.int64, device=F.device)
+    val = torch.empty((), dtype=torch.float64, device=F.device)
+    _check(load().sa_argmin_f64_static(ctypes.c_void_p(F.data_ptr()), F.numel(), ctypes.c_void_p(idx.data_ptr()),
+                                       ctypes.c_void_p(val.data_ptr()), _current_stream()), "sa_argmin_f64_static")
     return idx, val
