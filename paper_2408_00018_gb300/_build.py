@@ -22,6 +22,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-
 # contraction so that its rounding follows the written expressions.
 UNITS = {
     "sweep_f32.cu": [],
+    "sweep_f32w.cu": [],
     "sweep_f64.cu": ["-fmad=false"],
     "reduce.cu": [],
     "sa_api.cu": [],
@@ -58,7 +59,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_unit(item):
         src, extra = item
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        tuning = os.environ.get("SA_NVCC_FLAGS", "").split()  # e.g. -DSA_F32W_MIN_BLOCKS=2 for tuning runs
+        cmd = [cc, *ARCH, *COMMON, *extra, *tuning, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -55,6 +55,7 @@ struct sa_handle {
     std::vector<WorkItem> items;
     int block = 0;
     size_t smem = 0;
+    bool warp_mode = false;
     int max_argmin_blocks = 0;
     uint64_t fingerprint = 0;
     sa_status failed = SA_OK;
@@ -138,17 +139,65 @@ int pick_block(int precision, int n_max) {
     // possible.
     if (precision == SA_FP64) return 32;
     // ~64 KB of chain state per block: several blocks per SM, so that one
-    // block's end-of-level work overlaps the others' sweeps.
+    // block's end-of-level work overlaps the others' sweeps.  SA_BLOCK_BYTES
+    // overrides the per-block state budget for tuning runs.
     const int bytes = 4;
-    int b = 65536 / (bytes * n_max);
+    int budget = 65536;
+    if (const char* e = std::getenv("SA_BLOCK_BYTES")) {
+        const int v = std::atoi(e);
+        if (v >= 4096 && v <= 220 * 1024) budget = v;
+    }
+    int b = budget / (bytes * n_max);
     b = (b / 32) * 32;
     if (b > 256) b = 256;
     if (b < 32) b = 32;
     return b;
 }
 
+// Steps evaluated together per chain in the FP32 sweep: speculation pays when
+// two steps of a group rarely touch the same coordinate.  SA_UNROLL overrides
+// (1, 2 or 4) for tuning runs; the result is the same for every choice.
+int pick_unroll(int cost, int n) {
+    if (const char* e = std::getenv("SA_UNROLL")) {
+        const int u = std::atoi(e);
+        if (u == 1 || u == 2 || u == 4) return u;
+    }
+    if (cost == SA_ACKLEY) return 1;
+    if (n >= 64) return 4;
+    if (n >= 16) return 2;
+    return 1;
+}
+
+// FP32 sweep layout: one chain per warp (32 consecutive steps per group)
+// pays when a group rarely touches a coordinate twice and the cost has no
+// global running sums.  SA_WARP_MODE=0/1 overrides for tuning runs.
+bool pick_warp_mode(int cost, int n) {
+    if (const char* e = std::getenv("SA_WARP_MODE")) {
+        if (e[0] == '0') return false;
+        if (e[0] == '1') return cost == SA_SCHWEFEL || cost == SA_RASTRIGIN || cost == SA_ROSENBROCK;
+    }
+    // Measured on the n = 256 Schwefel workload: 2.11 ms per level against
+    // 2.05 ms for one chain per thread with two-step groups (the warp layout
+    // issues at ~60% but is limited by constant loads on the ADU pipe), so
+    // the thread layout stays the default.
+    (void)n;
+    return false;
+}
+
+// Bound on the FP32 error of one accepted step's dF over the whole box (the
+// per-step bounds of sa_device.cuh at their largest), used by the warp layout.
+float step_kappa(int cost, int n, const std::vector<float>& lo32, const std::vector<float>& hi32) {
+    double B = 0.0;
+    for (size_t k = 0; k < lo32.size(); ++k) B = std::fmax(B, std::fmax(std::fabs((double)lo32[k]), std::fabs((double)hi32[k])));
+    double kap = 0.0;
+    if (cost == SA_SCHWEFEL) kap = (2.0 * B * (std::sqrt(B) * 4.8e-7 + 2.6e-6) + 2.0 * B * 2.4e-7) / n;
+    else if (cost == SA_RASTRIGIN) kap = 4.8e-5 + 4.0 * (B * B + 10.0) * 1.2e-7;
+    return (float)(kap * 1.01);
+}
+
 cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
     if (h->precision == SA_FP64) return launch_sweep_f64(h->args, (int)h->items.size(), h->block, h->smem, s);
+    if (h->warp_mode) return launch_sweep_f32w(h->args, (int)h->items.size(), h->smem, s);
     return launch_sweep_f32(h->args, (int)h->items.size(), h->block, h->smem, s);
 }
 
@@ -215,17 +264,22 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     if (h->levels_total < 1) return SA_EINVAL;
 
     // launch shape
+    h->warp_mode = h->precision == SA_FP32;
+    for (int p = 0; p < P; ++p) h->warp_mode = h->warp_mode && pick_warp_mode(h->probs[p].cost, h->probs[p].n);
     h->block = pick_block(h->precision, n_max);
-    h->smem = h->precision == SA_FP64 ? sweep_f64_smem_bytes(n_max, h->block) : sweep_f32_smem_bytes(n_max, h->block);
+    if (h->warp_mode) h->smem = sweep_f32w_smem_bytes(n_max);
+    else h->smem = h->precision == SA_FP64 ? sweep_f64_smem_bytes(n_max, h->block) : sweep_f32_smem_bytes(n_max, h->block);
     int dev = 0, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if ((int)h->smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
-    if ((h->precision == SA_FP64 ? sweep_f64_set_smem(h->smem) : sweep_f32_set_smem(h->smem)) != cudaSuccess)
-        return SA_ECUDA;
+    cudaError_t se = h->warp_mode ? sweep_f32w_set_smem(h->smem)
+                                  : (h->precision == SA_FP64 ? sweep_f64_set_smem(h->smem) : sweep_f32_set_smem(h->smem));
+    if (se != cudaSuccess) return SA_ECUDA;
+    const int per_item = h->warp_mode ? sweep_f32w_chains_per_block() : h->block;
     for (int p = 0; p < P; ++p)
-        for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += h->block) {
-            const int64_t cnt = h->probs[p].chains - c0 < h->block ? h->probs[p].chains - c0 : h->block;
+        for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += per_item) {
+            const int64_t cnt = h->probs[p].chains - c0 < per_item ? h->probs[p].chains - c0 : per_item;
             h->items.push_back(WorkItem{p, (int32_t)cnt, c0});
         }
     h->max_argmin_blocks = 1;
@@ -256,13 +310,22 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         if (d.nblk_argmin > h->max_argmin_blocks) h->max_argmin_blocks = d.nblk_argmin;
         std::vector<double> sig(n);
         std::vector<float> lo32(n), hi32(n), sig32(n);
+        bool uniform = true;
         for (int k = 0; k < n; ++k) {
             sig[k] = h->sch.sigma_frac * (hp.hi[k] - hp.lo[k]);
             lo32[k] = round_up_f(hp.lo[k]);
             hi32[k] = round_down_f(hp.hi[k]);
             if (lo32[k] > hi32[k]) lo32[k] = hi32[k] = (float)hp.lo[k];
             sig32[k] = (float)sig[k];
+            uniform = uniform && hp.lo[k] == hp.lo[0] && hp.hi[k] == hp.hi[0];
         }
+        d.uniform = uniform ? 1 : 0;
+        d.lo_u = lo32[0];
+        d.hi_u = hi32[0];
+        d.sig_u = sig32[0];
+        d.unroll = pick_unroll(hp.cost, n);
+        d.warp_mode = h->warp_mode ? 1 : 0;
+        d.kappa = step_kappa(hp.cost, n, lo32, hi32);
         double *dlo, *dhi, *dsig, *xb64, *xinc, *scal, *pval, *lf, *lfi;
         float *dlo32, *dhi32, *dsig32, *xb32;
         unsigned long long *lmin, *acc;
@@ -334,6 +397,10 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     a.key1 = (uint32_t)(h->seed >> 32) ^ kTagSweep;
     a.ikey0 = (uint32_t)h->seed;
     a.ikey1 = (uint32_t)(h->seed >> 32) ^ kTagInit;
+    for (int r = 0; r < 10; ++r) {  // Philox key schedule k + r (W0, W1)
+        a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
 
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return SA_ECUDA;
     if ((st = capture_levels(h, 1, &h->g1))) return st;

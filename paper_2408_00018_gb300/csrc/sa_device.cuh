@@ -17,15 +17,60 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        // one 32x32 -> 64-bit product per multiplier gives both halves
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+    }
+    return c;
+}
+
+// The same generator for a fixed (c1, c2, c3) and a varying step counter c0:
+// the parts of rounds 1 and 2 that do not depend on c0 are computed once per
+// chain and level (philox_prep), the rest per step (philox_step).  The output
+// equals philox4x32_10(make_uint4(c0, c1, c2, c3), k0, k1) bit for bit.
+// rk: the key of every round, rk[2r] and rk[2r+1] for round r (the schedule
+// k + r (W0, W1) tabulated once on the host and passed as kernel parameters).
+struct PhiloxFixed {
+    uint32_t w0, w1;        // words 0, 1 after round 1 (independent of c0)
+    uint32_t hi2, lo2;      // round 2's product of word 0
+    uint32_t c3;
+};
+__device__ __forceinline__ PhiloxFixed philox_prep(uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* rk) {
+    PhiloxFixed f;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+    f.w0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk[0];
+    f.w1 = (uint32_t)p1;
+    const unsigned long long q0 = (unsigned long long)0xD2511F53u * f.w0;
+    f.hi2 = (uint32_t)(q0 >> 32);
+    f.lo2 = (uint32_t)q0;
+    f.c3 = c3;
+    return f;
+}
+__device__ __forceinline__ uint4 philox_step(uint32_t c0, const PhiloxFixed& f, const uint32_t* rk) {
+    // round 1 (words 2, 3 depend on c0)
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+    const uint32_t w2 = (uint32_t)(p0 >> 32) ^ f.c3 ^ rk[1];
+    const uint32_t w3 = (uint32_t)p0;
+    // round 2
+    const unsigned long long q1 = (unsigned long long)0xCD9E8D57u * w2;
+    uint4 c = make_uint4((uint32_t)(q1 >> 32) ^ f.w1 ^ rk[2], (uint32_t)q1, f.hi2 ^ w3 ^ rk[3], f.lo2);
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const unsigned long long a = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long b = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(b >> 32) ^ c.y ^ rk[2 * r], (uint32_t)b, (uint32_t)(a >> 32) ^ c.w ^ rk[2 * r + 1],
+                       (uint32_t)a);
     }
     return c;
 }
 
 // Uniform in (0,1) from the top 23 bits of a word; exact in FP32 and FP64.
-__device__ __forceinline__ float u23f(uint32_t w) { return __uint2float_rn(w >> 9) * 1.1920928955078125e-7f + 5.9604644775390625e-8f; }
+// FP32 form without an integer-to-float conversion: the top 23 bits become the
+// mantissa of a number in [1, 2); subtracting 1 - 2^-24 is exact and gives (k + 1/2) 2^-23.
+__device__ __forceinline__ float u23f(uint32_t w) {
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.999999940395355225f;
+}
 __device__ __forceinline__ double u23d(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 // Coordinate d = (w n) >> 32, uniform over [0, n).
 __device__ __forceinline__ int coord_of(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
@@ -55,8 +100,9 @@ __device__ __forceinline__ float cos2pi(float t) {
 // Each returns dF and a bound eb on |dF_computed - dF_exact| (exact = real
 // arithmetic at the same FP32 inputs).  Constants: unit roundoff u = 2^-24,
 // SFU sine/cosine absolute error <= 2^-21.41 on [-pi, pi] (taken as 2^-20),
-// approximate square root relative error taken as 2^-21; every bound carries
-// a further factor 2 of margin.
+// approximate square root relative error taken as 2^-22 (measured on this
+// GPU: <= 2^-23.25 over [1e-3, 500]); every bound carries a further factor 2
+// of margin.
 // ---------------------------------------------------------------------------
 struct SepState {   // per-chain running sums that some costs keep (Ackley)
     float s1, s2, a;  // sum x^2, sum cos(2 pi x), current Ackley value from (s1, s2)

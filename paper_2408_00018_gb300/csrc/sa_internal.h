@@ -26,6 +26,11 @@ struct ProbDev {
     int64_t x_base;       // offset (elements) of this problem's [n][chains] state block
     uint32_t pid;         // Philox counter word 3
     int32_t nblk_argmin;  // blocks of the argmin kernel for this problem
+    int32_t uniform;      // 1: every coordinate has the same [lo, hi] (scalars below are used)
+    int32_t unroll;       // steps evaluated together per chain in the FP32 sweep (1, 2 or 4)
+    int32_t warp_mode;    // FP32 sweep: 0 = one chain per thread, 1 = one chain per warp
+    float kappa;          // warp mode: bound on the FP32 error of one accepted step's dF
+    float lo_u, hi_u, sig_u;  // the uniform box and sigma_frac (hi - lo) in FP32
     const double* lo;     // [n]
     const double* hi;     // [n]
     const double* sig;    // [n] sigma_frac (hi - lo)
@@ -77,6 +82,7 @@ struct SweepArgs {
     int32_t boundary;      // 0 reflect then clip, 1 clip
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
+    uint32_t rk[20];       // sweep key of each Philox round r: (rk[2r], rk[2r+1]) (kernel-parameter operands)
 };
 
 // Launch wrappers (one per translation unit).
@@ -88,6 +94,10 @@ cudaError_t launch_level_end(RunDev* run, cudaStream_t s);
 cudaError_t launch_reset(ProbDev* probs, int num_probs, RunDev* run, cudaStream_t s);
 cudaError_t launch_stamp_start(RunDev* run, cudaStream_t s);
 cudaError_t sweep_f32_set_smem(size_t bytes);
+cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, size_t smem, cudaStream_t s);
+size_t sweep_f32w_smem_bytes(int n);
+cudaError_t sweep_f32w_set_smem(size_t bytes);
+int sweep_f32w_chains_per_block();
 cudaError_t sweep_f64_set_smem(size_t bytes);
 
 constexpr int kArgminThreads = 256;

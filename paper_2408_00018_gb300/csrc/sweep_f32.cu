@@ -8,14 +8,22 @@
 // O(1) difference of the terms that touch coordinate d instead of the
 // paper's full recompute of f(x1).
 //
+// Steps of one chain are independent except through the coordinates they
+// touch, so U consecutive steps are proposed and evaluated together (their
+// Philox blocks, transcendental functions and state loads interleave), then
+// committed in order; a step whose coordinate (or, for Rosenbrock, a
+// neighbour; for Ackley, any coordinate) was changed by an earlier accepted
+// step of the same group is re-evaluated from the current state before its
+// decision.  The decisions are exactly those of the one-step-at-a-time chain.
+//
 // At the end of the level every chain holds F_start + dS with a running
 // bound e on its FP32 error.  The block takes part in a device-wide
 // threshold M = min(F + e) (atomicMin on an ordered key); only chains with
 // F - e <= M can hold the level's minimum, and only those are re-evaluated
 // in FP64 and have their state written to global memory.  The FP64 argmin
 // over those candidates (reduce.cu) is therefore exact.
-#include <cmath>
 #include <cfloat>
+#include <cmath>
 #include <math_constants.h>
 
 #include "sa_device.cuh"
@@ -94,7 +102,7 @@ __device__ float start_value32(const float* xs, int B, int n, int t, float inv_n
         if (COST == kSchwefel) {
             const float r = sqrt_approx(fabsf(x));
             const float g = x * sin_reduced(r);
-            e += fabsf(x) * fmaf(r, 9.6e-7f, 2.6e-6f);
+            e += fabsf(x) * fmaf(r, 4.8e-7f, 2.6e-6f);
             s += g;
             sabs += fabsf(g);
         } else if (COST == kRastrigin) {
@@ -131,7 +139,104 @@ __device__ float start_value32(const float* xs, int B, int n, int t, float inv_n
     return F;
 }
 
+// One proposed step.  a, b: cost-specific values kept for the error bound
+// (Schwefel: sqrt|xo|, sqrt|xp|; Rastrigin: g(xo), g(xp); Rosenbrock: the
+// neighbours x_{d-1}, x_{d+1}; Ackley: the candidate sums).
+struct Step {
+    int d;
+    float z, tau, xo, xp, dF, a, b, ap;
+};
+
+struct Ctx {
+    float* xcol;       // this chain's column (stride B)
+    int B, n;
+    float inv_n;
+    float lo_u, hi_u, sig_u;         // uniform box (sig_u already scaled by sqrt(T/T0))
+    const float *slo, *shi, *ssig;   // per-coordinate box (ssig scaled)
+    int boundary;
+    float neg_T_ln2;  // -T ln 2: tau = -T ln u3 = neg_T_ln2 * log2(u3)
+    uint32_t level, chain, pid, key0, key1;
+};
+
+// Randomness of step s: coordinate, Gaussian deviate, acceptance threshold.
+__device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
+    const uint4 w = philox4x32_10(make_uint4(s, C.level, C.chain, C.pid), C.key0, C.key1);
+    p.d = coord_of(w.x, C.n);
+    const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
+    // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
+    const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
+    p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+    // u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3   (tau > 0, so dF <= 0 is always accepted)
+    p.tau = C.neg_T_ln2 * __log2f(u3);
+}
+
+// Move and energy difference of a proposed step from the chain's current state.
+template <int COST, bool UB>
+__device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step& p) {
+    const int d = p.d;
+    const float xo = C.xcol[d * C.B];
+    float lo, hi, sg;
+    if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
+    else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
+    float xp = fmaf(sg, p.z, xo);
+    if (C.boundary == 0) {
+        if (xp < lo) xp = 2.0f * lo - xp;
+        else if (xp > hi) xp = 2.0f * hi - xp;
+    }
+    xp = fminf(fmaxf(xp, lo), hi);
+    p.xo = xo;
+    p.xp = xp;
+    if (COST == kSchwefel) {
+        const float ro = sqrt_approx(fabsf(xo)), rp = sqrt_approx(fabsf(xp));
+        p.dF = (xo * sin_reduced(ro) - xp * sin_reduced(rp)) * C.inv_n;
+        p.a = ro;
+        p.b = rp;
+    } else if (COST == kRastrigin) {
+        const float go = g_rastrigin(xo), gp = g_rastrigin(xp);
+        p.dF = gp - go;
+        p.a = go;
+        p.b = gp;
+    } else if (COST == kAckley) {
+        p.a = st.s1 + (xp - xo) * (xp + xo);
+        p.b = st.s2 + (cos2pi(xp) - cos2pi(xo));
+        p.ap = ackley_value(p.a, p.b, C.inv_n);
+        p.dF = p.ap - st.a;
+    } else {
+        float dummy = 0.0f, before = 0.0f, after = 0.0f;
+        const float xm = d > 0 ? C.xcol[(d - 1) * C.B] : 0.0f;
+        const float xq = d + 1 < C.n ? C.xcol[(d + 1) * C.B] : 0.0f;
+        if (d > 0) { before += rosen_term(xm, xo, dummy); after += rosen_term(xm, xp, dummy); }
+        if (d + 1 < C.n) { before += rosen_term(xo, xq, dummy); after += rosen_term(xp, xq, dummy); }
+        p.dF = after - before;
+        p.a = xm;
+        p.b = xq;
+        p.ap = before + after;
+    }
+}
+
+// Bound on the FP32 error of an accepted step's dF (see sa_device.cuh for the constants).
 template <int COST>
+__device__ __forceinline__ float step_bound(const Ctx& C, const Step& p) {
+    if (COST == kSchwefel)
+        return (fabsf(p.xo) * fmaf(p.a, 4.8e-7f, 2.6e-6f) + fabsf(p.xp) * fmaf(p.b, 4.8e-7f, 2.6e-6f)) * C.inv_n +
+               fabsf(p.dF) * 2.4e-7f;
+    if (COST == kRastrigin) return 4.8e-5f + (fabsf(p.a) + fabsf(p.b) + fabsf(p.dF)) * 1.2e-7f;
+    if (COST == kAckley) return 1e-4f + fabsf(p.dF) * 2.4e-7f;
+    float eb = 0.0f;
+    if (p.d > 0) { rosen_term(p.a, p.xo, eb); rosen_term(p.a, p.xp, eb); }
+    if (p.d + 1 < C.n) { rosen_term(p.xo, p.b, eb); rosen_term(p.xp, p.b, eb); }
+    return eb + (p.ap + fabsf(p.dF)) * 1.2e-7f;
+}
+
+// Does an accepted earlier step k invalidate the speculative evaluation of step j?
+template <int COST>
+__device__ __forceinline__ bool conflicts(int dk, int dj) {
+    if (COST == kAckley) return true;                              // global sums changed
+    if (COST == kRosenbrock) return dk >= dj - 1 && dk <= dj + 1;  // neighbour terms
+    return dk == dj;
+}
+
+template <int COST, bool UB, int U>
 __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
                            float* xs, float* slo, float* shi, float* ssig, double* red, int* cand, int* ncand) {
     const int t = threadIdx.x, B = blockDim.x, n = P.n;
@@ -139,11 +244,11 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     const int64_t c = it.c0 + t;
     const int64_t gc = P.chain_base + c;
     const double T = A.T_tab[level];
-    const float Tf = (float)T;
     const float sl = (float)A.s_tab[level];
     const float inv_n = 1.0f / (float)n;
 
-    for (int k = t; k < n; k += B) { slo[k] = P.lo32[k]; shi[k] = P.hi32[k]; ssig[k] = P.sig32[k] * sl; }
+    if (!UB)
+        for (int k = t; k < n; k += B) { slo[k] = P.lo32[k]; shi[k] = P.hi32[k]; ssig[k] = P.sig32[k] * sl; }
     if (level == 0) {
         if (active) {
             for (int k = 0; k < n; k += 4) {
@@ -180,77 +285,71 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
         }
     }
 
+    Ctx C;
+    C.xcol = xs + t;
+    C.B = B;
+    C.n = n;
+    C.inv_n = inv_n;
+    C.lo_u = P.lo_u;
+    C.hi_u = P.hi_u;
+    C.sig_u = P.sig_u * sl;
+    C.slo = slo;
+    C.shi = shi;
+    C.ssig = ssig;
+    C.boundary = A.boundary;
+    C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
+    C.level = (uint32_t)level;
+    C.chain = (uint32_t)c;
+    C.pid = P.pid;
+    C.key0 = A.key0;
+    C.key1 = A.key1;
+
     const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     float dS = 0.0f, e = 0.0f;
     uint32_t nacc = 0;
     if (active) {
         uint32_t bw = 0;
-        float* xcol = xs + t;
-        for (int s = 0; s < A.L; ++s) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), A.key0, A.key1);
-            const int d = coord_of(w.x, n);
-            const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
-            // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
-            const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
-            const float z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
-            // Acceptance u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3  (tau > 0 covers dF <= 0).
-            const float tau = -Tf * 0.69314718055994531f * __log2f(u3);
-            const float xo = xcol[d * B];
-            const float lo = slo[d], hi = shi[d];
-            float xp = fmaf(ssig[d], z, xo);
-            if (A.boundary == 0) {
-                if (xp < lo) xp = 2.0f * lo - xp;
-                else if (xp > hi) xp = 2.0f * hi - xp;
-            }
-            xp = fminf(fmaxf(xp, lo), hi);
-
-            float dF, eb;
-            float s1p = 0.0f, s2p = 0.0f, ap = 0.0f;
-            if (COST == kSchwefel) {
-                const float ro = sqrt_approx(fabsf(xo)), rp = sqrt_approx(fabsf(xp));
-                const float ho = xo * sin_reduced(ro), hp = xp * sin_reduced(rp);
-                dF = (ho - hp) * inv_n;
-                eb = (fabsf(xo) * fmaf(ro, 9.6e-7f, 2.6e-6f) + fabsf(xp) * fmaf(rp, 9.6e-7f, 2.6e-6f)) * inv_n +
-                     fabsf(dF) * 2.4e-7f;
-            } else if (COST == kRastrigin) {
-                const float go = g_rastrigin(xo), gp = g_rastrigin(xp);
-                dF = gp - go;
-                eb = 4.8e-5f + (fabsf(go) + fabsf(gp) + fabsf(dF)) * 1.2e-7f;
-            } else if (COST == kAckley) {
-                s1p = st.s1 + (xp - xo) * (xp + xo);
-                s2p = st.s2 + (cos2pi(xp) - cos2pi(xo));
-                ap = ackley_value(s1p, s2p, inv_n);
-                dF = ap - st.a;
-                eb = 1e-4f + fabsf(dF) * 2.4e-7f;
-            } else {
-                eb = 0.0f;
-                float before = 0.0f, after = 0.0f;
-                if (d > 0) {
-                    const float xm = xcol[(d - 1) * B];
-                    before += rosen_term(xm, xo, eb);
-                    after += rosen_term(xm, xp, eb);
-                }
-                if (d + 1 < n) {
-                    const float xq = xcol[(d + 1) * B];
-                    before += rosen_term(xo, xq, eb);
-                    after += rosen_term(xp, xq, eb);
-                }
-                dF = after - before;
-                eb += (before + after + fabsf(dF)) * 1.2e-7f;
-            }
-            const bool acc = dF < tau;
+        const int L = A.L;
+        int s = 0;
+        auto commit = [&](Step& p, int sidx) -> bool {
+            const bool acc = p.dF < p.tau;
             if (acc) {
-                xcol[d * B] = xp;
-                dS += dF;
-                e += eb + fabsf(dS) * 1.2e-7f;
+                C.xcol[p.d * B] = p.xp;
+                dS += p.dF;
+                e += step_bound<COST>(C, p) + fabsf(dS) * 1.2e-7f;
                 ++nacc;
-                if (COST == kAckley) { st.s1 = s1p; st.s2 = s2p; st.a = ap; }
+                if (COST == kAckley) { st.s1 = p.a; st.s2 = p.b; st.a = p.ap; }
             }
             if (tracing) {
-                bw |= (acc ? 1u : 0u) << (s & 31);
-                if ((s & 31) == 31 || s == A.L - 1) { mybits[s >> 5] = bw; bw = 0; }
+                bw |= (acc ? 1u : 0u) << (sidx & 31);
+                if ((sidx & 31) == 31 || sidx == L - 1) { mybits[sidx >> 5] = bw; bw = 0; }
             }
+            return acc;
+        };
+        if (U > 1) {
+            for (; s + U <= L; s += U) {
+                Step p[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) propose(C, (uint32_t)(s + j), p[j]);
+#pragma unroll
+                for (int j = 0; j < U; ++j) evaluate<COST, UB>(C, st, p[j]);
+                bool acc[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    bool dirty = false;
+#pragma unroll
+                    for (int k = 0; k < j; ++k) dirty |= acc[k] && conflicts<COST>(p[k].d, p[j].d);
+                    if (dirty) evaluate<COST, UB>(C, st, p[j]);
+                    acc[j] = commit(p[j], s + j);
+                }
+            }
+        }
+        for (; s < L; ++s) {
+            Step p;
+            propose(C, (uint32_t)s, p);
+            evaluate<COST, UB>(C, st, p);
+            commit(p, s);
         }
     }
 
@@ -278,15 +377,29 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     if (is_cand) cand[atomicAdd(ncand, 1)] = t;
     else if (active) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
     __syncthreads();
+    // One warp per candidate: lane-strided partial sums in index order, then a
+    // fixed butterfly, so the FP64 value does not depend on the block shape
+    // (the chain-per-warp kernel evaluates candidates in the same order).
     const int nc = *ncand;
-    for (int j = 0; j < nc; ++j) {
+    const int lane = t & 31;
+    for (int j = t >> 5; j < nc; j += (B + 31) >> 5) {
         const int tc = cand[j];
-        double p1, p2;
-        partials64<COST>(xs, B, n, tc, p1, p2);
-        block_sum2(p1, p2, red);
-        if (t == 0) A.F[P.chain_base + it.c0 + tc] = assemble64<COST>(n, p1, p2);
+        double p1 = 0.0, p2 = 0.0;
+        for (int k = lane; k < n; k += 32) {
+            const double x = (double)xs[k * B + tc];
+            if (COST == kSchwefel) p1 += h64_schwefel(x);
+            else if (COST == kRastrigin) p1 += g64_rastrigin(x);
+            else if (COST == kAckley) { p1 += x * x; p2 += cos(6.283185307179586 * x); }
+            else if (k + 1 < n) p1 += rosen64(x, (double)xs[(k + 1) * B + tc]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+            p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+        }
+        if (lane == 0) A.F[P.chain_base + it.c0 + tc] = assemble64<COST>(n, p1, p2);
         float* dst = A.X32 + P.x_base + it.c0 + tc;
-        for (int k = t; k < n; k += B) dst[(size_t)k * (size_t)P.chains] = xs[k * B + tc];
+        for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xs[k * B + tc];
     }
     // accepted-move count of the tile
     double a1 = (double)nacc, a2 = 0.0;
@@ -294,13 +407,30 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     if (t == 0) atomicAdd(P.accepts, (unsigned long long)a1);
 }
 
-__global__ void __launch_bounds__(kMaxBlock) sweep_f32_kernel(SweepArgs A) {
+template <int COST>
+__device__ __forceinline__ void dispatch_u(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
+                                           float* xs, float* slo, float* shi, float* ssig, double* red, int* cand,
+                                           int* ncand) {
+    const bool ub = P.uniform != 0;
+    const int u = (COST == kAckley) ? 1 : P.unroll;
+    if (ub) {
+        if (u >= 4) sweep_tile<COST, true, 4>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else if (u == 2) sweep_tile<COST, true, 2>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else sweep_tile<COST, true, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+    } else {
+        if (u >= 4) sweep_tile<COST, false, 4>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else if (u == 2) sweep_tile<COST, false, 2>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else sweep_tile<COST, false, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+    }
+}
+
+__global__ void __launch_bounds__(kMaxBlock, 1) sweep_f32_kernel(SweepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const WorkItem it = A.items[blockIdx.x];
-    const ProbDev P = A.probs[it.problem];
+    const ProbDev& P = A.probs[it.problem];
     const int level = A.run->level;
     const int n = P.n, B = blockDim.x;
-    double* red = reinterpret_cast<double*>(smem_raw);          // 72 doubles
+    double* red = reinterpret_cast<double*>(smem_raw);                    // 72 doubles
     int* cand = reinterpret_cast<int*>(smem_raw + 72 * sizeof(double));  // B ints
     int* ncand = cand + kMaxBlock;
     float* xs = reinterpret_cast<float*>(smem_raw + 72 * sizeof(double) + (kMaxBlock + 4) * sizeof(int));
@@ -308,10 +438,10 @@ __global__ void __launch_bounds__(kMaxBlock) sweep_f32_kernel(SweepArgs A) {
     float* shi = slo + n;
     float* ssig = shi + n;
     switch (P.cost) {
-    case kSchwefel: sweep_tile<kSchwefel>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
-    case kRastrigin: sweep_tile<kRastrigin>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
-    case kAckley: sweep_tile<kAckley>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
-    case kRosenbrock: sweep_tile<kRosenbrock>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kSchwefel: dispatch_u<kSchwefel>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kRastrigin: dispatch_u<kRastrigin>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kAckley: dispatch_u<kAckley>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
+    case kRosenbrock: dispatch_u<kRosenbrock>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand); break;
     default: if (threadIdx.x == 0) A.run->status = 1; break;
     }
 }

@@ -230,3 +230,36 @@ def test_schwefel_n256_full_size_level0_sampled(sa):
     assert full >= 0.5 * len(sample)
     assert g["log"]["argmin"][0] == int(np.argmin(Fg))
     assert abs(Fg[g["log"]["argmin"][0]] - oracle.cost("schwefel", X[g["log"]["argmin"][0]])) < 1e-9
+
+
+@pytest.mark.parametrize("cost", ["schwefel", "rastrigin", "ackley", "rosenbrock"])
+@pytest.mark.parametrize("n", [3, 20, 100])
+def test_fp32_speculative_groups_are_exact(sa, cost, n, monkeypatch):
+    """Evaluating U steps of a chain together and committing them in order
+    gives exactly the one-step-at-a-time chain, for U = 1, 2, 4."""
+    C, L, K = 300, 97, 3   # L not a multiple of 4 or 32: partial groups at the end
+    results = []
+    # (chain-per-warp layout, steps per group of the chain-per-thread layout)
+    for wm, u in (("0", "1"), ("0", "2"), ("0", "4"), ("1", "1")):
+        monkeypatch.setenv("SA_WARP_MODE", wm)
+        monkeypatch.setenv("SA_UNROLL", u)
+        g = _run_gpu(sa, cost, n, C, L, K, 30.0, 0.8, 13, "fp32", trace_levels=K)
+        results.append((g["bits"], g["log"]["argmin"], g["f"], g["x"]))
+        g["h"].destroy()
+    for b, a, f, x in results[1:]:
+        for l in range(K):
+            assert np.array_equal(b[l], results[0][0][l])
+        assert np.array_equal(a, results[0][1]) and f == results[0][2] and np.array_equal(x, results[0][3])
+
+
+def test_fp32_nonuniform_box_matches_uniform_path(sa):
+    """A box whose bounds differ per coordinate takes the table path; with all
+    coordinates equal except an irrelevant last digit it must agree with the
+    uniform path where the boxes coincide."""
+    n, C, L, K = 40, 256, 64, 3
+    lo, hi = np.full(n, -5.12), np.full(n, 5.12)
+    a = _run_gpu(sa, "rastrigin", n, C, L, K, 10.0, 0.8, 2, "fp32", trace_levels=1, lo=lo, hi=hi)
+    lo2 = lo.copy()
+    lo2[-1] = np.nextafter(lo2[-1], -10)  # forces the per-coordinate path; same FP32 box after rounding up
+    b = _run_gpu(sa, "rastrigin", n, C, L, K, 10.0, 0.8, 2, "fp32", trace_levels=1, lo=lo2, hi=hi)
+    assert np.array_equal(a["bits"][0], b["bits"][0])
