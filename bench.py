@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of synchronous parallel simulated annealing on one GB300 (or N replicas).
 
-Workload (one "step" = one full annealing run): normalised Schwefel, n = 256,
-box [-500, 500]^n, 262144 chains, L = 1000 Metropolis steps per level,
+Default workload (one "step" = one full annealing run): normalised Schwefel,
+n = 256, box [-500, 500]^n, 262144 chains, L = 1000 Metropolis steps per level,
 200 levels, T0 = 100, rho = 0.95, sigma = 0.1 width sqrt(T/T0), FP32 state with
-FP64 argmin, seed 0 -- 5.24e10 Metropolis steps per run.
+FP64 argmin, seed 0 -- 5.24e10 Metropolis steps per run.  ``--workload`` selects
+the other workloads (measurement lines for the other rows; the default line is
+the headline).
 
 Prints one JSON line: Metropolis steps/s (device-timed, inputs resident), the
 same through the public C ABI with host buffers (e2e), time-to-target, the
@@ -28,11 +30,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Metropolis steps/s and time-to-target (best f within 1e-6 rel) on 1 GB300"
 UNIT = "Metropolis steps/s"
-WORKLOAD = "schwefel_n256_c262144_L1000_K200_fp32"
-MUFU_PER_STEP = 6          # algorithmic SFU ops per Metropolis step
 MUFU_PER_CLK_SM = 16
-NUM_SMS_NOMINAL = 152
-SWEEP_SOURCES = ["sweep_f32.cu", "sa_device.cuh", "sa_internal.h"]
+# Algorithmic SFU operations per Metropolis step, per cost: the proposal needs
+# log2 and sqrt (Box-Muller radius) and cos (angle); the acceptance test one
+# log2 (tau = -T ln u3); the energy difference the transcendental terms of the
+# new coordinate value only (the old one's term can be kept): Schwefel sqrt +
+# sin, Rastrigin cos, Ackley cos + sqrt + 2 exp, Rosenbrock none.
+SFU_PER_STEP = {"schwefel": 6, "rastrigin": 5, "ackley": 8, "rosenbrock": 4}
+SWEEP_SOURCES = ["sweep_f32.cu", "sweep_f32w.cu", "sa_device.cuh", "sa_internal.h"]
+WORKLOADS = ("schwefel_n256", "schwefel_n2", "batched")
 
 
 def parse():
@@ -41,17 +47,67 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=WORKLOADS, default="schwefel_n256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--levels", type=int, default=0, help="override the level count (testing only)")
+    ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling runs only)")
     return ap.parse_args()
 
 
-def workload(levels_override=0):
-    from paper_2408_00018_gb300 import inputs
-    cfg = dict(inputs.SCHWEFEL_N256_FP32)
-    if levels_override:
-        cfg["levels"] = levels_override
-    return cfg
+# ------------------------------------------------------------------ workloads
+class Workload:
+    """One workload: how to build its handle and what one run amounts to."""
+
+    def __init__(self, name, levels_override=0):
+        from paper_2408_00018_gb300 import inputs
+        self.name = name
+        if name in ("schwefel_n256", "schwefel_n2"):
+            cfg = dict(inputs.SCHWEFEL_N256_FP32 if name == "schwefel_n256" else inputs.SCHWEFEL_N2_FP64)
+            if levels_override:
+                cfg["levels"] = levels_override
+            lo, hi = inputs.box(cfg["cost"], cfg["n"])
+            self.problems = [{"cost": cfg["cost"], "n": cfg["n"], "chains": cfg["chains"], "lo": lo, "hi": hi}]
+            self.L, self.K, self.T0, self.rho = cfg["L"], cfg["levels"], cfg["T0"], cfg["rho"]
+            self.sigma_frac, self.precision, self.seed = cfg["sigma_frac"], cfg["precision"], cfg["seed"]
+            self.batch = False
+            self.tag = (f"schwefel_n{cfg['n']}_c{cfg['chains']}_L{cfg['L']}_K{cfg['levels']}_{cfg['precision']}")
+        else:  # 512 independent problems of uneven n and chain count
+            self.problems = inputs.batch_problems(count=512, seed=0)
+            self.L, self.K = 500, levels_override or 100
+            self.T0, self.rho, self.sigma_frac, self.precision, self.seed = 100.0, 0.95, 0.1, "fp32", 0
+            self.batch = True
+            self.tag = f"batched512_L500_K{self.K}_fp32_autotuned"
+        self.steps_per_run = sum(p["chains"] for p in self.problems) * self.L * self.K
+        self.sfu_per_level = sum(p["chains"] * self.L * SFU_PER_STEP[p["cost"]] for p in self.problems)
+        self.f_star = [inputs.F_STAR[p["cost"]] for p in self.problems]
+
+    def schedule(self, sa):
+        return sa.Schedule(T0=self.T0, rho=self.rho, levels=self.K, sigma_frac=self.sigma_frac,
+                           precision=self.precision)
+
+    def create(self, sa, tune=True):
+        if self.batch:
+            h = sa.create_batch(self.problems, self.L, self.schedule(sa), seed=self.seed)
+            if tune:
+                h.autotune()
+            return h
+        p = self.problems[0]
+        return sa.create(p["cost"], p["lo"], p["hi"], p["n"], p["chains"], self.L, self.schedule(sa), seed=self.seed)
+
+    def launches_per_run(self, h):
+        groups = len(h.describe())
+        return 1 + self.K * (groups + 2)  # start stamp + per level (group sweeps, argmin/restart, level advance)
+
+    def config(self):
+        c = {"workload": self.tag, "L": self.L, "levels": self.K, "T0": self.T0, "rho": self.rho, "seed": self.seed,
+             "steps_per_run": self.steps_per_run, "argmin": "f64"}
+        if self.batch:
+            c.update({"problems": len(self.problems), "chains_total": sum(p["chains"] for p in self.problems),
+                      "n_range": [min(p["n"] for p in self.problems), max(p["n"] for p in self.problems)],
+                      "costs": "uniform over schwefel/rastrigin/ackley/rosenbrock"})
+        else:
+            p = self.problems[0]
+            c.update({"cost": p["cost"], "n": p["n"], "chains": p["chains"]})
+        return c
 
 
 # ------------------------------------------------------------------ clocks
@@ -116,46 +172,76 @@ def sweep_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile():
+def traffic_from_profile(workload):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on this source."""
-    p = os.path.join(ROOT, "profiles", "sweep_f32_traffic.json")
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     try:
-        d = json.load(open(p))
+        d = json.load(open(p)).get(workload)
     except Exception:
         return None
-    if d.get("src_sha") != sweep_source_hash():
+    if not d or d.get("src_sha") != sweep_source_hash():
         return None
     return d.get("dram_bytes_per_launch")
 
 
-def time_to_target(log, t_start_ns, f_star):
-    tol = 1e-6 * max(1.0, abs(f_star))
-    for l, f in enumerate(log["f_inc"]):
-        if abs(f - f_star) <= tol:
-            return {"reached": True, "level": l, "seconds": (int(log["t_ns"][l]) - int(t_start_ns)) * 1e-9}
-    f_last = float(log["f_inc"][-1]) if len(log["f_inc"]) else None
-    return {"reached": False, "level": None, "seconds": None, "final_f": f_last,
-            "final_rel_gap": None if f_last is None else abs(f_last - f_star) / abs(f_star)}
+def time_to_target(logs, t_start_ns, f_stars):
+    """Per problem: first level whose incumbent is within 1e-6 max(1, |f*|) of f*."""
+    reached, last_t, gaps = 0, 0.0, []
+    for log, fs in zip(logs, f_stars):
+        tol = 1e-6 * max(1.0, abs(fs))
+        hit = [l for l, f in enumerate(log["f_inc"]) if abs(f - fs) <= tol]
+        if hit:
+            reached += 1
+            last_t = max(last_t, (int(log["t_ns"][hit[0]]) - int(t_start_ns)) * 1e-9)
+        else:
+            f_last = float(log["f_inc"][-1])
+            gaps.append(abs(f_last - fs) / max(1.0, abs(fs)))
+    out = {"reached": reached == len(f_stars), "problems_reached": reached, "problems": len(f_stars),
+           "seconds": last_t if reached == len(f_stars) else None}
+    if gaps:
+        out["worst_final_rel_gap"] = max(gaps)
+        out["median_final_rel_gap"] = statistics.median(gaps)
+    if len(f_stars) == 1 and not gaps:
+        out["level"] = next(l for l, f in enumerate(logs[0]["f_inc"])
+                            if abs(f - f_stars[0]) <= 1e-6 * max(1.0, abs(f_stars[0])))
+    return out
 
 
-def oracle_sample(cfg, chains, levels, threads):
-    """The FP64 CPU oracle, as it stands, on levels 0..levels-1 of `chains` chains of the workload."""
+def oracle_sample(w, budget_steps, threads):
+    """The FP64 CPU oracle, as it stands, on level 0 (and 1) of a bounded part of the workload."""
     import oracle
-    from paper_2408_00018_gb300 import inputs
-    lo, hi = inputs.box(cfg["cost"], cfg["n"])
-    p = oracle.Problem(cfg["cost"], cfg["n"], lo, hi, chains=chains, L=cfg["L"], T0=cfg["T0"], rho=cfg["rho"],
-                       sigma_frac=cfg["sigma_frac"], seed=cfg["seed"], mode=1, threads=threads)
-    t = time.perf_counter()
-    p.run(levels)
-    dt = time.perf_counter() - t
-    return chains * cfg["L"] * levels / dt, dt
+    done, t0 = 0, time.perf_counter()
+    descr = []
+    mode = 0 if w.precision == "fp64" else 1
+    for p_idx, p in enumerate(w.problems):
+        levels = 1 if w.batch else (w.K if w.steps_per_run <= budget_steps else 2)
+        chains = p["chains"]
+        steps = chains * w.L * levels
+        if done + steps > budget_steps:
+            chains = max(1, (budget_steps - done) // (w.L * levels))
+            steps = chains * w.L * levels
+        op = oracle.Problem(p["cost"], p["n"], p["lo"], p["hi"], chains=chains, L=w.L, T0=w.T0, rho=w.rho,
+                            sigma_frac=w.sigma_frac, seed=w.seed, problem=p_idx, mode=mode, threads=threads)
+        op.run(levels)
+        done += steps
+        descr.append(p_idx)
+        if done >= budget_steps:
+            break
+    dt = time.perf_counter() - t0
+    if w.batch:
+        what = f"level 0 of the first {len(descr)} of {len(w.problems)} problems, {done:.3g} steps"
+    elif levels == w.K:
+        what = f"the full run ({w.K} levels of {w.problems[0]['chains']} chains x L={w.L}), {done:.3g} steps"
+    else:
+        what = f"levels 0-1 of {w.problems[0]['chains'] if done >= w.problems[0]['chains'] * w.L * 2 else 'part of the'} chains x L={w.L}, {done:.3g} steps"
+    return done / dt, dt, what + f" (FP64 oracle, {dt:.1f} s)"
 
 
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
-    from paper_2408_00018_gb300 import _build, inputs, sa
+    from paper_2408_00018_gb300 import _build, sa
 
     torch.cuda.set_device(local_rank)
     if rank == 0 or world == 1:
@@ -163,14 +249,9 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     sa.load()
-    cfg = workload(args.levels)
-    n, C, L, K = cfg["n"], cfg["chains"], cfg["L"], cfg["levels"]
-    lo, hi = inputs.box(cfg["cost"], n)
-    sch = sa.Schedule(T0=cfg["T0"], rho=cfg["rho"], levels=K, sigma_frac=cfg["sigma_frac"], precision=cfg["precision"])
-    steps_per_run = C * L * K
-    launches_per_run = 1 + 3 * K   # start stamp + (sweep, argmin/restart, level advance) per level
-
-    h = sa.create(cfg["cost"], lo, hi, n, C, L, sch, seed=cfg["seed"])
+    w = Workload(args.workload, args.levels)
+    h = w.create(sa)
+    groups = h.describe()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     for _ in range(args.warmup):
         h.reset()
@@ -198,30 +279,34 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    x, f, st = h.best()
-    log = h.level_log()
-    ttt = time_to_target(log, st["t_start_ns"], inputs.SCHWEFEL_F_STAR)
+    bests = [h.best(p) for p in range(len(w.problems))]
+    logs = [h.level_log(p) for p in range(len(w.problems))]
+    ttt = time_to_target(logs, bests[0][2]["t_start_ns"], w.f_star)
 
     t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(t_max.item())
-    value = steps_per_run * args.steps * world / (ms_max * 1e-3)
+    value = w.steps_per_run * args.steps * world / (ms_max * 1e-3)
 
     # ---- live per-kernel timing of the sweep (eager launches, CUDA events on the same stream)
     h.reset()
     sweep_ms, level_ms = h.profile()
-    sweep_avg = float(np.mean(sweep_ms))
+    launches = w.launches_per_run(h)
     h.destroy()
+    sweep_avg = float(np.mean(sweep_ms))
     sm_mhz = clocks["sm_mhz"] or 2070.0
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    achieved = MUFU_PER_STEP * C * L / (sweep_avg * 1e-3) / 1e12
+    achieved = w.sfu_per_level / (sweep_avg * 1e-3) / 1e12
     peak = MUFU_PER_CLK_SM * sms * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "TMUFU-op/s (SFU: 6 algorithmic ops per Metropolis step)", "frac": round(achieved / peak, 4),
-                "traffic": traffic_from_profile(), "kernel": "sweep_f32_kernel",
-                "launch_ms": round(sweep_avg, 4), "sweep_share_of_level": round(float(np.sum(sweep_ms) / np.sum(level_ms)), 4),
-                "peak_basis": f"16 MUFU/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (median sampled SM clock)"}
+                "unit": "TSFU-op/s (algorithmic SFU ops per Metropolis step: " +
+                        ", ".join(f"{k} {v}" for k, v in SFU_PER_STEP.items()) + ")",
+                "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(args.workload),
+                "kernel": "sweep (" + ", ".join(g["kind"] for g in groups) + ")",
+                "launch_ms": round(sweep_avg, 4),
+                "sweep_share_of_level": round(float(np.sum(sweep_ms) / np.sum(level_ms)), 4),
+                "peak_basis": f"16 SFU ops/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (median sampled SM clock)"}
 
     # ---- end to end through the public API with host buffers, every step
     e2e_times = []
@@ -229,9 +314,10 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        hh = sa.create(cfg["cost"], lo, hi, n, C, L, sch, seed=cfg["seed"])
+        hh = w.create(sa, tune=False)
         hh.run()
-        xx, ff, stt = hh.best()
+        for p in range(len(w.problems)):
+            xx, ff, stt = hh.best(p)
         hh.destroy()
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t)
@@ -239,27 +325,27 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(e2e_s, op=torch.distributed.ReduceOp.MAX)
-    e2e = {"value": steps_per_run * args.steps * world / float(e2e_s.item()), "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    e2e = {"value": w.steps_per_run * args.steps * world / float(e2e_s.item()), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "note": "create (H2D of boxes and descriptors) + run + best (D2H) + destroy per step"
+                   + ("; default launch shapes (no autotune)" if w.batch else "")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        chains_s, levels_s = 262144, 2
-        v, dt = oracle_sample(cfg, chains_s, levels_s, threads)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"levels 0-1 of the workload, all {chains_s} chains x L={L} (FP64 oracle, {dt:.1f} s)"}
+        v, dt, what = oracle_sample(w, 5.3e8 if not w.batch else 3e8, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": what}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "cost": cfg["cost"], "n": n, "chains": C, "L": L, "levels": K,
-                          "T0": cfg["T0"], "rho": cfg["rho"], "seed": cfg["seed"],
-                          "steps_per_run": steps_per_run, "parallelism": f"replicas{world}",
-                          "l2": "flushed between runs (256 MiB write)", "argmin": "f64"},
-               "time_to_target": ttt, "best_f": f, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clocks, "gpu_launches": launches_per_run * args.steps}
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f32",
+               "data": "synthetic",
+               "config": dict(w.config(), parallelism=f"replicas{world}", l2="flushed between runs (256 MiB write)",
+                              launch_groups=groups),
+               "time_to_target": ttt, "best_f": bests[0][1] if len(bests) == 1 else None,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": launches * args.steps}
         print(json.dumps(out), flush=True)
 
 
@@ -267,23 +353,23 @@ def run_ours(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cfg = workload(args.levels)
+    w = Workload(args.workload, args.levels)
     threads = os.cpu_count() or 1
-    chains_s, levels_s = 32768, 2
+    budget = 6.5e7
     for _ in range(args.warmup):
-        oracle_sample(cfg, chains_s, levels_s, threads)
-    total_steps, total_s = 0, 0.0
+        oracle_sample(w, budget, threads)
+    total_steps, total_s, what = 0, 0.0, ""
     for _ in range(args.steps):
-        v, dt = oracle_sample(cfg, chains_s, levels_s, threads)
-        total_steps += chains_s * cfg["L"] * levels_s
+        v, dt, what = oracle_sample(w, budget, threads)
+        total_steps += v * dt
         total_s += dt
     value = total_steps / total_s
-    sample = f"each step: levels 0-1 of {chains_s} of the workload's chains x L={cfg['L']} (FP64 oracle)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "parallelism": "cpu"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "config": dict(w.config(), parallelism="cpu"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": "each step: " + what},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -120,6 +120,39 @@ sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int
                     sa_handle** out);
 
 /*
+ * Create one solver for num_problems independent problems that share L and
+ * the schedule (each problem p has its own cost, box, n[p] and chains[p]).
+ * Every level runs all problems' sweeps in one graph launch (problems are
+ * grouped by dimension; the groups' kernels run concurrently) followed by one
+ * argmin/restart launch over all problems.  Problem p draws its randomness
+ * from Philox counter word 3 = p, so its result equals a single-problem run
+ * with that problem index.  Arguments are arrays of length num_problems with
+ * the meaning and checks of sa_create.  Errors: as sa_create, plus SA_EINVAL
+ * if num_problems < 1.
+ */
+sa_status sa_create_batch(const sa_problem* problems, const sa_box* boxes, const int32_t* n,
+                          const int64_t* chains, int32_t num_problems, int32_t L,
+                          const sa_schedule* schedule, uint64_t seed, void* stream,
+                          sa_handle** out);
+
+/*
+ * Pick the block shape (chains per block) and the number of steps evaluated
+ * together per chain for each dimension group by timing the level-0 sweep of
+ * that group with each candidate (results do not depend on the choice).
+ * Leaves the handle rewound to level 0 and re-captures its graphs; *ms_out
+ * (may be NULL) receives the sum of the chosen level-0 sweep times.
+ * Synchronises.  Errors: SA_ESTATE on a failed handle, SA_ECUDA.
+ */
+sa_status sa_autotune(sa_handle* h, double* ms_out);
+
+/*
+ * Describe the launch groups of a handle as a JSON array (kind, problems,
+ * n_max, block, smem, unroll, work items) into buf (NUL-terminated, truncated
+ * to len).  Returns the full length of the description, or -1 on NULL h.
+ */
+int32_t sa_describe(const sa_handle* h, char* buf, size_t len);
+
+/*
  * Run up to `levels` further temperature levels (-1 = all remaining).  Each
  * level is: Metropolis sweep of every chain (Listing 4), reduction to the
  * lowest-f chain with lowest-index tie-break, restart and cooling (Listing 3).

@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -37,6 +39,23 @@ struct HostProb {
     ProbDev dev;  // with device pointers
 };
 
+// Problems whose sweep runs as one kernel launch with one block shape.  A
+// batch of problems of uneven dimension is split by n into groups; within a
+// level the groups' sweeps run concurrently on forked streams.
+enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2 };
+struct Group {
+    int kind = kSweepF32;
+    int n_max = 1;
+    int block = 32;        // threads per block
+    size_t smem = 0;       // dynamic shared memory per block
+    std::vector<int> probs;
+    std::vector<WorkItem> items;
+    WorkItem* d_items = nullptr;  // capacity: items at the smallest block shape
+    size_t items_cap = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
 }  // namespace
 
 struct sa_handle {
@@ -52,10 +71,8 @@ struct sa_handle {
     int64_t total_chains = 0;
     int64_t total_x = 0;
     std::vector<HostProb> probs;
-    std::vector<WorkItem> items;
-    int block = 0;
-    size_t smem = 0;
-    bool warp_mode = false;
+    std::vector<Group> groups;
+    cudaEvent_t fork_ev = nullptr;
     int max_argmin_blocks = 0;
     uint64_t fingerprint = 0;
     sa_status failed = SA_OK;
@@ -63,7 +80,7 @@ struct sa_handle {
     // device
     std::vector<void*> allocs;
     ProbDev* d_probs = nullptr;
-    WorkItem* d_items = nullptr;
+    std::vector<ProbDev> pd;  // host copy of the descriptors
     RunDev* d_run = nullptr;
     double* d_T = nullptr;
     double* d_s = nullptr;
@@ -195,11 +212,64 @@ float step_kappa(int cost, int n, const std::vector<float>& lo32, const std::vec
     return (float)(kap * 1.01);
 }
 
-cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
-    if (h->precision == SA_FP64) return launch_sweep_f64(h->args, (int)h->items.size(), h->block, h->smem, s);
-    if (h->warp_mode) return launch_sweep_f32w(h->args, (int)h->items.size(), h->smem, s);
-    return launch_sweep_f32(h->args, (int)h->items.size(), h->block, h->smem, s);
+cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
+    SweepArgs a = h->args;
+    a.items = g.d_items;
+    const int num = (int)g.items.size();
+    if (num == 0) return cudaSuccess;
+    if (g.kind == kSweepF64) return launch_sweep_f64(a, num, g.block, g.smem, s);
+    if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.smem, s);
+    return launch_sweep_f32(a, num, g.block, g.smem, s);
 }
+
+// The sweep of one level: one launch per group; several groups run
+// concurrently on forked streams (also inside a captured graph).
+cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
+    if (h->groups.size() == 1) return launch_group(h, h->groups[0], s);
+    cudaError_t e = cudaEventRecord(h->fork_ev, s);
+    for (Group& g : h->groups) {
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, h->fork_ev, 0);
+        if (e == cudaSuccess) e = launch_group(h, g, g.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
+    }
+    for (Group& g : h->groups)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.done, 0);
+    return e;
+}
+
+// Work items of a group for its current block shape (tiles of one problem's
+// chains), largest problems first; uploaded on the handle's stream.
+sa_status set_group_items(sa_handle* h, Group& g) {
+    const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block() : g.block;
+    std::vector<int> order = g.probs;
+    std::sort(order.begin(), order.end(), [h](int a, int b) { return h->probs[a].chains > h->probs[b].chains; });
+    g.items.clear();
+    for (int p : order)
+        for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += per_item) {
+            const int64_t cnt = h->probs[p].chains - c0 < per_item ? h->probs[p].chains - c0 : per_item;
+            g.items.push_back(WorkItem{p, (int32_t)cnt, c0});
+        }
+    if (g.items.size() > g.items_cap) return SA_EINVAL;
+    if (g.items.empty()) return SA_OK;
+    h->h2d_bytes += (int64_t)(g.items.size() * sizeof(WorkItem));
+    return cudaMemcpyAsync(g.d_items, g.items.data(), g.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                           h->stream) == cudaSuccess ? SA_OK : SA_ECUDA;
+}
+
+size_t group_smem(const Group& g) {
+    if (g.kind == kSweepF32Warp) return sweep_f32w_smem_bytes(g.n_max);
+    if (g.kind == kSweepF64) return sweep_f64_smem_bytes(g.n_max, g.block);
+    return sweep_f32_smem_bytes(g.n_max, g.block);
+}
+
+cudaError_t group_set_smem(const Group& g) {
+    if (g.kind == kSweepF32Warp) return sweep_f32w_set_smem(g.smem);
+    if (g.kind == kSweepF64) return sweep_f64_set_smem(g.smem);
+    return sweep_f32_set_smem(g.smem);
+}
+
+// FP32 dimension buckets: problems with n in (bound[i-1], bound[i]] share a group.
+constexpr int kBucketBounds[] = {16, 32, 64, 128, 256, 512, 1 << 30};
 
 cudaError_t launch_level_tail(sa_handle* h, cudaStream_t s) {
     cudaError_t e = launch_argmin_restart(h->args, h->d_probs, (int)h->probs.size(), h->max_argmin_blocks,
@@ -263,29 +333,50 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     h->levels_total = h->sch.levels > 0 ? h->sch.levels : sa_levels_for(h->sch.T0, h->sch.rho, h->sch.T_min);
     if (h->levels_total < 1) return SA_EINVAL;
 
-    // launch shape
-    h->warp_mode = h->precision == SA_FP32;
-    for (int p = 0; p < P; ++p) h->warp_mode = h->warp_mode && pick_warp_mode(h->probs[p].cost, h->probs[p].n);
-    h->block = pick_block(h->precision, n_max);
-    if (h->warp_mode) h->smem = sweep_f32w_smem_bytes(n_max);
-    else h->smem = h->precision == SA_FP64 ? sweep_f64_smem_bytes(n_max, h->block) : sweep_f32_smem_bytes(n_max, h->block);
+    // launch groups: FP64 -> one group; FP32 -> one group per dimension bucket
+    (void)n_max;
+    if (h->precision == SA_FP64) {
+        h->groups.resize(1);
+        h->groups[0].kind = kSweepF64;
+        for (int p = 0; p < P; ++p) h->groups[0].probs.push_back(p);
+    } else {
+        const int nb = (int)(sizeof(kBucketBounds) / sizeof(int));
+        std::vector<Group> b(nb);
+        for (int p = 0; p < P; ++p) {
+            int i = 0;
+            while (h->probs[p].n > kBucketBounds[i]) ++i;
+            b[i].probs.push_back(p);
+        }
+        for (Group& g : b)
+            if (!g.probs.empty()) h->groups.push_back(g);
+        for (Group& g : h->groups) {
+            bool warp = true;
+            for (int p : g.probs) warp = warp && pick_warp_mode(h->probs[p].cost, h->probs[p].n);
+            g.kind = warp ? kSweepF32Warp : kSweepF32;
+        }
+    }
     int dev = 0, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((int)h->smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
-    cudaError_t se = h->warp_mode ? sweep_f32w_set_smem(h->smem)
-                                  : (h->precision == SA_FP64 ? sweep_f64_set_smem(h->smem) : sweep_f32_set_smem(h->smem));
-    if (se != cudaSuccess) return SA_ECUDA;
-    const int per_item = h->warp_mode ? sweep_f32w_chains_per_block() : h->block;
-    for (int p = 0; p < P; ++p)
-        for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += per_item) {
-            const int64_t cnt = h->probs[p].chains - c0 < per_item ? h->probs[p].chains - c0 : per_item;
-            h->items.push_back(WorkItem{p, (int32_t)cnt, c0});
-        }
+    for (Group& g : h->groups) {
+        for (int p : g.probs) g.n_max = std::max(g.n_max, h->probs[p].n);
+        g.block = g.kind == kSweepF32Warp ? 256 : pick_block(h->precision, g.n_max);
+        g.smem = group_smem(g);
+        if ((int)g.smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
+        if (group_set_smem(g) != cudaSuccess) return SA_ECUDA;
+        for (int p : g.probs) g.items_cap += (size_t)((h->probs[p].chains + 7) / 8);  // smallest tile: 8 chains
+        if ((st = dalloc(h, &g.d_items, g.items_cap))) return st;
+        if (h->groups.size() > 1 &&
+            (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess))
+            return SA_ECUDA;
+    }
+    if (h->groups.size() > 1 && cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+        return SA_ECUDA;
     h->max_argmin_blocks = 1;
 
     // device memory
-    if ((st = dalloc(h, &h->d_probs, P)) || (st = dalloc(h, &h->d_items, h->items.size())) ||
+    if ((st = dalloc(h, &h->d_probs, P)) ||
         (st = dalloc(h, &h->d_run, 1)) || (st = dalloc(h, &h->d_T, h->levels_total)) ||
         (st = dalloc(h, &h->d_s, h->levels_total)) || (st = dalloc(h, &h->d_F, h->total_chains)))
         return st;
@@ -294,7 +385,8 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     const int tl = h->sch.trace_levels < h->levels_total ? h->sch.trace_levels : h->levels_total;
     if (tl > 0 && (st = dalloc(h, &h->d_bits, (size_t)tl * h->total_chains * h->words))) return st;
 
-    std::vector<ProbDev> pd(P);
+    std::vector<ProbDev>& pd = h->pd;
+    pd.resize(P);
     for (int p = 0; p < P; ++p) {
         HostProb& hp = h->probs[p];
         const int n = hp.n;
@@ -324,7 +416,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         d.hi_u = hi32[0];
         d.sig_u = sig32[0];
         d.unroll = pick_unroll(hp.cost, n);
-        d.warp_mode = h->warp_mode ? 1 : 0;
+        d.warp_mode = 0;
         d.kappa = step_kappa(hp.cost, n, lo32, hi32);
         double *dlo, *dhi, *dsig, *xb64, *xinc, *scal, *pval, *lf, *lfi;
         float *dlo32, *dhi32, *dsig32, *xb32;
@@ -372,7 +464,11 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         Tl = Tl * h->sch.rho;
     }
     RunDev run{0, 0, 0};
-    if ((st = h2d(h, h->d_probs, pd.data(), P)) || (st = h2d(h, h->d_items, h->items.data(), h->items.size())) ||
+    for (Group& g : h->groups) {
+        for (int p : g.probs) pd[p].warp_mode = g.kind == kSweepF32Warp ? 1 : 0;
+        if ((st = set_group_items(h, g))) return st;
+    }
+    if ((st = h2d(h, h->d_probs, pd.data(), P)) ||
         (st = h2d(h, h->d_run, &run, 1)) || (st = h2d(h, h->d_T, T.data(), T.size())) ||
         (st = h2d(h, h->d_s, s.data(), s.size())))
         return st;
@@ -380,7 +476,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
 
     SweepArgs& a = h->args;
     a.probs = h->d_probs;
-    a.items = h->d_items;
+    a.items = nullptr;  // per group at launch
     a.run = h->d_run;
     a.T_tab = h->d_T;
     a.s_tab = h->d_s;
@@ -757,8 +853,124 @@ void sa_destroy(sa_handle* h) {
     if (h->gN) cudaGraphExecDestroy(h->gN);
     for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (Group& g : h->groups) {
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     cudaGetLastError();
     delete h;
+}
+
+sa_status sa_create_batch(const sa_problem* problems, const sa_box* boxes, const int32_t* n, const int64_t* chains,
+                          int32_t num_problems, int32_t L, const sa_schedule* schedule, uint64_t seed, void* stream,
+                          sa_handle** out) {
+    if (out) *out = nullptr;
+    if (!problems || !boxes || !n || !chains || !out || num_problems < 1 || L < 1) return SA_EINVAL;
+    if (check_schedule(schedule) != SA_OK) return SA_EINVAL;
+    for (int p = 0; p < num_problems; ++p) {
+        if (n[p] < 1 || chains[p] < 1 || chains[p] > 2147483647LL || !boxes[p].lo || !boxes[p].hi) return SA_EINVAL;
+        if (problems[p].cost < SA_SCHWEFEL || problems[p].cost > SA_ROSENBROCK) return SA_EINVAL;
+        for (int k = 0; k < n[p]; ++k)
+            if (!std::isfinite(boxes[p].lo[k]) || !std::isfinite(boxes[p].hi[k]) || boxes[p].lo[k] > boxes[p].hi[k])
+                return SA_EINVAL;
+    }
+    sa_handle* h = new (std::nothrow) sa_handle();
+    if (!h) return SA_ENOMEM;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->sch = *schedule;
+    h->seed = seed;
+    h->L = L;
+    h->precision = schedule->precision;
+    sa_status st = build(h, problems, boxes, n, chains, num_problems);
+    if (st != SA_OK) {
+        sa_destroy(h);
+        return st;
+    }
+    *out = h;
+    return SA_OK;
+}
+
+sa_status sa_autotune(sa_handle* h, double* ms_out) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(h, SA_ECUDA);
+    sa_status st = SA_OK;
+    double total = 0.0;
+    static const int kBudgets[] = {16384, 32768, 65536, 114688};
+    static const int kUnrolls[] = {1, 2, 4};
+    for (Group& g : h->groups) {
+        if (g.kind != kSweepF32) continue;  // the other layouts have one shape
+        double best = 1e30;
+        int best_block = g.block, best_u = 1, last_block = -1;
+        for (int budget : kBudgets) {
+            int b = budget / (4 * g.n_max);
+            b = std::min(256, std::max(32, (b / 32) * 32));
+            if (b == last_block) continue;
+            last_block = b;
+            for (int u : kUnrolls) {
+                g.block = b;
+                g.smem = group_smem(g);
+                if (group_set_smem(g) != cudaSuccess) { st = SA_ECUDA; break; }
+                if ((st = set_group_items(h, g))) break;
+                for (int p : g.probs) h->pd[p].unroll = (h->probs[p].cost == SA_ACKLEY) ? 1 : u;
+                if ((st = h2d(h, h->d_probs, h->pd.data(), h->pd.size()))) break;
+                float ms = 0.f;
+                if (launch_reset(h->d_probs, (int)h->probs.size(), h->d_run, h->stream) != cudaSuccess ||
+                    cudaEventRecord(e0, h->stream) != cudaSuccess || launch_group(h, g, h->stream) != cudaSuccess ||
+                    cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    st = SA_ECUDA;
+                    break;
+                }
+                if (ms < best) { best = ms; best_block = b; best_u = u; }
+            }
+            if (st != SA_OK) break;
+        }
+        if (st != SA_OK) break;
+        g.block = best_block;
+        g.smem = group_smem(g);
+        if (group_set_smem(g) != cudaSuccess) { st = SA_ECUDA; break; }
+        if ((st = set_group_items(h, g))) break;
+        for (int p : g.probs) h->pd[p].unroll = (h->probs[p].cost == SA_ACKLEY) ? 1 : best_u;
+        total += best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == SA_OK) st = h2d(h, h->d_probs, h->pd.data(), h->pd.size());
+    if (st == SA_OK && launch_reset(h->d_probs, (int)h->probs.size(), h->d_run, h->stream) != cudaSuccess) st = SA_ECUDA;
+    if (st == SA_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = SA_ECUDA;
+    if (st != SA_OK) return fail(h, st);
+    h->levels_done = 0;
+    // the graphs hold the old launch shapes: capture again
+    if (h->g1) { cudaGraphExecDestroy(h->g1); h->g1 = nullptr; }
+    if (h->gN) { cudaGraphExecDestroy(h->gN); h->gN = nullptr; }
+    if ((st = capture_levels(h, 1, &h->g1))) return fail(h, st);
+    if (h->levels_total >= kGraphLevels && (st = capture_levels(h, kGraphLevels, &h->gN))) return fail(h, st);
+    if (ms_out) *ms_out = total;
+    return SA_OK;
+}
+
+int32_t sa_describe(const sa_handle* h, char* buf, size_t len) {
+    if (!h) return -1;
+    std::string s = "[";
+    for (size_t i = 0; i < h->groups.size(); ++i) {
+        const Group& g = h->groups[i];
+        int u = g.probs.empty() ? 1 : h->pd[g.probs[0]].unroll;
+        char tmp[256];
+        std::snprintf(tmp, sizeof(tmp), "%s{\"kind\":\"%s\",\"problems\":%zu,\"n_max\":%d,\"block\":%d,\"smem\":%zu,\"unroll\":%d,\"items\":%zu}",
+                      i ? "," : "", g.kind == kSweepF64 ? "fp64" : (g.kind == kSweepF32Warp ? "fp32_warp" : "fp32_thread"),
+                      g.probs.size(), g.n_max, g.block, g.smem, u, g.items.size());
+        s += tmp;
+    }
+    s += "]";
+    if (buf && len > 0) {
+        std::strncpy(buf, s.c_str(), len - 1);
+        buf[len - 1] = '\0';
+    }
+    return (int32_t)s.size();
 }
 
 sa_status sa_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t key0, uint32_t key1, int64_t count,

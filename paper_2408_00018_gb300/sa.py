@@ -58,6 +58,9 @@ SIGNATURES = {
     "sa_default_schedule": (None, [_V]),
     "sa_levels_for": (_I32, [_D, _D, _D]),
     "sa_create": (ctypes.c_int, [_V, _V, _I32, _I64, _I32, _V, _U64, _V, _V]),
+    "sa_create_batch": (ctypes.c_int, [_V, _V, _V, _V, _I32, _I32, _V, _U64, _V, _V]),
+    "sa_autotune": (ctypes.c_int, [_V, _V]),
+    "sa_describe": (_I32, [_V, _V, _SZ]),
     "sa_run": (ctypes.c_int, [_V, _I32]),
     "sa_reset": (ctypes.c_int, [_V]),
     "sa_profile": (ctypes.c_int, [_V, _I32, _V, _V]),
@@ -149,6 +152,21 @@ class Handle:
 
     def reset(self):
         _check(load().sa_reset(self._ptr), "sa_reset")
+
+    def autotune(self) -> float:
+        """Pick launch shapes per dimension group by timing level-0 sweeps; returns the summed ms."""
+        ms = ctypes.c_double()
+        _check(load().sa_autotune(self._ptr, ctypes.byref(ms)), "sa_autotune")
+        return ms.value
+
+    def describe(self):
+        """The handle's launch groups (kind, problems, n_max, block, smem, unroll, items)."""
+        import json
+        lib = load()
+        m = lib.sa_describe(self._ptr, None, 0)
+        buf = ctypes.create_string_buffer(m + 1)
+        lib.sa_describe(self._ptr, buf, m + 1)
+        return json.loads(buf.value.decode())
 
     def profile(self, levels: int = -1):
         """Eager run with CUDA events: per-level (sweep_ms, level_ms)."""
@@ -243,6 +261,65 @@ def create(cost, lo, hi, n, chains, L, schedule: Schedule | None = None, seed: i
     _check(lib.sa_create(ctypes.byref(prob), ctypes.byref(box), n, chains, L, ctypes.byref(sch), seed, s,
                          ctypes.byref(out)), "sa_create")
     return Handle(out, n, chains, L, schedule)
+
+
+class BatchHandle(Handle):
+    """sa_create_batch: several independent problems in one solver."""
+
+    def __init__(self, ptr, ns, chains, L, schedule):
+        super().__init__(ptr, max(ns), sum(chains), L, schedule)
+        self.ns, self.chains_per = list(ns), list(chains)
+
+    def best(self, problem: int = 0):
+        x = np.zeros(self.ns[problem])
+        f = ctypes.c_double()
+        st = _Stats()
+        _check(load().sa_best(self._ptr, problem, x.ctypes.data, ctypes.byref(f), ctypes.byref(st)), "sa_best")
+        return x, f.value, {k: getattr(st, k) for k, _ in _Stats._fields_}
+
+    def trace_states(self, level: int):
+        """Final states of a traced level: list over problems of (X [chains_p, n_p], F [chains_p])."""
+        total = sum(n * c for n, c in zip(self.ns, self.chains_per))
+        X = np.zeros(total)
+        F = np.zeros(sum(self.chains_per))
+        _check(load().sa_trace_states(self._ptr, level, X.ctypes.data, F.ctypes.data), "sa_trace_states")
+        out, xo, co = [], 0, 0
+        for n, c in zip(self.ns, self.chains_per):
+            out.append((X[xo:xo + n * c].reshape(c, n), F[co:co + c]))
+            xo += n * c
+            co += c
+        return out
+
+    def trace(self, level: int):
+        """Accept bits of a traced level: list over problems of [chains_p, words]."""
+        words = (self.L + 31) // 32
+        bits = np.zeros((sum(self.chains_per), words), np.uint32)
+        _check(load().sa_trace(self._ptr, level, bits.ctypes.data, bits.size), "sa_trace")
+        out, co = [], 0
+        for c in self.chains_per:
+            out.append(bits[co:co + c])
+            co += c
+        return out
+
+
+def create_batch(problems, L, schedule: Schedule | None = None, seed: int = 0, stream=None) -> BatchHandle:
+    """sa_create_batch: problems is a list of dicts with cost, n, chains, lo, hi."""
+    lib = load()
+    schedule = schedule or Schedule()
+    P = len(problems)
+    los = [np.ascontiguousarray(np.broadcast_to(np.asarray(p["lo"], np.float64), (p["n"],))) for p in problems]
+    his = [np.ascontiguousarray(np.broadcast_to(np.asarray(p["hi"], np.float64), (p["n"],))) for p in problems]
+    probs = (_Problem * P)(*[_Problem(COSTS[p["cost"]] if isinstance(p["cost"], str) else int(p["cost"]), None)
+                            for p in problems])
+    boxes = (_Box * P)(*[_Box(lo.ctypes.data, hi.ctypes.data) for lo, hi in zip(los, his)])
+    ns = np.array([p["n"] for p in problems], np.int32)
+    cs = np.array([p["chains"] for p in problems], np.int64)
+    sch = schedule._c()
+    out = ctypes.c_void_p()
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check(lib.sa_create_batch(probs, boxes, ns.ctypes.data, cs.ctypes.data, P, L, ctypes.byref(sch), seed, s,
+                               ctypes.byref(out)), "sa_create_batch")
+    return BatchHandle(out, ns.tolist(), cs.tolist(), L, schedule)
 
 
 def philox_fill(ctr, key, out) -> None:
