@@ -180,25 +180,25 @@ int pick_unroll(int cost, int n) {
         if (u == 1 || u == 2 || u == 4) return u;
     }
     if (cost == SA_ACKLEY) return 1;
-    if (n >= 64) return 4;
-    if (n >= 16) return 2;
+    if (n >= 16) return 2;  // measured at n = 256: U = 2 2.05 ms, U = 4 2.08 ms, U = 1 2.47 ms per level
     return 1;
 }
 
 // FP32 sweep layout: one chain per warp (32 consecutive steps per group)
 // pays when a group rarely touches a coordinate twice and the cost has no
 // global running sums.  SA_WARP_MODE=0/1 overrides for tuning runs.
+bool warp_eligible(int cost) { return cost == SA_SCHWEFEL || cost == SA_RASTRIGIN || cost == SA_ROSENBROCK; }
+
 bool pick_warp_mode(int cost, int n) {
+    if (!warp_eligible(cost)) return false;
     if (const char* e = std::getenv("SA_WARP_MODE")) {
         if (e[0] == '0') return false;
-        if (e[0] == '1') return cost == SA_SCHWEFEL || cost == SA_RASTRIGIN || cost == SA_ROSENBROCK;
+        if (e[0] == '1') return true;
     }
-    // Measured on the n = 256 Schwefel workload: 2.11 ms per level against
-    // 2.05 ms for one chain per thread with two-step groups (the warp layout
-    // issues at ~60% but is limited by constant loads on the ADU pipe), so
-    // the thread layout stays the default.
-    (void)n;
-    return false;
+    // Default before autotuning.  At n = 256 the two layouts are within 3%
+    // (2.05 ms vs 2.11 ms per level on the Schwefel workload); above that the
+    // thread layout's shared memory per chain leaves too few warps per SM.
+    return n > 256;
 }
 
 // Bound on the FP32 error of one accepted step's dF over the whole box (the
@@ -340,19 +340,23 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         h->groups[0].kind = kSweepF64;
         for (int p = 0; p < P; ++p) h->groups[0].probs.push_back(p);
     } else {
+        // one group per (dimension bucket, layout-eligible) pair: the
+        // chain-per-warp layout serves costs without global running sums
         const int nb = (int)(sizeof(kBucketBounds) / sizeof(int));
-        std::vector<Group> b(nb);
+        std::vector<Group> b(2 * nb);
         for (int p = 0; p < P; ++p) {
             int i = 0;
             while (h->probs[p].n > kBucketBounds[i]) ++i;
-            b[i].probs.push_back(p);
+            const bool eligible = warp_eligible(h->probs[p].cost);
+            b[2 * i + (eligible ? 1 : 0)].probs.push_back(p);
         }
-        for (Group& g : b)
-            if (!g.probs.empty()) h->groups.push_back(g);
-        for (Group& g : h->groups) {
-            bool warp = true;
-            for (int p : g.probs) warp = warp && pick_warp_mode(h->probs[p].cost, h->probs[p].n);
-            g.kind = warp ? kSweepF32Warp : kSweepF32;
+        for (int i = 0; i < 2 * nb; ++i) {
+            Group& g = b[i];
+            if (g.probs.empty()) continue;
+            int nmax = 1;
+            for (int p : g.probs) nmax = std::max(nmax, h->probs[p].n);
+            g.kind = ((i & 1) && pick_warp_mode(h->probs[g.probs[0]].cost, nmax)) ? kSweepF32Warp : kSweepF32;
+            h->groups.push_back(g);
         }
     }
     int dev = 0, max_optin = 0;
@@ -901,40 +905,51 @@ sa_status sa_autotune(sa_handle* h, double* ms_out) {
     double total = 0.0;
     static const int kBudgets[] = {16384, 32768, 65536, 114688};
     static const int kUnrolls[] = {1, 2, 4};
+    struct Shape { int kind, block, unroll; };
+    // Apply a launch shape to a group (block, shared memory, work items, per-problem unroll).
+    auto apply = [h](Group& g, const Shape& c) -> sa_status {
+        g.kind = c.kind;
+        g.block = c.block;
+        g.smem = group_smem(g);
+        if (group_set_smem(g) != cudaSuccess) return SA_ECUDA;
+        sa_status s2 = set_group_items(h, g);
+        if (s2) return s2;
+        for (int p : g.probs) {
+            h->pd[p].unroll = (h->probs[p].cost == SA_ACKLEY) ? 1 : c.unroll;
+            h->pd[p].warp_mode = c.kind == kSweepF32Warp ? 1 : 0;
+        }
+        return h2d(h, h->d_probs, h->pd.data(), h->pd.size());
+    };
     for (Group& g : h->groups) {
-        if (g.kind != kSweepF32) continue;  // the other layouts have one shape
-        double best = 1e30;
-        int best_block = g.block, best_u = 1, last_block = -1;
+        if (g.kind == kSweepF64) continue;  // one shape only
+        std::vector<Shape> cands;
+        int last_block = -1;
         for (int budget : kBudgets) {
             int b = budget / (4 * g.n_max);
             b = std::min(256, std::max(32, (b / 32) * 32));
             if (b == last_block) continue;
             last_block = b;
-            for (int u : kUnrolls) {
-                g.block = b;
-                g.smem = group_smem(g);
-                if (group_set_smem(g) != cudaSuccess) { st = SA_ECUDA; break; }
-                if ((st = set_group_items(h, g))) break;
-                for (int p : g.probs) h->pd[p].unroll = (h->probs[p].cost == SA_ACKLEY) ? 1 : u;
-                if ((st = h2d(h, h->d_probs, h->pd.data(), h->pd.size()))) break;
-                float ms = 0.f;
-                if (launch_reset(h->d_probs, (int)h->probs.size(), h->d_run, h->stream) != cudaSuccess ||
-                    cudaEventRecord(e0, h->stream) != cudaSuccess || launch_group(h, g, h->stream) != cudaSuccess ||
-                    cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    st = SA_ECUDA;
-                    break;
-                }
-                if (ms < best) { best = ms; best_block = b; best_u = u; }
+            for (int u : kUnrolls) cands.push_back(Shape{kSweepF32, b, u});
+        }
+        bool eligible = true;
+        for (int p : g.probs) eligible = eligible && warp_eligible(h->probs[p].cost);
+        if (eligible) cands.push_back(Shape{kSweepF32Warp, 256, 1});
+        double best = 1e30;
+        Shape best_shape = cands[0];
+        for (const Shape& c : cands) {
+            if ((st = apply(g, c))) break;
+            float ms = 0.f;
+            if (launch_reset(h->d_probs, (int)h->probs.size(), h->d_run, h->stream) != cudaSuccess ||
+                cudaEventRecord(e0, h->stream) != cudaSuccess || launch_group(h, g, h->stream) != cudaSuccess ||
+                cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = SA_ECUDA;
+                break;
             }
-            if (st != SA_OK) break;
+            if (ms < best) { best = ms; best_shape = c; }
         }
         if (st != SA_OK) break;
-        g.block = best_block;
-        g.smem = group_smem(g);
-        if (group_set_smem(g) != cudaSuccess) { st = SA_ECUDA; break; }
-        if ((st = set_group_items(h, g))) break;
-        for (int p : g.probs) h->pd[p].unroll = (h->probs[p].cost == SA_ACKLEY) ? 1 : best_u;
+        if ((st = apply(g, best_shape))) break;
         total += best;
     }
     cudaEventDestroy(e0);
