@@ -78,7 +78,9 @@ typedef struct {
     int32_t boundary;   /* SA_REFLECT (reflect once, then clip) or SA_CLIP */
     int32_t precision;  /* SA_FP64 or SA_FP32 (state in FP32, argmin in FP64) */
     int32_t surrogate;  /* reserved, must be 0 */
-    int32_t polish_k;   /* reserved, must be 0 */
+    int32_t polish_k;   /* hybrid SA: after the last level, polish the polish_k best final
+                           states (0..1024) with sa_polish's method; the best polished point
+                           becomes the incumbent if it is lower (0 = off) */
     int32_t trace_levels; /* record accept bits of the first trace_levels levels (0 = off) */
 } sa_schedule;
 
@@ -229,6 +231,24 @@ sa_status sa_restore(sa_handle* h, const void* buf, size_t len);
 void sa_destroy(sa_handle* h);
 
 const char* sa_strerror(sa_status s);
+
+/*
+ * Local minimiser of the hybrid SA (the paper polishes SA points with
+ * Nelder-Mead, Sec. 4.2 / Table 10; this library uses box-projected gradient
+ * descent): from each of k start points x0[j*n .. j*n+n) (host), iterate
+ * x <- P_I(x - alpha grad f(x)) in FP64 with alpha halved from 1 (at most 30
+ * times) until f(x_new) <= f(x) + 1e-4 grad f . (x_new - x); stop when the
+ * projected gradient's infinity norm is below tol, when no step decreases
+ * f, or after max_iter iterations.  Writes the final points to x_out (host
+ * [k*n]), their values to f_out (host [k]) and the iteration counts to
+ * iters_out (host [k], may be NULL).  Separable costs only (Q must be NULL).
+ * Allocates its device buffers stream-ordered; synchronises `stream`.
+ * Errors: SA_EINVAL on n < 1, k not in [1, 1024], a bad box, max_iter < 0,
+ * tol < 0, a NULL array or a rotated cost; SA_ENOMEM; SA_ECUDA.
+ */
+sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
+                    const double* x0, int32_t max_iter, double tol, double* x_out, double* f_out,
+                    int32_t* iters_out, void* stream);
 
 /*
  * Kernel-level entry point: Philox4x32-10 (Salmon et al., SC'11) blocks for

@@ -463,6 +463,8 @@ int sao_level_chains(const sao_cfg* cfg, int32_t level, const double* x_start, i
 /* Box-projected gradient descent with Armijo backtracking: the local       */
 /* minimiser of the hybrid SA (the paper hands the SA point to Nelder-Mead, */
 /* Sec. 4.2 / Table 10; here a projected gradient method takes that role).  */
+/* The first search starts at alpha = 1, every later one at twice the last  */
+/* accepted step (capped at 1e12), halving at most max_halvings times.       */
 /* ------------------------------------------------------------------------ */
 int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
             double* x, int32_t max_iter, double tol, double armijo_c, int32_t max_halvings,
@@ -473,6 +475,7 @@ int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const d
     if (!g || !xn || !yw) { free(g); free(xn); free(yw); return -2; }
     for (int i = 0; i < n; ++i) x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
     double f = sao_cost_ws(cost, n, x, Q, yw);
+    double alpha_next = 1.0;
     int it = 0;
     for (; it < max_iter; ++it) {
         sao_grad(cost, n, x, Q, g);
@@ -482,7 +485,7 @@ int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const d
             if (fabs(v) > pg) pg = fabs(v);
         }
         if (pg < tol) break;
-        double alpha = 1.0;
+        double alpha = alpha_next;
         int ok = 0;
         double fn = f;
         for (int h = 0; h < max_halvings; ++h) {
@@ -498,6 +501,7 @@ int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const d
         if (!ok) break;
         memcpy(x, xn, sizeof(double) * (size_t)n);
         f = fn;
+        alpha_next = fmin(2.0 * alpha, 1e12);
     }
     free(g);
     free(xn);

@@ -27,6 +27,7 @@ UNITS = {
     "reduce.cu": [],
     "sa_api.cu": [],
     "argmin_static.cu": [],
+    "polish.cu": [],
 }
 
 

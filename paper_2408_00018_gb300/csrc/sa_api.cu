@@ -88,6 +88,11 @@ struct sa_handle {
     float* d_X32 = nullptr;
     double* d_X64 = nullptr;
     uint32_t* d_bits = nullptr;
+    // hybrid polish buffers (polish_k > 0)
+    double* d_Fcopy = nullptr;
+    int64_t* d_topk = nullptr;
+    double *d_px0 = nullptr, *d_px = nullptr, *d_pf = nullptr;
+    int* d_pit = nullptr;
     SweepArgs args{};
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
 };
@@ -145,7 +150,7 @@ sa_status check_schedule(const sa_schedule* s) {
     if (!(s->sigma_frac > 0.0) || !std::isfinite(s->sigma_frac)) return SA_EINVAL;
     if (s->boundary != SA_REFLECT && s->boundary != SA_CLIP) return SA_EINVAL;
     if (s->precision != SA_FP64 && s->precision != SA_FP32) return SA_EINVAL;
-    if (s->surrogate != 0 || s->polish_k != 0) return SA_EINVAL;
+    if (s->surrogate != 0 || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
     if (s->trace_levels < 0) return SA_EINVAL;
     return SA_OK;
 }
@@ -305,6 +310,28 @@ sa_status device_status(sa_handle* h) {
     if (st == 5) return fail(h, SA_ENUMERIC);
     if (st == 4) return fail(h, SA_ETIMEOUT);
     if (st != 0) return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
+// Hybrid SA (after the last level): the polish_k best final states of each
+// problem, by FP64 value with lowest index on ties, are polished by
+// box-projected gradient descent; the best polished point replaces the
+// incumbent if it is lower.
+sa_status run_polish(sa_handle* h) {
+    if (h->sch.polish_k <= 0) return SA_OK;
+    for (size_t p = 0; p < h->probs.size(); ++p) {
+        const HostProb& hp = h->probs[p];
+        const int k = (int)std::min<int64_t>(h->sch.polish_k, hp.chains);
+        if (cudaMemcpyAsync(h->d_Fcopy, h->d_F + hp.chain_base, hp.chains * sizeof(double), cudaMemcpyDeviceToDevice,
+                            h->stream) != cudaSuccess ||
+            launch_topk(h->d_Fcopy, hp.chains, k, h->d_topk, h->stream) != cudaSuccess ||
+            launch_gather(h->d_X32, h->d_X64, hp.x_base, hp.chains, hp.n, h->d_topk, k, h->d_px0, h->stream) !=
+                cudaSuccess ||
+            launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, k, h->d_px0, h->d_px, h->d_pf, h->d_pit, 1000, 1e-10,
+                       h->stream) != cudaSuccess ||
+            launch_polish_update(h->d_probs, (int)p, h->d_px, h->d_pf, k, h->stream) != cudaSuccess)
+            return fail(h, SA_ECUDA);
+    }
     return SA_OK;
 }
 
@@ -492,6 +519,16 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     a.L = h->L;
     a.words = h->words;
     a.trace_levels = tl;
+    a.full_level = h->sch.polish_k > 0 ? h->levels_total - 1 : -1;
+    if (h->sch.polish_k > 0) {
+        int n_max = 1;
+        for (auto& hp : h->probs) n_max = std::max(n_max, hp.n);
+        const size_t k = (size_t)h->sch.polish_k;
+        if ((st = dalloc(h, &h->d_Fcopy, h->total_chains)) || (st = dalloc(h, &h->d_topk, k)) ||
+            (st = dalloc(h, &h->d_px0, k * n_max)) || (st = dalloc(h, &h->d_px, k * n_max)) ||
+            (st = dalloc(h, &h->d_pf, k)) || (st = dalloc(h, &h->d_pit, k)))
+            return st;
+    }
     a.boundary = h->sch.boundary;
     a.key0 = (uint32_t)h->seed;
     a.key1 = (uint32_t)(h->seed >> 32) ^ kTagSweep;
@@ -603,6 +640,7 @@ sa_status sa_run(sa_handle* h, int32_t levels) {
         h->levels_done += step;
         k -= step;
     }
+    if (h->levels_done == h->levels_total) return run_polish(h);
     return SA_OK;
 }
 
@@ -649,7 +687,41 @@ sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* lev
         if (level_ms) level_ms[l] = b;
     }
     for (auto& e : ev) cudaEventDestroy(e);
+    if (st == SA_OK && h->levels_done == h->levels_total) return run_polish(h);
     return st == SA_OK ? SA_OK : fail(h, st);
+}
+
+sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
+                    const double* x0, int32_t max_iter, double tol, double* x_out, double* f_out, int32_t* iters_out,
+                    void* stream) {
+    if (n < 1 || k < 1 || k > 1024 || !lo || !hi || !x0 || !x_out || !f_out || max_iter < 0 || !(tol >= 0.0))
+        return SA_EINVAL;
+    if (cost < SA_SCHWEFEL || cost > SA_ROSENBROCK || Q) return SA_EINVAL;  // rotated costs: not in this call yet
+    for (int d = 0; d < n; ++d)
+        if (!std::isfinite(lo[d]) || !std::isfinite(hi[d]) || lo[d] > hi[d]) return SA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *dlo = nullptr, *dhi = nullptr, *dx0 = nullptr, *dx = nullptr, *df = nullptr;
+    int* dit = nullptr;
+    const size_t kn = (size_t)k * n;
+    sa_status st = SA_OK;
+    if (cudaMallocAsync(&dlo, n * sizeof(double), s) || cudaMallocAsync(&dhi, n * sizeof(double), s) ||
+        cudaMallocAsync(&dx0, kn * sizeof(double), s) || cudaMallocAsync(&dx, kn * sizeof(double), s) ||
+        cudaMallocAsync(&df, k * sizeof(double), s) || cudaMallocAsync(&dit, k * sizeof(int), s))
+        st = SA_ENOMEM;
+    if (st == SA_OK &&
+        (cudaMemcpyAsync(dlo, lo, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
+         cudaMemcpyAsync(dhi, hi, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
+         cudaMemcpyAsync(dx0, x0, kn * sizeof(double), cudaMemcpyHostToDevice, s) ||
+         launch_pgd(cost, n, dlo, dhi, k, dx0, dx, df, dit, max_iter, tol, s) ||
+         cudaMemcpyAsync(x_out, dx, kn * sizeof(double), cudaMemcpyDeviceToHost, s) ||
+         cudaMemcpyAsync(f_out, df, k * sizeof(double), cudaMemcpyDeviceToHost, s) ||
+         (iters_out && cudaMemcpyAsync(iters_out, dit, k * sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+         cudaStreamSynchronize(s)))
+        st = SA_ECUDA;
+    for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit})
+        if (p) cudaFreeAsync(p, s);
+    cudaGetLastError();
+    return st;
 }
 
 sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, sa_stats* stt) {

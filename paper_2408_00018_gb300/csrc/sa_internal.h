@@ -79,6 +79,7 @@ struct SweepArgs {
     int32_t L;
     int32_t words;         // ceil(L / 32)
     int32_t trace_levels;
+    int32_t full_level;    // level whose every chain is re-evaluated in FP64 and stored (-1: none)
     int32_t boundary;      // 0 reflect then clip, 1 clip
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
@@ -99,6 +100,12 @@ size_t sweep_f32w_smem_bytes(int n);
 cudaError_t sweep_f32w_set_smem(size_t bytes);
 int sweep_f32w_chains_per_block();
 cudaError_t sweep_f64_set_smem(size_t bytes);
+cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, int k, const double* x0, double* x_out,
+                       double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s);
+cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStream_t s);
+cudaError_t launch_gather(const float* X32, const double* X64, int64_t x_base, int64_t chains, int n, const int64_t* idx,
+                          int k, double* out, cudaStream_t s);
+cudaError_t launch_polish_update(ProbDev* probs, int problem, const double* xs, const double* fs, int k, cudaStream_t s);
 
 constexpr int kArgminThreads = 256;
 constexpr int kArgminPerThread = 8;

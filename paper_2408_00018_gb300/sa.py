@@ -73,6 +73,7 @@ SIGNATURES = {
     "sa_destroy": (None, [_V]),
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
+    "sa_polish": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _I32, _D, _V, _V, _V, _V]),
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
     "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
@@ -130,10 +131,11 @@ class Schedule:
     boundary: str = "reflect"
     precision: str = "fp64"
     trace_levels: int = 0
+    polish_k: int = 0
 
     def _c(self) -> _Schedule:
         return _Schedule(self.T0, self.rho, self.T_min, self.levels, self.sigma_frac, BOUNDARY[self.boundary],
-                         PRECISION[self.precision], 0, 0, self.trace_levels)
+                         PRECISION[self.precision], 0, self.polish_k, self.trace_levels)
 
 
 def levels_for(T0: float, rho: float, T_min: float) -> int:
@@ -320,6 +322,22 @@ def create_batch(problems, L, schedule: Schedule | None = None, seed: int = 0, s
     _check(lib.sa_create_batch(probs, boxes, ns.ctypes.data, cs.ctypes.data, P, L, ctypes.byref(sch), seed, s,
                                ctypes.byref(out)), "sa_create_batch")
     return BatchHandle(out, ns.tolist(), cs.tolist(), L, schedule)
+
+
+def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, stream=None):
+    """sa_polish: box-projected gradient descent from each row of x0 (k x n); returns (x, f, iters)."""
+    x0 = np.ascontiguousarray(np.atleast_2d(np.asarray(x0, np.float64)))
+    k, n = x0.shape
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (n,)))
+    x = np.zeros_like(x0)
+    f = np.zeros(k)
+    it = np.zeros(k, np.int32)
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check(load().sa_polish(COSTS[cost] if isinstance(cost, str) else int(cost), n, lo.ctypes.data, hi.ctypes.data,
+                            None, k, x0.ctypes.data, max_iter, tol, x.ctypes.data, f.ctypes.data, it.ctypes.data, s),
+           "sa_polish")
+    return x, f, it
 
 
 def philox_fill(ctr, key, out) -> None:
