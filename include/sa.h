@@ -251,6 +251,19 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
                     int32_t* iters_out, void* stream);
 
 /*
+ * Kernel-level entry point: tensor-core GEMM D = A . B^T with A [M x K] and
+ * B [N x K] row-major BF16 (K contiguous; leading dimensions lda, ldb in
+ * elements, rows 16-byte aligned) and D [M x N] row-major FP32 (leading
+ * dimension ldd), FP32 accumulation (tcgen05 on sm_103a).  Used by the
+ * rotated-cost transform and the surrogate network; exposed for testing.
+ * M must be a multiple of 128, N of 64, K of 64, ldd of 4.  d_status (device
+ * int, may be NULL) receives SA_ETIMEOUT if a bounded wait inside the kernel
+ * expires.  Asynchronous.  Errors: SA_EINVAL on shapes, alignment or NULL.
+ */
+sa_status sa_gemm_bf16(const void* d_A, int32_t lda, const void* d_B, int32_t ldb, float* d_D, int32_t ldd,
+                       int32_t M, int32_t N, int32_t K, int32_t* d_status, void* stream);
+
+/*
  * Kernel-level entry point: Philox4x32-10 (Salmon et al., SC'11) blocks for
  * counters (c0 + i, c1, c2, c3), i = 0..count-1, with key (key0, key1);
  * block i goes to d_out[4 i .. 4 i + 3].  d_out: device, >= 4 count uint32.

@@ -28,6 +28,7 @@ UNITS = {
     "sa_api.cu": [],
     "argmin_static.cu": [],
     "polish.cu": [],
+    "gemm_tc.cu": [],
 }
 
 

@@ -691,6 +691,16 @@ sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* lev
     return st == SA_OK ? SA_OK : fail(h, st);
 }
 
+sa_status sa_gemm_bf16(const void* d_A, int32_t lda, const void* d_B, int32_t ldb, float* d_D, int32_t ldd, int32_t M,
+                       int32_t N, int32_t K, int32_t* d_status, void* stream) {
+    if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldd < N) return SA_EINVAL;
+    if (M % 128 || N % 64 || K % 64 || ldd % 4) return SA_EINVAL;
+    int* st = d_status ? d_status : gemm_status_ptr();
+    const cudaError_t e = launch_gemm_bf16_f32(d_A, lda, d_B, ldb, d_D, ldd, M, N, K, st, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorInvalidValue) { cudaGetLastError(); return SA_EINVAL; }
+    return e == cudaSuccess ? SA_OK : SA_ECUDA;
+}
+
 sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
                     const double* x0, int32_t max_iter, double tol, double* x_out, double* f_out, int32_t* iters_out,
                     void* stream) {

@@ -103,6 +103,9 @@ cudaError_t sweep_f64_set_smem(size_t bytes);
 cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, int k, const double* x0, double* x_out,
                        double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s);
 cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStream_t s);
+cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
+                                 int* status, cudaStream_t s);
+int* gemm_status_ptr();
 cudaError_t launch_gather(const float* X32, const double* X64, int64_t x_base, int64_t chains, int n, const int64_t* idx,
                           int k, double* out, cudaStream_t s);
 cudaError_t launch_polish_update(ProbDev* probs, int problem, const double* xs, const double* fs, int k, cudaStream_t s);

@@ -74,6 +74,7 @@ SIGNATURES = {
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
     "sa_polish": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _I32, _D, _V, _V, _V, _V]),
+    "sa_gemm_bf16": (ctypes.c_int, [_V, _I32, _V, _I32, _V, _I32, _I32, _I32, _I32, _V, _V]),
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
     "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
