@@ -94,6 +94,7 @@ typedef struct {
     int64_t h2d_bytes;    /* bytes this handle copied host -> device so far */
     int64_t d2h_bytes;    /* bytes this handle copied device -> host so far */
     int64_t t_start_ns;   /* device clock (ns) when level 0 of the current run started */
+    int64_t rechecks;     /* rotated costs: decisions re-taken in FP64 so far (0 otherwise) */
 } sa_stats;
 
 typedef struct sa_handle sa_handle;
@@ -111,10 +112,17 @@ int32_t sa_levels_for(double T0, double rho, double T_min);
  * Create a solver for one problem (Eq. 1) with `chains` Markov chains of `L`
  * steps per level.  Copies box, Q and the schedule to device memory that the
  * handle owns (stream-ordered allocation on `stream`).  Launches nothing.
+ * Rotated costs (SA_ROT_*) need precision SA_FP32: each chain keeps y = Q x
+ * as an FP32 pair (hi + lo), updates it by rank-1 corrections on accepted
+ * moves, decides in FP32 with a rigorous error bound and re-takes in FP64
+ * every decision that falls inside the bound (sa_stats.rechecks counts them);
+ * level 0 transforms the initial points as one FP64 product X0 Q^T.  They
+ * hold 12 chains n bytes of level-0 buffers and 24 n^2 bytes of copies of Q.
  * Errors: SA_EINVAL if n < 1, chains < 1, L < 1, lo[k] > hi[k] or not finite,
  * T0 <= 0, rho not in (0,1), levels < 0, levels == 0 and T_min not in
  * (0, T0), sigma_frac <= 0, unknown cost/boundary/precision, a rotated cost
- * without Q, surrogate or polish_k != 0, or chains > 2^31 - 1;
+ * without Q, with a non-finite Q entry, with n^2 > 2^28, with precision other
+ * than SA_FP32 or with polish_k != 0, surrogate != 0, or chains > 2^31 - 1;
  * SA_ENOMEM / SA_ECUDA on allocation or copy failure.  *out is NULL on error.
  */
 sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains,

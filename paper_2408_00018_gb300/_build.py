@@ -29,6 +29,8 @@ UNITS = {
     "argmin_static.cu": [],
     "polish.cu": [],
     "gemm_tc.cu": [],
+    "sweep_rot.cu": [],
+    "rot_prep.cu": [],
 }
 
 

@@ -116,8 +116,10 @@ __global__ void __launch_bounds__(kArgminThreads) argmin_restart_kernel(const Pr
                 xb = (double)xf;
             }
             if (improve) P.x_inc[k] = xb;
-            p1 += xb * xb;
-            p2 += cos(6.283185307179586 * xb);
+            if (P.cost == kAckley) {
+                p1 += xb * xb;
+                p2 += cos(6.283185307179586 * xb);
+            }
         }
         if (P.cost == kAckley) {
 #pragma unroll
@@ -166,6 +168,7 @@ __global__ void reset_kernel(ProbDev* probs, int num_probs, RunDev* run) {
         *P.level_min = 0xFFF0000000000000ull;
         *P.done = 0u;
         *P.accepts = 0ull;
+        if (P.rechecks) *P.rechecks = 0ull;
     }
     if (p == 0) {
         run->level = 0;

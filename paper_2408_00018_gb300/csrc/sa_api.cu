@@ -42,7 +42,9 @@ struct HostProb {
 // Problems whose sweep runs as one kernel launch with one block shape.  A
 // batch of problems of uneven dimension is split by n into groups; within a
 // level the groups' sweeps run concurrently on forked streams.
-enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2 };
+enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2, kSweepRot = 3 };
+
+bool is_rot(int cost) { return cost == SA_ROT_RASTRIGIN || cost == SA_ROT_SCHWEFEL; }
 struct Group {
     int kind = kSweepF32;
     int n_max = 1;
@@ -155,6 +157,22 @@ sa_status check_schedule(const sa_schedule* s) {
     return SA_OK;
 }
 
+// Checks of one problem shared by sa_create and sa_create_batch.
+sa_status check_problem(const sa_problem& pr, const sa_box& box, int32_t n, int64_t chains, const sa_schedule& sch) {
+    if (n < 1 || chains < 1 || chains > 2147483647LL || !box.lo || !box.hi) return SA_EINVAL;
+    if (pr.cost < SA_SCHWEFEL || pr.cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
+    if (is_rot(pr.cost)) {
+        // rotated costs run the FP32 rank-1 sweep; the hybrid polish covers separable costs
+        if (!pr.Q || sch.precision != SA_FP32 || sch.polish_k != 0) return SA_EINVAL;
+        if ((int64_t)n * n > ((int64_t)1 << 28)) return SA_EINVAL;
+        for (size_t k = 0; k < (size_t)n * n; ++k)
+            if (!std::isfinite(pr.Q[k])) return SA_EINVAL;
+    }
+    for (int k = 0; k < n; ++k)
+        if (!std::isfinite(box.lo[k]) || !std::isfinite(box.hi[k]) || box.lo[k] > box.hi[k]) return SA_EINVAL;
+    return SA_OK;
+}
+
 int pick_block(int precision, int n_max) {
     // FP64 arithmetic is a small fraction of the FP32 rate on this GPU, so the
     // FP64 sweep uses one warp per block: chains spread over as many SMs as
@@ -224,6 +242,7 @@ cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
     if (num == 0) return cudaSuccess;
     if (g.kind == kSweepF64) return launch_sweep_f64(a, num, g.block, g.smem, s);
     if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.smem, s);
+    if (g.kind == kSweepRot) return launch_sweep_rot(a, num, g.smem, s);
     return launch_sweep_f32(a, num, g.block, g.smem, s);
 }
 
@@ -245,7 +264,9 @@ cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
 // Work items of a group for its current block shape (tiles of one problem's
 // chains), largest problems first; uploaded on the handle's stream.
 sa_status set_group_items(sa_handle* h, Group& g) {
-    const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block() : g.block;
+    const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block()
+                         : g.kind == kSweepRot   ? sweep_rot_chains_per_block()
+                                                 : g.block;
     std::vector<int> order = g.probs;
     std::sort(order.begin(), order.end(), [h](int a, int b) { return h->probs[a].chains > h->probs[b].chains; });
     g.items.clear();
@@ -263,12 +284,14 @@ sa_status set_group_items(sa_handle* h, Group& g) {
 
 size_t group_smem(const Group& g) {
     if (g.kind == kSweepF32Warp) return sweep_f32w_smem_bytes(g.n_max);
+    if (g.kind == kSweepRot) return sweep_rot_smem_bytes(g.n_max);
     if (g.kind == kSweepF64) return sweep_f64_smem_bytes(g.n_max, g.block);
     return sweep_f32_smem_bytes(g.n_max, g.block);
 }
 
 cudaError_t group_set_smem(const Group& g) {
     if (g.kind == kSweepF32Warp) return sweep_f32w_set_smem(g.smem);
+    if (g.kind == kSweepRot) return sweep_rot_set_smem(g.smem);
     if (g.kind == kSweepF64) return sweep_f64_set_smem(g.smem);
     return sweep_f32_set_smem(g.smem);
 }
@@ -279,9 +302,16 @@ constexpr int kBucketBounds[] = {16, 32, 64, 128, 256, 512, 1 << 30};
 cudaError_t launch_level_tail(sa_handle* h, cudaStream_t s) {
     cudaError_t e = launch_argmin_restart(h->args, h->d_probs, (int)h->probs.size(), h->max_argmin_blocks,
                                           h->precision == SA_FP64 ? 0 : 1, s);
+    // rotated costs: y_best = Q x_best and F(y_best) for the next level
+    for (size_t p = 0; p < h->probs.size() && e == cudaSuccess; ++p)
+        if (is_rot(h->probs[p].cost)) e = launch_rot_restart(h->d_probs + p, h->probs[p].n, s);
     if (e == cudaSuccess) e = launch_level_end(h->d_run, s);
     return e;
 }
+
+// Work that precedes level 0 of a run: the start stamp and, for rotated
+// costs, the initial points X0 and their transform Y0 = X0 Q^T.
+cudaError_t launch_level0_prep(sa_handle* h, cudaStream_t s);
 
 sa_status capture_levels(sa_handle* h, int levels, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
@@ -335,6 +365,51 @@ sa_status run_polish(sa_handle* h) {
     return SA_OK;
 }
 
+// Device copies of Q for a rotated cost (row-major FP64; transposed FP64 and
+// its FP32 hi + lo split for the sweep's column reads), the restart pair and
+// the level-0 buffers X0 [chains][n] and Y0 [chains][n] (pairs).
+sa_status setup_rot(sa_handle* h, HostProb& hp, ProbDev& d) {
+    const int n = hp.n;
+    const size_t nn = (size_t)n * n;
+    std::vector<double> qt(nn);
+    std::vector<float> qh(nn), ql(nn);
+    double qmax = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double q = hp.Q[(size_t)i * n + j];
+            qt[(size_t)j * n + i] = q;
+            qmax = std::fmax(qmax, std::fabs(q));
+        }
+    for (size_t k = 0; k < nn; ++k) {
+        qh[k] = (float)qt[k];
+        ql[k] = (float)(qt[k] - (double)qh[k]);
+    }
+    double *q64, *qt64, *rpart;
+    float *qth, *qtl, *ybh, *ybl, *x0;
+    float2* y0;
+    unsigned long long* rech;
+    unsigned int* rdone;
+    sa_status st;
+    const size_t cn = (size_t)hp.chains * n;
+    if ((st = dalloc(h, &q64, nn)) || (st = dalloc(h, &qt64, nn)) || (st = dalloc(h, &qth, nn)) ||
+        (st = dalloc(h, &qtl, nn)) || (st = dalloc(h, &ybh, n)) || (st = dalloc(h, &ybl, n)) ||
+        (st = dalloc(h, &x0, cn)) || (st = dalloc(h, &y0, cn)) || (st = dalloc(h, &rech, 1)) ||
+        (st = dalloc(h, &rdone, 1)) || (st = dalloc(h, &rpart, rot_restart_blocks(n))))
+        return st;
+    const unsigned long long z64 = 0;
+    const unsigned int z32 = 0;
+    if ((st = h2d(h, q64, hp.Q.data(), nn)) || (st = h2d(h, qt64, qt.data(), nn)) || (st = h2d(h, qth, qh.data(), nn)) ||
+        (st = h2d(h, qtl, ql.data(), nn)) || (st = h2d(h, rech, &z64, 1)) || (st = h2d(h, rdone, &z32, 1)))
+        return st;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SA_ECUDA;  // host temporaries die here
+    d.q64 = q64; d.qt64 = qt64; d.qt_hi = qth; d.qt_lo = qtl; d.ybest_hi = ybh; d.ybest_lo = ybl;
+    d.x0 = x0; d.y0 = y0; d.rechecks = rech; d.rot_done = rdone; d.rot_part = rpart;
+    float qm = (float)qmax;
+    if ((double)qm < qmax) qm = std::nextafterf(qm, INFINITY);
+    d.qmax = qm;
+    return SA_OK;
+}
+
 sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, const int32_t* ns,
                 const int64_t* chains, int32_t num) {
     sa_status st;
@@ -354,6 +429,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         h->total_x += (int64_t)hp.n * hp.chains;
         hp.lo.assign(boxes[p].lo, boxes[p].lo + hp.n);
         hp.hi.assign(boxes[p].hi, boxes[p].hi + hp.n);
+        if (is_rot(hp.cost)) hp.Q.assign(problems[p].Q, problems[p].Q + (size_t)hp.n * hp.n);
         if (hp.n > n_max) n_max = hp.n;
     }
     h->words = (h->L + 31) / 32;
@@ -367,22 +443,26 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         h->groups[0].kind = kSweepF64;
         for (int p = 0; p < P; ++p) h->groups[0].probs.push_back(p);
     } else {
-        // one group per (dimension bucket, layout-eligible) pair: the
-        // chain-per-warp layout serves costs without global running sums
+        // one group per (dimension bucket, class) pair: class 0 = thread
+        // layout only, 1 = costs the chain-per-warp layout serves (no global
+        // running sums), 2 = rotated costs (chain-per-warp rank-1 sweep)
         const int nb = (int)(sizeof(kBucketBounds) / sizeof(int));
-        std::vector<Group> b(2 * nb);
+        std::vector<Group> b(3 * nb);
         for (int p = 0; p < P; ++p) {
             int i = 0;
             while (h->probs[p].n > kBucketBounds[i]) ++i;
-            const bool eligible = warp_eligible(h->probs[p].cost);
-            b[2 * i + (eligible ? 1 : 0)].probs.push_back(p);
+            const int cls = is_rot(h->probs[p].cost) ? 2 : (warp_eligible(h->probs[p].cost) ? 1 : 0);
+            b[3 * i + cls].probs.push_back(p);
         }
-        for (int i = 0; i < 2 * nb; ++i) {
+        for (int i = 0; i < 3 * nb; ++i) {
             Group& g = b[i];
             if (g.probs.empty()) continue;
             int nmax = 1;
             for (int p : g.probs) nmax = std::max(nmax, h->probs[p].n);
-            g.kind = ((i & 1) && pick_warp_mode(h->probs[g.probs[0]].cost, nmax)) ? kSweepF32Warp : kSweepF32;
+            const int cls = i % 3;
+            g.kind = cls == 2 ? kSweepRot
+                     : (cls == 1 && pick_warp_mode(h->probs[g.probs[0]].cost, nmax)) ? kSweepF32Warp
+                                                                                     : kSweepF32;
             h->groups.push_back(g);
         }
     }
@@ -391,11 +471,13 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (Group& g : h->groups) {
         for (int p : g.probs) g.n_max = std::max(g.n_max, h->probs[p].n);
-        g.block = g.kind == kSweepF32Warp ? 256 : pick_block(h->precision, g.n_max);
+        g.block = g.kind == kSweepF32Warp ? 256 : g.kind == kSweepRot ? 32 * sweep_rot_chains_per_block()
+                                                                        : pick_block(h->precision, g.n_max);
         g.smem = group_smem(g);
         if ((int)g.smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
         if (group_set_smem(g) != cudaSuccess) return SA_ECUDA;
-        for (int p : g.probs) g.items_cap += (size_t)((h->probs[p].chains + 7) / 8);  // smallest tile: 8 chains
+        const int64_t tile = g.kind == kSweepRot ? sweep_rot_chains_per_block() : 8;  // smallest tile
+        for (int p : g.probs) g.items_cap += (size_t)((h->probs[p].chains + tile - 1) / tile);
         if ((st = dalloc(h, &g.d_items, g.items_cap))) return st;
         if (h->groups.size() > 1 &&
             (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -468,6 +550,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         d.x_best64 = xb64; d.x_best32 = xb32; d.x_inc = xinc; d.scal = scal; d.level_min = lmin; d.done = done;
         d.part_val = pval; d.part_idx = pidx; d.log_argmin = la; d.log_f = lf; d.log_finc = lfi; d.log_t = lt;
         d.accepts = acc;
+        if (is_rot(hp.cost) && (st = setup_rot(h, hp, d))) return st;
         hp.dev = d;
         pd[p] = d;
         std::vector<double> sc(kNumScalars, 0.0);
@@ -548,6 +631,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     fp = fnv(fp, &h->seed, sizeof(h->seed));
     fp = fnv(fp, &h->L, sizeof(h->L));
     for (auto& hp : h->probs) {
+        fp = fnv(fp, hp.Q.data(), hp.Q.size() * sizeof(double));
         fp = fnv(fp, &hp.cost, sizeof(hp.cost));
         fp = fnv(fp, &hp.n, sizeof(hp.n));
         fp = fnv(fp, &hp.chains, sizeof(hp.chains));
@@ -556,6 +640,17 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     }
     h->fingerprint = fp;
     return SA_OK;
+}
+
+cudaError_t launch_level0_prep(sa_handle* h, cudaStream_t s) {
+    cudaError_t e = launch_stamp_start(h->d_run, s);
+    for (size_t p = 0; p < h->probs.size() && e == cudaSuccess; ++p) {
+        const HostProb& hp = h->probs[p];
+        if (is_rot(hp.cost))
+            e = launch_rot_level0(h->d_probs + p, hp.dev, h->args, const_cast<float*>(hp.dev.x0),
+                                  const_cast<float2*>(hp.dev.y0), s);
+    }
+    return e;
 }
 
 }  // namespace
@@ -601,12 +696,9 @@ const char* sa_strerror(sa_status s) {
 sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains, int32_t L,
                     const sa_schedule* schedule, uint64_t seed, void* stream, sa_handle** out) {
     if (out) *out = nullptr;
-    if (!problem || !box || !out || !box->lo || !box->hi || n < 1 || chains < 1 || chains > 2147483647LL || L < 1)
-        return SA_EINVAL;
+    if (!problem || !box || !out || L < 1) return SA_EINVAL;
     if (check_schedule(schedule) != SA_OK) return SA_EINVAL;
-    if (problem->cost < SA_SCHWEFEL || problem->cost > SA_ROSENBROCK) return SA_EINVAL;  // rotated: not in this build yet
-    for (int k = 0; k < n; ++k)
-        if (!std::isfinite(box->lo[k]) || !std::isfinite(box->hi[k]) || box->lo[k] > box->hi[k]) return SA_EINVAL;
+    if (check_problem(*problem, *box, n, chains, *schedule) != SA_OK) return SA_EINVAL;
     sa_handle* h = new (std::nothrow) sa_handle();
     if (!h) return SA_ENOMEM;
     h->stream = static_cast<cudaStream_t>(stream);
@@ -630,7 +722,7 @@ sa_status sa_run(sa_handle* h, int32_t levels) {
     const int remaining = h->levels_total - h->levels_done;
     if (remaining <= 0) return SA_ESTATE;
     int k = (levels == -1 || levels > remaining) ? remaining : levels;
-    if (h->levels_done == 0 && launch_stamp_start(h->d_run, h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    if (h->levels_done == 0 && launch_level0_prep(h, h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
     while (k > 0) {
         cudaError_t e;
         int step;
@@ -666,7 +758,7 @@ sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* lev
             return fail(h, SA_ECUDA);
         }
     sa_status st = SA_OK;
-    if (h->levels_done == 0 && launch_stamp_start(h->d_run, h->stream) != cudaSuccess) st = SA_ECUDA;
+    if (h->levels_done == 0 && launch_level0_prep(h, h->stream) != cudaSuccess) st = SA_ECUDA;
     for (int l = 0; l < k && st == SA_OK; ++l) {
         if (cudaEventRecord(ev[3 * l], h->stream) != cudaSuccess || launch_sweep(h, h->stream) != cudaSuccess ||
             cudaEventRecord(ev[3 * l + 1], h->stream) != cudaSuccess || launch_level_tail(h, h->stream) != cudaSuccess ||
@@ -743,7 +835,7 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
     if (st != SA_OK) return st;
     const HostProb& hp = h->probs[problem];
     std::vector<double> sc(kNumScalars);
-    unsigned long long acc = 0;
+    unsigned long long acc = 0, rech = 0;
     int64_t am = -1;
     long long t0 = 0;
     h->d2h_bytes += (int64_t)(sizeof(double) * kNumScalars + sizeof(acc) + sizeof(am) + sizeof(t0) +
@@ -751,6 +843,7 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
     if (cudaMemcpyAsync(sc.data(), hp.dev.scal, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, h->stream) ||
         cudaMemcpyAsync(&t0, &h->d_run->t_start, sizeof(t0), cudaMemcpyDeviceToHost, h->stream) ||
         cudaMemcpyAsync(&acc, hp.dev.accepts, sizeof(acc), cudaMemcpyDeviceToHost, h->stream) ||
+        (hp.dev.rechecks && cudaMemcpyAsync(&rech, hp.dev.rechecks, sizeof(rech), cudaMemcpyDeviceToHost, h->stream)) ||
         cudaMemcpyAsync(&am, hp.dev.log_argmin + (h->levels_done - 1), sizeof(am), cudaMemcpyDeviceToHost, h->stream) ||
         (x_out && cudaMemcpyAsync(x_out, hp.dev.x_inc, sizeof(double) * hp.n, cudaMemcpyDeviceToHost, h->stream)) ||
         cudaStreamSynchronize(h->stream))
@@ -766,6 +859,7 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
         stt->h2d_bytes = h->h2d_bytes;
         stt->d2h_bytes = h->d2h_bytes;
         stt->t_start_ns = t0;
+        stt->rechecks = (int64_t)rech;
     }
     return SA_OK;
 }
@@ -929,6 +1023,12 @@ sa_status sa_restore(sa_handle* h, const void* buf, size_t len) {
     }
     RunDev run{done, 0};
     if (cudaMemcpy(h->d_run, &run, sizeof(run), cudaMemcpyHostToDevice)) return fail(h, SA_ECUDA);
+    // rotated costs: the next level starts from y_best = Q x_best
+    for (size_t p = 0; p < h->probs.size() && done > 0; ++p)
+        if (is_rot(h->probs[p].cost) &&
+            (launch_rot_restart(h->d_probs + p, h->probs[p].n, h->stream) != cudaSuccess ||
+             cudaStreamSynchronize(h->stream) != cudaSuccess))
+            return fail(h, SA_ECUDA);
     h->levels_done = done;
     return SA_OK;
 }
@@ -954,13 +1054,8 @@ sa_status sa_create_batch(const sa_problem* problems, const sa_box* boxes, const
     if (out) *out = nullptr;
     if (!problems || !boxes || !n || !chains || !out || num_problems < 1 || L < 1) return SA_EINVAL;
     if (check_schedule(schedule) != SA_OK) return SA_EINVAL;
-    for (int p = 0; p < num_problems; ++p) {
-        if (n[p] < 1 || chains[p] < 1 || chains[p] > 2147483647LL || !boxes[p].lo || !boxes[p].hi) return SA_EINVAL;
-        if (problems[p].cost < SA_SCHWEFEL || problems[p].cost > SA_ROSENBROCK) return SA_EINVAL;
-        for (int k = 0; k < n[p]; ++k)
-            if (!std::isfinite(boxes[p].lo[k]) || !std::isfinite(boxes[p].hi[k]) || boxes[p].lo[k] > boxes[p].hi[k])
-                return SA_EINVAL;
-    }
+    for (int p = 0; p < num_problems; ++p)
+        if (check_problem(problems[p], boxes[p], n[p], chains[p], *schedule) != SA_OK) return SA_EINVAL;
     sa_handle* h = new (std::nothrow) sa_handle();
     if (!h) return SA_ENOMEM;
     h->stream = static_cast<cudaStream_t>(stream);
@@ -1003,7 +1098,7 @@ sa_status sa_autotune(sa_handle* h, double* ms_out) {
         return h2d(h, h->d_probs, h->pd.data(), h->pd.size());
     };
     for (Group& g : h->groups) {
-        if (g.kind == kSweepF64) continue;  // one shape only
+        if (g.kind == kSweepF64 || g.kind == kSweepRot) continue;  // one shape only
         std::vector<Shape> cands;
         int last_block = -1;
         for (int budget : kBudgets) {
@@ -1058,7 +1153,7 @@ int32_t sa_describe(const sa_handle* h, char* buf, size_t len) {
         int u = g.probs.empty() ? 1 : h->pd[g.probs[0]].unroll;
         char tmp[256];
         std::snprintf(tmp, sizeof(tmp), "%s{\"kind\":\"%s\",\"problems\":%zu,\"n_max\":%d,\"block\":%d,\"smem\":%zu,\"unroll\":%d,\"items\":%zu}",
-                      i ? "," : "", g.kind == kSweepF64 ? "fp64" : (g.kind == kSweepF32Warp ? "fp32_warp" : "fp32_thread"),
+                      i ? "," : "", g.kind == kSweepF64 ? "fp64" : g.kind == kSweepF32Warp ? "fp32_warp" : g.kind == kSweepRot ? "rot_warp" : "fp32_thread",
                       g.probs.size(), g.n_max, g.block, g.smem, u, g.items.size());
         s += tmp;
     }

@@ -15,6 +15,7 @@ enum ScalarSlot : int {
     kFInc = 1,    // incumbent value
     kS1 = 2,      // Ackley: sum x_best^2 (FP64)
     kS2 = 3,      // Ackley: sum cos(2 pi x_best) (FP64)
+    kFRot = 4,    // rotated costs: F at the pair Q x_best (restart value of the next level)
     kNumScalars = 8
 };
 
@@ -50,6 +51,19 @@ struct ProbDev {
     double* log_finc;     // [levels]
     long long* log_t;     // [levels] device clock (ns) at the end of the level
     unsigned long long* accepts;  // running count of accepted moves
+    // rotated costs f(x) = F(Q x) (NULL otherwise)
+    const double* q64;    // [n][n] Q row-major (FP64)
+    const double* qt64;   // [n][n] Q transposed: qt64[d * n + i] = Q[i][d]
+    const float* qt_hi;   // [n][n] FP32 part of qt64
+    const float* qt_lo;   // [n][n] FP32 remainder: qt64 - qt_hi rounded to FP32
+    float* ybest_hi;      // [n] Q x_best as a double-float pair (hi + lo)
+    float* ybest_lo;      // [n]
+    const float* x0;      // [chains][n] level-0 states (FP32)
+    const float2* y0;     // [chains][n] Q x0 as (hi, lo) pairs
+    unsigned long long* rechecks;  // running count of FP64 re-checked decisions
+    unsigned int* rot_done;  // last-block-done counter of the restart transform
+    double* rot_part;     // [ceil(n / 128)] its partial sums
+    float qmax;           // max |Q_ij| rounded up to FP32
 };
 
 // Device-resident run state shared by all problems of a handle.
@@ -109,6 +123,15 @@ int* gemm_status_ptr();
 cudaError_t launch_gather(const float* X32, const double* X64, int64_t x_base, int64_t chains, int n, const int64_t* idx,
                           int k, double* out, cudaStream_t s);
 cudaError_t launch_polish_update(ProbDev* probs, int problem, const double* xs, const double* fs, int k, cudaStream_t s);
+
+cudaError_t launch_sweep_rot(const SweepArgs& a, int num_items, size_t smem, cudaStream_t s);
+size_t sweep_rot_smem_bytes(int n);
+cudaError_t sweep_rot_set_smem(size_t bytes);
+int sweep_rot_chains_per_block();
+cudaError_t launch_rot_restart(const ProbDev* d_prob, int n, cudaStream_t s);
+int rot_restart_blocks(int n);
+cudaError_t launch_rot_level0(const ProbDev* d_prob, const ProbDev& host_prob, const SweepArgs& a, float* x0, float2* y0,
+                              cudaStream_t s);
 
 constexpr int kArgminThreads = 256;
 constexpr int kArgminPerThread = 8;

@@ -58,3 +58,8 @@ SCHWEFEL_N2_FP64 = dict(cost="schwefel", n=2, chains=1024, L=100, levels=50, T0=
                         sigma_frac=0.1, precision="fp64", seed=0)
 SCHWEFEL_N256_FP32 = dict(cost="schwefel", n=256, chains=262144, L=1000, levels=200, T0=100.0, rho=0.95,
                           sigma_frac=0.1, precision="fp32", seed=0)
+# Rotated costs: Q = rotation(n, q_seed).
+ROT_RASTRIGIN_N1024 = dict(cost="rot_rastrigin", n=1024, chains=65536, L=500, levels=100, T0=100.0, rho=0.95,
+                           sigma_frac=0.1, precision="fp32", seed=0, q_seed=0)
+ROT_SCHWEFEL_N128 = dict(cost="rot_schwefel", n=128, chains=131072, L=2000, levels=150, T0=100.0, rho=0.95,
+                         sigma_frac=0.1, precision="fp32", seed=0, q_seed=0)

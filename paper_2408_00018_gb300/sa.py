@@ -46,7 +46,8 @@ class _Schedule(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("accepts", ctypes.c_int64), ("levels_done", ctypes.c_int32),
                 ("levels_total", ctypes.c_int32), ("f_level", ctypes.c_double), ("argmin", ctypes.c_int64),
-                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("t_start_ns", ctypes.c_int64)]
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
+                ("rechecks", ctypes.c_int64)]
 
 
 _lib = None
@@ -306,14 +307,15 @@ class BatchHandle(Handle):
 
 
 def create_batch(problems, L, schedule: Schedule | None = None, seed: int = 0, stream=None) -> BatchHandle:
-    """sa_create_batch: problems is a list of dicts with cost, n, chains, lo, hi."""
+    """sa_create_batch: problems is a list of dicts with cost, n, chains, lo, hi (and Q for rotated costs)."""
     lib = load()
     schedule = schedule or Schedule()
     P = len(problems)
     los = [np.ascontiguousarray(np.broadcast_to(np.asarray(p["lo"], np.float64), (p["n"],))) for p in problems]
     his = [np.ascontiguousarray(np.broadcast_to(np.asarray(p["hi"], np.float64), (p["n"],))) for p in problems]
-    probs = (_Problem * P)(*[_Problem(COSTS[p["cost"]] if isinstance(p["cost"], str) else int(p["cost"]), None)
-                            for p in problems])
+    Qs = [None if p.get("Q") is None else np.ascontiguousarray(p["Q"], dtype=np.float64) for p in problems]
+    probs = (_Problem * P)(*[_Problem(COSTS[p["cost"]] if isinstance(p["cost"], str) else int(p["cost"]),
+                                      None if q is None else q.ctypes.data) for p, q in zip(problems, Qs)])
     boxes = (_Box * P)(*[_Box(lo.ctypes.data, hi.ctypes.data) for lo, hi in zip(los, his)])
     ns = np.array([p["n"] for p in problems], np.int32)
     cs = np.array([p["chains"] for p in problems], np.int64)
