@@ -36,9 +36,24 @@ MUFU_PER_CLK_SM = 16
 # log2 (tau = -T ln u3); the energy difference the transcendental terms of the
 # new coordinate value only (the old one's term can be kept): Schwefel sqrt +
 # sin, Rastrigin cos, Ackley cos + sqrt + 2 exp, Rosenbrock none.
+# Rotated costs: every rotated coordinate changes, so n transcendental terms
+# per step (Rastrigin: one sine per coordinate in the product-to-sum form;
+# Schwefel: sqrt and sine of the new term) plus the 4 of the proposal and test.
 SFU_PER_STEP = {"schwefel": 6, "rastrigin": 5, "ackley": 8, "rosenbrock": 4}
-SWEEP_SOURCES = ["sweep_f32.cu", "sweep_f32w.cu", "sa_device.cuh", "sa_internal.h"]
-WORKLOADS = ("schwefel_n256", "schwefel_n2", "batched")
+
+
+def sfu_per_step(cost, n):
+    if cost == "rot_rastrigin":
+        return n + 4
+    if cost == "rot_schwefel":
+        return 2 * n + 4
+    return SFU_PER_STEP[cost]
+
+
+SWEEP_SOURCES = ["sweep_f32.cu", "sweep_f32w.cu", "sweep_rot.cu", "sa_device.cuh", "sa_internal.h"]
+WARMUP_MIN_S = 4.0
+WORKLOADS = ("schwefel_n256", "schwefel_n2", "batched", "rot_rastrigin_n1024", "rot_schwefel_n128")
+ROT_WORKLOADS = {"rot_rastrigin_n1024": "ROT_RASTRIGIN_N1024", "rot_schwefel_n128": "ROT_SCHWEFEL_N128"}
 
 
 def parse():
@@ -60,16 +75,21 @@ class Workload:
     def __init__(self, name, levels_override=0):
         from paper_2408_00018_gb300 import inputs
         self.name = name
-        if name in ("schwefel_n256", "schwefel_n2"):
-            cfg = dict(inputs.SCHWEFEL_N256_FP32 if name == "schwefel_n256" else inputs.SCHWEFEL_N2_FP64)
+        if name in ("schwefel_n256", "schwefel_n2") or name in ROT_WORKLOADS:
+            if name in ROT_WORKLOADS:
+                cfg = dict(getattr(inputs, ROT_WORKLOADS[name]))
+            else:
+                cfg = dict(inputs.SCHWEFEL_N256_FP32 if name == "schwefel_n256" else inputs.SCHWEFEL_N2_FP64)
             if levels_override:
                 cfg["levels"] = levels_override
             lo, hi = inputs.box(cfg["cost"], cfg["n"])
-            self.problems = [{"cost": cfg["cost"], "n": cfg["n"], "chains": cfg["chains"], "lo": lo, "hi": hi}]
+            Q = inputs.rotation(cfg["n"], cfg["q_seed"]) if "q_seed" in cfg else None
+            self.problems = [{"cost": cfg["cost"], "n": cfg["n"], "chains": cfg["chains"], "lo": lo, "hi": hi, "Q": Q}]
             self.L, self.K, self.T0, self.rho = cfg["L"], cfg["levels"], cfg["T0"], cfg["rho"]
             self.sigma_frac, self.precision, self.seed = cfg["sigma_frac"], cfg["precision"], cfg["seed"]
             self.batch = False
-            self.tag = (f"schwefel_n{cfg['n']}_c{cfg['chains']}_L{cfg['L']}_K{cfg['levels']}_{cfg['precision']}")
+            self.tag = (f"{cfg['cost']}_n{cfg['n']}_c{cfg['chains']}_L{cfg['L']}_K{cfg['levels']}_{cfg['precision']}"
+                        + (f"_Q{cfg['q_seed']}" if Q is not None else ""))
         else:  # 512 independent problems of uneven n and chain count
             self.problems = inputs.batch_problems(count=512, seed=0)
             self.L, self.K = 500, levels_override or 100
@@ -77,8 +97,9 @@ class Workload:
             self.batch = True
             self.tag = f"batched512_L500_K{self.K}_fp32_autotuned"
         self.steps_per_run = sum(p["chains"] for p in self.problems) * self.L * self.K
-        self.sfu_per_level = sum(p["chains"] * self.L * SFU_PER_STEP[p["cost"]] for p in self.problems)
-        self.f_star = [inputs.F_STAR[p["cost"]] for p in self.problems]
+        self.sfu_per_level = sum(p["chains"] * self.L * sfu_per_step(p["cost"], p["n"]) for p in self.problems)
+        self.f_star = [inputs.F_STAR.get(p["cost"]) for p in self.problems]
+        self.rotated = [p["cost"].startswith("rot_") for p in self.problems]
 
     def schedule(self, sa):
         return sa.Schedule(T0=self.T0, rho=self.rho, levels=self.K, sigma_frac=self.sigma_frac,
@@ -91,11 +112,15 @@ class Workload:
                 h.autotune()
             return h
         p = self.problems[0]
-        return sa.create(p["cost"], p["lo"], p["hi"], p["n"], p["chains"], self.L, self.schedule(sa), seed=self.seed)
+        return sa.create(p["cost"], p["lo"], p["hi"], p["n"], p["chains"], self.L, self.schedule(sa), seed=self.seed,
+                         Q=p.get("Q"))
 
     def launches_per_run(self, h):
         groups = len(h.describe())
-        return 1 + self.K * (groups + 2)  # start stamp + per level (group sweeps, argmin/restart, level advance)
+        rot = sum(self.rotated)
+        # start stamp (+ initial points and Y0 = X0 Q^T per rotated problem), then per level the
+        # group sweeps, the argmin/restart, the restart transform per rotated problem, the level advance
+        return 1 + 2 * rot + self.K * (groups + 2 + rot)
 
     def config(self):
         c = {"workload": self.tag, "L": self.L, "levels": self.K, "T0": self.T0, "rho": self.rho, "seed": self.seed,
@@ -107,6 +132,8 @@ class Workload:
         else:
             p = self.problems[0]
             c.update({"cost": p["cost"], "n": p["n"], "chains": p["chains"]})
+            if p.get("Q") is not None:
+                c["Q"] = "Q factor of a seeded N(0,1) matrix (inputs.rotation)"
         return c
 
 
@@ -164,28 +191,31 @@ def gpu_id_for(dev: int) -> str:
 
 
 # ------------------------------------------------------------------ helpers
-def sweep_source_hash() -> str:
+def source_hash(files) -> str:
     h = hashlib.sha256()
-    for f in SWEEP_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2408_00018_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def traffic_from_profile(workload):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on this source."""
+    """DRAM bytes per sweep launch from the committed ncu summary, if the profiled
+    kernel's source files are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     try:
         d = json.load(open(p)).get(workload)
+        if not d or d.get("src_sha") != source_hash(d.get("files", SWEEP_SOURCES)):
+            return None
     except Exception:
-        return None
-    if not d or d.get("src_sha") != sweep_source_hash():
         return None
     return d.get("dram_bytes_per_launch")
 
 
 def time_to_target(logs, t_start_ns, f_stars):
     """Per problem: first level whose incumbent is within 1e-6 max(1, |f*|) of f*."""
+    if any(fs is None for fs in f_stars):
+        return {"reached": None, "note": "no closed-form minimum for this cost (rotated Schwefel in a box)"}
     reached, last_t, gaps = 0, 0.0, []
     for log, fs in zip(logs, f_stars):
         tol = 1e-6 * max(1.0, abs(fs))
@@ -221,7 +251,8 @@ def oracle_sample(w, budget_steps, threads):
             chains = max(1, (budget_steps - done) // (w.L * levels))
             steps = chains * w.L * levels
         op = oracle.Problem(p["cost"], p["n"], p["lo"], p["hi"], chains=chains, L=w.L, T0=w.T0, rho=w.rho,
-                            sigma_frac=w.sigma_frac, seed=w.seed, problem=p_idx, mode=mode, threads=threads)
+                            sigma_frac=w.sigma_frac, seed=w.seed, problem=p_idx, mode=mode, threads=threads,
+                            Q=p.get("Q"))
         op.run(levels)
         done += steps
         descr.append(p_idx)
@@ -253,10 +284,14 @@ def run_ours(args, rank, world, local_rank):
     h = w.create(sa)
     groups = h.describe()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-    for _ in range(args.warmup):
+    # W warm-up runs, continued until at least WARMUP_MIN_S of device work has
+    # passed: the first seconds of work after idle run ~20% slower on this GPU.
+    t_warm, warm_runs = time.perf_counter(), 0
+    while warm_runs < args.warmup or time.perf_counter() - t_warm < WARMUP_MIN_S:
         h.reset()
         h.run()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        warm_runs += 1
     if world > 1:
         torch.distributed.barrier()
 
@@ -333,7 +368,8 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        v, dt, what = oracle_sample(w, 5.3e8 if not w.batch else 3e8, threads)
+        budget = 3e8 if w.batch else 5.3e8 / (w.problems[0]["n"] / 4 if any(w.rotated) else 1)
+        v, dt, what = oracle_sample(w, budget, threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": what}
 
     if rank == 0:
@@ -342,9 +378,10 @@ def run_ours(args, rank, world, local_rank):
                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f32",
                "data": "synthetic",
                "config": dict(w.config(), parallelism=f"replicas{world}", l2="flushed between runs (256 MiB write)",
-                              launch_groups=groups),
+                              launch_groups=groups, warmup_runs=warm_runs, warmup_min_s=WARMUP_MIN_S),
                "time_to_target": ttt, "best_f": bests[0][1] if len(bests) == 1 else None,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "fp64_rechecks_per_step": (bests[0][2]["rechecks"] / bests[0][2]["steps"]) if any(w.rotated) else None,
                "gpu_launches": launches * args.steps}
         print(json.dumps(out), flush=True)
 
@@ -355,7 +392,7 @@ def run_reference(args, rank, world):
         return
     w = Workload(args.workload, args.levels)
     threads = os.cpu_count() or 1
-    budget = 6.5e7
+    budget = 6.5e7 / (w.problems[0]["n"] / 4 if any(w.rotated) else 1)
     for _ in range(args.warmup):
         oracle_sample(w, budget, threads)
     total_steps, total_s, what = 0, 0.0, ""

@@ -4,7 +4,7 @@
  * implementation of parallel simulated annealing algorithm in GPUs").
  *
  * The problem (Eq. 1):  minimise f(x) over the box I = prod_k [l_k, u_k].
- * The method (Sec. 3.2.2, Listings 3-4): C Markov chains each run L
+ * The method (Sec. 2.2.2, Listings 3-4): C Markov chains each run L
  * Metropolis steps at the temperature of the current level; a reduction then
  * finds the chain with the lowest f, every chain restarts from it, and the
  * temperature is cooled geometrically, T <- rho T (Sec. 2.1, Step 5).
@@ -281,7 +281,7 @@ sa_status sa_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uin
                          uint32_t key1, int64_t count, uint32_t* d_out, void* stream);
 
 /*
- * Kernel-level entry point: the reduction of Sec. 3.2.2 on its own.  Finds
+ * Kernel-level entry point: the reduction of Sec. 2.2.2 on its own.  Finds
  * p = argmin_c d_F[c] over c < count (lowest index among equal values; NaN
  * never wins) and writes it to *d_index and d_F[p] to *d_value (device).
  * d_scratch: device, >= sa_argmin_scratch_bytes(count) bytes, caller-owned.

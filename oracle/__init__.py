@@ -4,7 +4,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench
 may import this package.  It shares no code with the CUDA library: the C source
 ``sa_oracle.c`` is compiled on its own with gcc (``-ffp-contract=off``) and loaded
 through ctypes.  Every function follows the paper's algorithm step by step
-(Sec. 2.1 Steps 1-5, Sec. 3.2.2, Listings 3-4); see the header of ``sa_oracle.c``
+(Sec. 2.1 Steps 1-5, Sec. 2.2.2, Listings 3-4); see the header of ``sa_oracle.c``
 for the readings taken where the paper is silent.
 
 Pins: the tests under ``tests/test_oracle_*.py`` check this oracle against

@@ -14,7 +14,7 @@
  *     (Sec. 2.1 Steps 2-3, Eq. "proba", k_b = 1)
  *   - at the end of every level a reduction picks the chain with the lowest
  *     final f; all chains restart from it and T is cooled geometrically
- *     T <- rho T  (Sec. 3.2.2 synchronous approach; Listings 3-4; Sec. 2.1 Step 5)
+ *     T <- rho T  (Sec. 2.2.2 synchronous approach; Listings 3-4; Sec. 2.1 Step 5)
  *
  * Readings where the paper is silent (each one is also a pinned test):
  *   - randomness: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), one
@@ -404,7 +404,7 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
             else memcpy(x, out->x_best, sizeof(double) * (size_t)n);
             F[c] = sao_chain_level(cfg, level, c, x, bits ? bits + (size_t)c * words : NULL, &A[c]);
         }
-        /* Reduction over the chains' final values, lowest index on ties (Sec. 3.2.2). */
+        /* Reduction over the chains' final values, lowest index on ties (Sec. 2.2.2). */
         int64_t p = 0;
         int64_t acc = 0;
         for (int64_t c = 0; c < C; ++c) {

@@ -1,4 +1,4 @@
-// reduce.cu -- the synchronisation step of the synchronous approach (Sec. 3.2.2,
+// reduce.cu -- the synchronisation step of the synchronous approach (Sec. 2.2.2,
 // Listing 3): argmin over the chains' final values with the lowest index
 // winning ties, restart of every chain from the winner, incumbent update and
 // the per-level log.  One grid per level: blockIdx.y = problem; each block
