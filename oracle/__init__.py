@@ -83,6 +83,10 @@ def lib():
             L.sao_chain_level.restype = f64
             L.sao_chain_level_steps.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, vp, vp, vp, vp]
             L.sao_chain_level_steps.restype = f64
+            L.sao_da_chain_level.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp]
+            L.sao_da_chain_level.restype = f64
+            L.sao_da_chain_level_fn.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, f64, vp, vp, vp]
+            L.sao_da_chain_level_fn.restype = f64
             L.sao_run.argtypes = [ctypes.POINTER(Cfg), ctypes.POINTER(Out)]
             L.sao_run.restype = ctypes.c_int
             L.sao_level_chains.argtypes = [ctypes.POINTER(Cfg), i32, vp, i64, i64, vp, vp, vp, vp]
@@ -188,6 +192,33 @@ class Problem:
         tau = np.zeros(self.L)
         F = lib().sao_chain_level_steps(ctypes.byref(cfg), level, c, _p(x), _p(bits), _p(acc), _p(dF), _p(tau))
         return F, x, bits, dF, tau
+
+    def da_chain_level(self, level, c, ft0, ft_prop, x_start=None):
+        """One chain, one level of delayed acceptance with given surrogate values
+        (ft0 at the start state, ft_prop[s] at step s's proposal); returns
+        (F_end, x_end, bits, accepts, true_evaluations)."""
+        cfg = self.cfg()
+        x = self.init_point(c) if x_start is None else np.array(x_start, np.float64)
+        ftp = np.ascontiguousarray(ft_prop, np.float64)
+        assert ftp.size == self.L
+        bits = np.zeros((self.L + 31) // 32, np.uint32)
+        acc = np.zeros(1, np.int64)
+        ev = np.zeros(1, np.int64)
+        F = lib().sao_da_chain_level(ctypes.byref(cfg), level, c, _p(x), float(ft0), _p(ftp), _p(bits), _p(acc),
+                                     _p(ev))
+        return F, x, bits, int(acc[0]), int(ev[0])
+
+    def da_chain_level_fn(self, level, c, a, b, x_start=None):
+        """Delayed acceptance with the analytic surrogate a f(x) + b sum_i sin(x_i);
+        returns (F_end, x_end, bits, accepts, true_evaluations)."""
+        cfg = self.cfg()
+        x = self.init_point(c) if x_start is None else np.array(x_start, np.float64)
+        bits = np.zeros((self.L + 31) // 32, np.uint32)
+        acc = np.zeros(1, np.int64)
+        ev = np.zeros(1, np.int64)
+        F = lib().sao_da_chain_level_fn(ctypes.byref(cfg), level, c, _p(x), float(a), float(b), _p(bits), _p(acc),
+                                        _p(ev))
+        return F, x, bits, int(acc[0]), int(ev[0])
 
     def level_chains(self, level, c0, c1, x_start=None, want_x=False, trace=False):
         """One level for chains [c0, c1); returns dict of per-chain results."""

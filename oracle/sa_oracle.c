@@ -281,8 +281,43 @@ static double f_from_gsum(int32_t cost, int n, double s) {
  * On return x holds the final state and the function returns f(x) recomputed
  * from the definition.  bits (may be NULL) receives the accept decisions.
  */
+/*
+ * Delayed acceptance (Christen & Fox 2005; not in the paper): when ft_prop is
+ * given, ft_prop[s] is the surrogate's value at step s's proposal and ft0 its
+ * value at the level's start state.  Stage 1 passes with probability
+ * min(1, exp(-dFs / T)), dFs = ft(x') - ft(x), drawn with word 0 of the Philox
+ * block (s, level, chain, problem) of stream tag 3; only then is the true dF
+ * evaluated, and the move is accepted with probability
+ * min(1, exp(-(dF - dFs) / T)) drawn with the sweep stream's u3.
+ * n_true (may be NULL) counts the true evaluations.
+ */
+typedef struct {
+    int kind;              /* 0: none; 1: table (ft0, ft_prop); 2: a f(x) + b sum_i sin(x_i) */
+    double ft0;
+    const double* ft_prop;
+    double a, b;
+} sao_da;
+
+static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
+                             uint32_t* bits, int64_t* n_accept, double* dF_out, double* tau_out,
+                             const sao_da* da, int64_t* n_true);
+
 static double chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
                           uint32_t* bits, int64_t* n_accept, double* dF_out, double* tau_out) {
+    return chain_level_da(cfg, level, c, x, bits, n_accept, dF_out, tau_out, NULL, NULL);
+}
+
+/* The analytic test surrogate a f(x) + b sum_i sin(x_i), in full. */
+static double da_fn(const sao_cfg* cfg, const sao_da* da, const double* x, double* ywork) {
+    double s = 0.0;
+    for (int i = 0; i < cfg->n; ++i) s += sin(x[i]);
+    return da->a * sao_cost_ws(cfg->cost, cfg->n, x, cfg->Q, ywork) + da->b * s;
+}
+
+static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
+                             uint32_t* bits, int64_t* n_accept, double* dF_out, double* tau_out,
+                             const sao_da* da, int64_t* n_true) {
+    double* ywork = (cfg->cost >= SAO_ROT_RASTRIGIN) ? (double*)malloc(sizeof(double) * (size_t)cfg->n) : NULL;
     const int n = cfg->n;
     const double T = sao_temperature(cfg->T0, cfg->rho, level);
     const double s_l = sqrt(T / cfg->T0);
@@ -294,7 +329,10 @@ static double chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* 
     if (cfg->mode == 1 && cfg->cost == SAO_ACKLEY)
         for (int i = 0; i < n; ++i) { S1 += x[i] * x[i]; S2 += cos(2.0 * M_PI * x[i]); }
     if (cfg->mode == 1 && rot) G = gsum(cfg->cost, n, y); /* y = Q x from the call above */
-    int64_t acc = 0;
+    int64_t acc = 0, evals = 0;
+    const int use_da = da && da->kind != 0;
+    double ft_cur = !use_da ? 0.0 : (da->kind == 1 ? da->ft0 : da_fn(cfg, da, x, ywork));
+    double ft_new = 0.0;
     const int words = (cfg->L + 31) / 32;
     if (bits) memset(bits, 0, sizeof(uint32_t) * (size_t)words);
 
@@ -308,6 +346,27 @@ static double chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* 
         const double sigma = cfg->sigma_frac * (cfg->hi[d] - cfg->lo[d]) * s_l;
         const double xd = x[d];
         const double xp = apply_box(xd + sigma * z, cfg->lo[d], cfg->hi[d], cfg->boundary);
+
+        /* Delayed acceptance, stage 1 (surrogate only). */
+        double dFs = 0.0;
+        if (use_da) {
+            uint32_t wd[4];
+            sao_block(cfg->seed, SAO_TAG_DA, (uint32_t)s, (uint32_t)level, (uint32_t)c, cfg->problem, wd);
+            if (da->kind == 1) {
+                ft_new = da->ft_prop[s];
+            } else {
+                x[d] = xp;
+                ft_new = da_fn(cfg, da, x, ywork);
+                x[d] = xd;
+            }
+            dFs = ft_new - ft_cur;
+            if (!(dFs <= 0.0 || sao_uniform(wd[0]) < exp(-dFs / T))) {
+                if (dF_out) dF_out[s] = NAN;
+                if (tau_out) tau_out[s] = NAN;
+                continue;
+            }
+        }
+        ++evals;
 
         /* Step 3: energy difference. */
         double dF, Fp = 0.0, S1p = 0.0, S2p = 0.0, Gp = 0.0;
@@ -336,13 +395,16 @@ static double chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* 
             dF = f_from_gsum(cfg->cost, n, Gp) - f_from_gsum(cfg->cost, n, G);
         }
 
-        /* Metropolis criterion, Eq. "proba" with k_b = 1. */
-        const int accept = (dF <= 0.0) || (u3 < exp(-dF / T));
+        /* Metropolis criterion, Eq. "proba" with k_b = 1 (stage 2 of delayed
+         * acceptance: the same test on dF - dFs). */
+        const double dFa = dF - dFs;
+        const int accept = (dFa <= 0.0) || (u3 < exp(-dFa / T));
         if (dF_out) dF_out[s] = dF;
         if (tau_out) tau_out[s] = -T * log(u3); /* the same test written as dF < tau */
         if (accept) {
             x[d] = xp;
             ++acc;
+            if (use_da) ft_cur = ft_new;
             if (bits) bits[s >> 5] |= 1u << (s & 31);
             if (cfg->mode == 0) {
                 F = Fp;
@@ -356,8 +418,24 @@ static double chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* 
     double Fend = sao_cost_ws(cfg->cost, n, x, cfg->Q, yp ? yp : y);
     free(y);
     free(yp);
+    free(ywork);
     if (n_accept) *n_accept = acc;
+    if (n_true) *n_true = evals;
     return Fend;
+}
+
+/* One chain, one level of delayed acceptance with the surrogate values given. */
+double sao_da_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double ft0,
+                          const double* ft_prop, uint32_t* bits, int64_t* n_accept, int64_t* n_true) {
+    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0};
+    return chain_level_da(cfg, level, c, x, bits, n_accept, NULL, NULL, &da, n_true);
+}
+
+/* The same with the analytic test surrogate a f(x) + b sum_i sin(x_i). */
+double sao_da_chain_level_fn(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double a, double b,
+                             uint32_t* bits, int64_t* n_accept, int64_t* n_true) {
+    const sao_da da = {2, 0.0, NULL, a, b};
+    return chain_level_da(cfg, level, c, x, bits, n_accept, NULL, NULL, &da, n_true);
 }
 
 double sao_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
