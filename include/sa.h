@@ -77,11 +77,14 @@ typedef struct {
     double sigma_frac;  /* Gaussian step sigma = sigma_frac (u_d - l_d) sqrt(T / T0), > 0 */
     int32_t boundary;   /* SA_REFLECT (reflect once, then clip) or SA_CLIP */
     int32_t precision;  /* SA_FP64 or SA_FP32 (state in FP32, argmin in FP64) */
-    int32_t surrogate;  /* reserved, must be 0 */
+    int32_t surrogate;  /* 0: Metropolis; 1: delayed acceptance with the learned surrogate
+                           (rotated costs, SA_FP32, sa_create only; see sa_da_trace) */
     int32_t polish_k;   /* hybrid SA: after the last level, polish the polish_k best final
                            states (0..1024) with sa_polish's method; the best polished point
                            becomes the incumbent if it is lower (0 = off) */
     int32_t trace_levels; /* record accept bits of the first trace_levels levels (0 = off) */
+    int32_t cost_repeat;  /* rotated costs: evaluate each energy difference this many times
+                             (0 or 1 = once; more only to emulate a costlier f, results unchanged) */
 } sa_schedule;
 
 typedef struct {
@@ -95,6 +98,7 @@ typedef struct {
     int64_t d2h_bytes;    /* bytes this handle copied device -> host so far */
     int64_t t_start_ns;   /* device clock (ns) when level 0 of the current run started */
     int64_t rechecks;     /* rotated costs: decisions re-taken in FP64 so far (0 otherwise) */
+    int64_t true_evals;   /* energy differences of f evaluated (= steps unless delayed acceptance) */
 } sa_stats;
 
 typedef struct sa_handle sa_handle;
@@ -223,6 +227,26 @@ sa_status sa_trace(sa_handle* h, int32_t level, uint32_t* bits_out, size_t nword
 sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_out);
 
 /*
+ * Delayed acceptance (schedule.surrogate == 1; an extension, the paper has no
+ * surrogate).  Each step, every chain's proposal x' first passes stage 1 with
+ * probability min(1, exp(-(f~(x') - f~(x)) / T)) on the surrogate f~ (Christen
+ * & Fox 2005), drawn from word 0 of the Philox block (step, level, chain,
+ * problem) of stream tag 3; only survivors have their true difference dF
+ * evaluated, and are accepted with probability min(1, exp(-(dF - (f~(x') -
+ * f~(x))) / T)) using the sweep's u3.  f~ = mu + sigma MLP((x - mid) / half),
+ * the network of sa_mlp_*, is re-initialised at level 0 of every run (seed of
+ * the handle), trained before each later level by 128 Adam steps (batches of
+ * 4096 drawn from a ring buffer of the last ~2^20 chain states -- taken 4 times
+ * per level, evenly spaced -- and their values, targets standardised by the
+ * buffer's mean and deviation) and frozen
+ * during the level.  sa_da_trace returns, for a traced completed level, the
+ * surrogate's value at every chain's start state (ft0_out: host [chains]) and
+ * at every proposal (ftp_out: host [L * chains], step-major); either may be
+ * NULL.  Checkpoints are not available for such handles (SA_EINVAL).
+ */
+sa_status sa_da_trace(sa_handle* h, int32_t level, float* ft0_out, float* ftp_out);
+
+/*
  * Serialise the state between levels (restart point, incumbent, level index,
  * counters) into buf.  With buf == NULL, *len receives the size needed.
  * Errors: SA_EINVAL if *len is too small.  Synchronises.
@@ -270,6 +294,33 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
  */
 sa_status sa_gemm_bf16(const void* d_A, int32_t lda, const void* d_B, int32_t ldb, float* d_D, int32_t ldd,
                        int32_t M, int32_t N, int32_t K, int32_t* d_status, void* stream);
+
+/*
+ * The learned surrogate of the delayed-acceptance sweep (an extension: the
+ * paper has no surrogate):  f~(x) = w3 . g(W2 g(W1 x + b1) + b2) + b3 with
+ * g(z) = z Phi(z) (erf-form GELU) and hidden widths 512 and 512, fitted to
+ * the mean squared error (1/2B) sum_b (f~(x_b) - t_b)^2 with Adam (Kingma & Ba,
+ * ICLR 2015).  Parameters are one FP32 device vector of sa_mlp_param_count(n)
+ * elements laid out W1 [512 x n] (row-major), b1 [512], W2 [512 x 512],
+ * b2 [512], w3 [512], b3 [1].  The matrix products run on the tensor cores
+ * (BF16 operands, FP32 accumulation); everything else in FP32.
+ *   sa_mlp_param_count  number of parameters (-1 if n < 1)
+ *   sa_mlp_init         He-normal weights from Philox (stream tag 2 of seed), zero biases
+ *   sa_mlp_forward      d_y[b] = f~(d_X[b]) for B rows of d_X [B x n] (FP32, device)
+ *   sa_mlp_loss_grad    d_grad = dL/dparams, *d_loss = L (FP32 device scalar, may be NULL)
+ *   sa_mlp_adam         one Adam step at step >= 1: moments d_m, d_v (device, count each) updated
+ * All are asynchronous on `stream`; forward and loss_grad allocate their
+ * workspace stream-ordered.  Errors: SA_EINVAL on NULL pointers, n not in
+ * [1, 4096], B < 1, count < 1, step < 1 or hyper-parameters out of range;
+ * SA_ENOMEM; SA_ECUDA.
+ */
+int64_t sa_mlp_param_count(int32_t n);
+sa_status sa_mlp_init(float* d_params, int32_t n, uint64_t seed, void* stream);
+sa_status sa_mlp_forward(const float* d_params, int32_t n, const float* d_X, int32_t B, float* d_y, void* stream);
+sa_status sa_mlp_loss_grad(const float* d_params, int32_t n, const float* d_X, const float* d_t, int32_t B,
+                           float* d_grad, float* d_loss, void* stream);
+sa_status sa_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t count, int32_t step,
+                      float lr, float beta1, float beta2, float eps, void* stream);
 
 /*
  * Kernel-level entry point: Philox4x32-10 (Salmon et al., SC'11) blocks for

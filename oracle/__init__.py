@@ -85,6 +85,8 @@ def lib():
             L.sao_chain_level_steps.restype = f64
             L.sao_da_chain_level.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp]
             L.sao_da_chain_level.restype = f64
+            L.sao_da_chain_level_steps.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp, vp]
+            L.sao_da_chain_level_steps.restype = f64
             L.sao_da_chain_level_fn.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, f64, vp, vp, vp]
             L.sao_da_chain_level_fn.restype = f64
             L.sao_run.argtypes = [ctypes.POINTER(Cfg), ctypes.POINTER(Out)]
@@ -207,6 +209,20 @@ class Problem:
         F = lib().sao_da_chain_level(ctypes.byref(cfg), level, c, _p(x), float(ft0), _p(ftp), _p(bits), _p(acc),
                                      _p(ev))
         return F, x, bits, int(acc[0]), int(ev[0])
+
+    def da_chain_level_steps(self, level, c, ft0, ft_prop, x_start=None):
+        """As da_chain_level, also returning dF [L]: each step's true difference (NaN
+        where stage 1 rejected the move)."""
+        cfg = self.cfg()
+        x = self.init_point(c) if x_start is None else np.array(x_start, np.float64)
+        ftp = np.ascontiguousarray(ft_prop, np.float64)
+        bits = np.zeros((self.L + 31) // 32, np.uint32)
+        acc = np.zeros(1, np.int64)
+        ev = np.zeros(1, np.int64)
+        dF = np.zeros(self.L)
+        F = lib().sao_da_chain_level_steps(ctypes.byref(cfg), level, c, _p(x), float(ft0), _p(ftp), _p(bits), _p(acc),
+                                           _p(ev), _p(dF))
+        return F, x, bits, int(acc[0]), int(ev[0]), dF
 
     def da_chain_level_fn(self, level, c, a, b, x_start=None):
         """Delayed acceptance with the analytic surrogate a f(x) + b sum_i sin(x_i);

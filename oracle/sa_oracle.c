@@ -431,6 +431,15 @@ double sao_da_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* 
     return chain_level_da(cfg, level, c, x, bits, n_accept, NULL, NULL, &da, n_true);
 }
 
+/* The same, also returning each step's true difference dF_out[s] (NaN where
+ * stage 1 rejected the move and f was not evaluated). */
+double sao_da_chain_level_steps(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double ft0,
+                                const double* ft_prop, uint32_t* bits, int64_t* n_accept, int64_t* n_true,
+                                double* dF_out) {
+    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0};
+    return chain_level_da(cfg, level, c, x, bits, n_accept, dF_out, NULL, &da, n_true);
+}
+
 /* The same with the analytic test surrogate a f(x) + b sum_i sin(x_i). */
 double sao_da_chain_level_fn(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double a, double b,
                              uint32_t* bits, int64_t* n_accept, int64_t* n_true) {

@@ -31,6 +31,8 @@ UNITS = {
     "gemm_tc.cu": [],
     "sweep_rot.cu": [],
     "rot_prep.cu": [],
+    "mlp.cu": [],
+    "da.cu": [],
 }
 
 

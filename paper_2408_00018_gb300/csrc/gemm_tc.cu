@@ -30,6 +30,9 @@ constexpr uint32_t kSpin = 1u << 20;  // bounded waits (each try_wait itself blo
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// GELU, erf form: z Phi(z) = z/2 (1 + erf(z / sqrt 2)).
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -216,6 +219,51 @@ struct EpiStoreF32 {
     }
 };
 
+// Surrogate layer: z = acc + bias; stores gelu(z) as BF16 (and z as FP32 when Z != nullptr).
+struct EpiBiasGelu {
+    const float* bias;
+    __nv_bfloat16* A;
+    int lda;
+    float* Z;
+    int ldz;
+    __device__ __forceinline__ void operator()(int row, int col, const float* v) const {
+        __align__(16) __nv_bfloat16 a[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float z = v[j] + bias[col + j];
+            if (Z) Z[(size_t)row * ldz + col + j] = z;
+            a[j] = __float2bfloat16_rn(gelu_f(z));
+        }
+        uint4* dst = reinterpret_cast<uint4*>(A + (size_t)row * lda + col);
+        dst[0] = reinterpret_cast<const uint4*>(a)[0];
+        dst[1] = reinterpret_cast<const uint4*>(a)[1];
+    }
+};
+
+// Surrogate output head: part[row][col / tile] = sum over the tile's columns of
+// gelu(acc + b) w (one thread owns a row of a tile, so the sum is sequential
+// and deterministic); stores z as FP32 when Z != nullptr.
+struct EpiBiasGeluDot {
+    const float* bias;
+    const float* w;
+    float* part;
+    int nparts;
+    int tile;
+    float* Z;
+    int ldz;
+    __device__ __forceinline__ void operator()(int row, int col, const float* v) const {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float z = v[j] + bias[col + j];
+            if (Z) Z[(size_t)row * ldz + col + j] = z;
+            s = fmaf(gelu_f(z), w[col + j], s);
+        }
+        float* dst = part + (size_t)row * nparts + col / tile;
+        *dst = (col % tile == 0) ? s : *dst + s;
+    }
+};
+
 // ---- host side ------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -278,6 +326,21 @@ cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb,
     EpiStoreF32 epi{D, ldd};
     if (N % 128 == 0) return launch_gemm<128>(A, lda, B, ldb, M, N, K, epi, status, s);
     return launch_gemm<64>(A, lda, B, ldb, M, N, K, epi, status, s);
+}
+
+cudaError_t launch_gemm_bias_gelu(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const float* bias,
+                                  void* out_bf16, int ldo, float* Z, int ldz, int* status, cudaStream_t s) {
+    EpiBiasGelu epi{bias, static_cast<__nv_bfloat16*>(out_bf16), ldo, Z, ldz};
+    if (N % 128 == 0) return launch_gemm<128>(A, lda, B, ldb, M, N, K, epi, status, s);
+    return launch_gemm<64>(A, lda, B, ldb, M, N, K, epi, status, s);
+}
+
+cudaError_t launch_gemm_bias_gelu_dot(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                                      const float* bias, const float* w, float* part, float* Z, int ldz, int* status,
+                                      cudaStream_t s) {
+    if (N % 128) return cudaErrorInvalidValue;
+    EpiBiasGeluDot epi{bias, w, part, N / 128, 128, Z, ldz};
+    return launch_gemm<128>(A, lda, B, ldb, M, N, K, epi, status, s);
 }
 
 int* gemm_status_ptr() {

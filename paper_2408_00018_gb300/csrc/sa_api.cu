@@ -42,7 +42,14 @@ struct HostProb {
 // Problems whose sweep runs as one kernel launch with one block shape.  A
 // batch of problems of uneven dimension is split by n into groups; within a
 // level the groups' sweeps run concurrently on forked streams.
-enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2, kSweepRot = 3 };
+enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2, kSweepRot = 3, kSweepDA = 4 };
+
+// Delayed acceptance: training per level and buffer sizes.
+constexpr int kDaTrainSteps = 128;
+constexpr int kDaBatch = 4096;
+constexpr float kDaLr = 1e-3f;
+constexpr int64_t kDaBufferRows = (int64_t)1 << 20;
+constexpr uint32_t kTagDa = 3u, kTagTrain = 4u;
 
 bool is_rot(int cost) { return cost == SA_ROT_RASTRIGIN || cost == SA_ROT_SCHWEFEL; }
 struct Group {
@@ -97,6 +104,10 @@ struct sa_handle {
     int* d_pit = nullptr;
     SweepArgs args{};
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
+    // delayed acceptance with the surrogate (schedule.surrogate == 1)
+    bool da = false;
+    DaDev dd{};
+    int* gemm_status = nullptr;  // status word of the tensor-core GEMMs (looked up once, outside capture)
 };
 
 namespace {
@@ -152,7 +163,8 @@ sa_status check_schedule(const sa_schedule* s) {
     if (!(s->sigma_frac > 0.0) || !std::isfinite(s->sigma_frac)) return SA_EINVAL;
     if (s->boundary != SA_REFLECT && s->boundary != SA_CLIP) return SA_EINVAL;
     if (s->precision != SA_FP64 && s->precision != SA_FP32) return SA_EINVAL;
-    if (s->surrogate != 0 || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
+    if ((s->surrogate != 0 && s->surrogate != 1) || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
+    if (s->cost_repeat < 0 || s->cost_repeat > 4096) return SA_EINVAL;
     if (s->trace_levels < 0) return SA_EINVAL;
     return SA_OK;
 }
@@ -161,6 +173,7 @@ sa_status check_schedule(const sa_schedule* s) {
 sa_status check_problem(const sa_problem& pr, const sa_box& box, int32_t n, int64_t chains, const sa_schedule& sch) {
     if (n < 1 || chains < 1 || chains > 2147483647LL || !box.lo || !box.hi) return SA_EINVAL;
     if (pr.cost < SA_SCHWEFEL || pr.cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
+    if (sch.surrogate && (!is_rot(pr.cost) || n > 4096)) return SA_EINVAL;
     if (is_rot(pr.cost)) {
         // rotated costs run the FP32 rank-1 sweep; the hybrid polish covers separable costs
         if (!pr.Q || sch.precision != SA_FP32 || sch.polish_k != 0) return SA_EINVAL;
@@ -243,6 +256,8 @@ cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
     if (g.kind == kSweepF64) return launch_sweep_f64(a, num, g.block, g.smem, s);
     if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.smem, s);
     if (g.kind == kSweepRot) return launch_sweep_rot(a, num, g.smem, s);
+    if (g.kind == kSweepDA)
+        return launch_da_level(a, h->dd, h->probs[h->dd.problem].chains, h->L, kDaTrainSteps, kDaLr, h->gemm_status, s);
     return launch_sweep_f32(a, num, g.block, g.smem, s);
 }
 
@@ -265,8 +280,8 @@ cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
 // chains), largest problems first; uploaded on the handle's stream.
 sa_status set_group_items(sa_handle* h, Group& g) {
     const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block()
-                         : g.kind == kSweepRot   ? sweep_rot_chains_per_block()
-                                                 : g.block;
+                         : (g.kind == kSweepRot || g.kind == kSweepDA) ? sweep_rot_chains_per_block()
+                                                                       : g.block;
     std::vector<int> order = g.probs;
     std::sort(order.begin(), order.end(), [h](int a, int b) { return h->probs[a].chains > h->probs[b].chains; });
     g.items.clear();
@@ -407,6 +422,71 @@ sa_status setup_rot(sa_handle* h, HostProb& hp, ProbDev& d) {
     float qm = (float)qmax;
     if ((double)qm < qmax) qm = std::nextafterf(qm, INFINITY);
     d.qmax = qm;
+    double ymax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < n; ++j) r += std::fabs(hp.Q[(size_t)i * n + j]) * std::fmax(std::fabs(hp.lo[j]), std::fabs(hp.hi[j]));
+        ymax = std::fmax(ymax, r);
+    }
+    d.ymax = (float)(ymax * 1.001);
+    return SA_OK;
+}
+
+// Buffers of the delayed-acceptance sweep and of the surrogate's training.
+sa_status setup_da(sa_handle* h) {
+    const HostProb& hp = h->probs[0];
+    DaDev& D = h->dd;
+    const int n = hp.n;
+    const int64_t C = hp.chains;
+    D.problem = 0;
+    D.np = (n + 63) / 64 * 64;
+    D.Cp = (int)((C + 127) / 128 * 128);
+    D.cap = std::max<int64_t>(1, kDaBufferRows / C) * C;  // a multiple of C: one insertion never wraps onto itself
+    D.batch = kDaBatch;
+    const int64_t P = mlp_offsets(n).total;
+    const int tl = h->args.trace_levels;
+    sa_status st;
+    float *mid, *ih;
+    if ((st = dalloc(h, &D.xf, (size_t)C * n)) || (st = dalloc(h, &D.yh, (size_t)C * n)) ||
+        (st = dalloc(h, &D.yl, (size_t)C * n)) || (st = dalloc(h, &D.xs, (size_t)D.Cp * D.np)) ||
+        (st = dalloc(h, &D.Fa, C)) || (st = dalloc(h, &D.Ea, C)) || (st = dalloc(h, &D.fts, C)) ||
+        (st = dalloc(h, &D.part, (size_t)D.Cp * 4)) || (st = dalloc(h, &D.A1, (size_t)D.Cp * kMlpHidden)) ||
+        (st = dalloc(h, &D.ms, 2)) || (st = dalloc(h, &mid, n)) || (st = dalloc(h, &ih, n)) ||
+        (st = dalloc(h, &D.evals, 1)) || (st = dalloc(h, &D.rx, (size_t)D.cap * n)) || (st = dalloc(h, &D.rf, D.cap)) ||
+        (st = dalloc(h, &D.bt, D.batch)) || (st = dalloc(h, &D.grad, P)) || (st = dalloc(h, &D.m, P)) ||
+        (st = dalloc(h, &D.v, P)) || (st = dalloc(h, &D.adam_step, 1)) || (st = dalloc(h, &D.train_on, 1)) ||
+        (st = dalloc(h, &D.mlp.p, P)) || (st = dalloc(h, &D.mlp.W1b, (size_t)kMlpHidden * D.np)) ||
+        (st = dalloc(h, &D.mlp.W2b, (size_t)kMlpHidden * kMlpHidden)) ||
+        (st = dalloc(h, &D.mlp.W2tb, (size_t)kMlpHidden * kMlpHidden)))
+        return st;
+    if (tl > 0 && ((st = dalloc(h, &D.trace_ft0, (size_t)tl * C)) || (st = dalloc(h, &D.trace_ftp, (size_t)tl * h->L * C))))
+        return st;
+    unsigned char* wbase;
+    if ((st = dalloc(h, &wbase, mlp_work_bytes(D.batch, D.np) + 1024))) return st;
+    mlp_work_carve(reinterpret_cast<void*>(((uintptr_t)wbase + 1023) & ~(uintptr_t)1023), D.batch, D.np, D.work);
+    D.mid = mid;
+    D.inv_half = ih;
+    if (!(h->gemm_status = gemm_status_ptr())) return SA_ECUDA;
+    D.mlp.n = n;
+    D.mlp.np = D.np;
+    D.b3 = D.mlp.p + mlp_offsets(n).b3;
+    D.dkey0 = (uint32_t)h->seed;
+    D.dkey1 = (uint32_t)(h->seed >> 32) ^ kTagDa;
+    D.tkey0 = (uint32_t)h->seed;
+    D.tkey1 = (uint32_t)(h->seed >> 32) ^ kTagTrain;
+    std::vector<float> m(n), ihv(n);
+    for (int k = 0; k < n; ++k) {
+        m[k] = (float)(0.5 * (hp.lo[k] + hp.hi[k]));
+        const double half = 0.5 * (hp.hi[k] - hp.lo[k]);
+        ihv[k] = (float)(half > 0.0 ? 1.0 / half : 0.0);
+    }
+    // zero the padded rows of the input matrix once (the kernels write only real rows)
+    if (cudaMemsetAsync(D.xs, 0, (size_t)D.Cp * D.np * sizeof(__nv_bfloat16), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(D.part, 0, (size_t)D.Cp * 4 * sizeof(float), h->stream) != cudaSuccess)
+        return SA_ECUDA;
+    if ((st = h2d(h, mid, m.data(), n)) || (st = h2d(h, ih, ihv.data(), n))) return st;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SA_ECUDA;
+    h->da = true;
     return SA_OK;
 }
 
@@ -438,7 +518,11 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
 
     // launch groups: FP64 -> one group; FP32 -> one group per dimension bucket
     (void)n_max;
-    if (h->precision == SA_FP64) {
+    if (h->sch.surrogate) {
+        h->groups.resize(1);
+        h->groups[0].kind = kSweepDA;
+        h->groups[0].probs.push_back(0);
+    } else if (h->precision == SA_FP64) {
         h->groups.resize(1);
         h->groups[0].kind = kSweepF64;
         for (int p = 0; p < P; ++p) h->groups[0].probs.push_back(p);
@@ -473,10 +557,10 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         for (int p : g.probs) g.n_max = std::max(g.n_max, h->probs[p].n);
         g.block = g.kind == kSweepF32Warp ? 256 : g.kind == kSweepRot ? 32 * sweep_rot_chains_per_block()
                                                                         : pick_block(h->precision, g.n_max);
-        g.smem = group_smem(g);
+        g.smem = g.kind == kSweepDA ? 0 : group_smem(g);
         if ((int)g.smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
-        if (group_set_smem(g) != cudaSuccess) return SA_ECUDA;
-        const int64_t tile = g.kind == kSweepRot ? sweep_rot_chains_per_block() : 8;  // smallest tile
+        if (g.kind != kSweepDA && group_set_smem(g) != cudaSuccess) return SA_ECUDA;
+        const int64_t tile = (g.kind == kSweepRot || g.kind == kSweepDA) ? sweep_rot_chains_per_block() : 8;  // smallest tile
         for (int p : g.probs) g.items_cap += (size_t)((h->probs[p].chains + tile - 1) / tile);
         if ((st = dalloc(h, &g.d_items, g.items_cap))) return st;
         if (h->groups.size() > 1 &&
@@ -622,9 +706,12 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
     }
 
+    a.cost_repeat = h->sch.cost_repeat > 1 ? h->sch.cost_repeat : 1;
+    if (h->sch.surrogate && (st = setup_da(h))) return st;
+
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return SA_ECUDA;
     if ((st = capture_levels(h, 1, &h->g1))) return st;
-    if (h->levels_total >= kGraphLevels && (st = capture_levels(h, kGraphLevels, &h->gN))) return st;
+    if (h->levels_total >= kGraphLevels && !h->da && (st = capture_levels(h, kGraphLevels, &h->gN))) return st;
 
     uint64_t fp = 1469598103934665603ull;
     fp = fnv(fp, &h->sch, sizeof(h->sch));
@@ -644,6 +731,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
 
 cudaError_t launch_level0_prep(sa_handle* h, cudaStream_t s) {
     cudaError_t e = launch_stamp_start(h->d_run, s);
+    if (e == cudaSuccess && h->da) e = da_run_start(h->dd, h->seed, s);
     for (size_t p = 0; p < h->probs.size() && e == cudaSuccess; ++p) {
         const HostProb& hp = h->probs[p];
         if (is_rot(hp.cost))
@@ -835,7 +923,7 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
     if (st != SA_OK) return st;
     const HostProb& hp = h->probs[problem];
     std::vector<double> sc(kNumScalars);
-    unsigned long long acc = 0, rech = 0;
+    unsigned long long acc = 0, rech = 0, evals = 0;
     int64_t am = -1;
     long long t0 = 0;
     h->d2h_bytes += (int64_t)(sizeof(double) * kNumScalars + sizeof(acc) + sizeof(am) + sizeof(t0) +
@@ -844,6 +932,7 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
         cudaMemcpyAsync(&t0, &h->d_run->t_start, sizeof(t0), cudaMemcpyDeviceToHost, h->stream) ||
         cudaMemcpyAsync(&acc, hp.dev.accepts, sizeof(acc), cudaMemcpyDeviceToHost, h->stream) ||
         (hp.dev.rechecks && cudaMemcpyAsync(&rech, hp.dev.rechecks, sizeof(rech), cudaMemcpyDeviceToHost, h->stream)) ||
+        (h->da && cudaMemcpyAsync(&evals, h->dd.evals, sizeof(evals), cudaMemcpyDeviceToHost, h->stream)) ||
         cudaMemcpyAsync(&am, hp.dev.log_argmin + (h->levels_done - 1), sizeof(am), cudaMemcpyDeviceToHost, h->stream) ||
         (x_out && cudaMemcpyAsync(x_out, hp.dev.x_inc, sizeof(double) * hp.n, cudaMemcpyDeviceToHost, h->stream)) ||
         cudaStreamSynchronize(h->stream))
@@ -860,7 +949,21 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
         stt->d2h_bytes = h->d2h_bytes;
         stt->t_start_ns = t0;
         stt->rechecks = (int64_t)rech;
+        stt->true_evals = h->da ? (int64_t)evals : stt->steps;
     }
+    return SA_OK;
+}
+
+sa_status sa_da_trace(sa_handle* h, int32_t level, float* ft0_out, float* ftp_out) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (!h->da || level < 0 || level >= h->args.trace_levels || level >= h->levels_done) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    const int64_t C = h->probs[0].chains;
+    if ((ft0_out && cudaMemcpy(ft0_out, h->dd.trace_ft0 + (size_t)level * C, sizeof(float) * C, cudaMemcpyDeviceToHost)) ||
+        (ftp_out && cudaMemcpy(ftp_out, h->dd.trace_ftp + (size_t)level * h->L * C, sizeof(float) * h->L * C,
+                               cudaMemcpyDeviceToHost)))
+        return fail(h, SA_ECUDA);
     return SA_OK;
 }
 
@@ -926,6 +1029,7 @@ sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_
 sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len) {
     if (!h || !len) return SA_EINVAL;
     if (h->failed != SA_OK) return SA_ESTATE;
+    if (h->da) return SA_EINVAL;  // the surrogate's state is not part of a checkpoint
     size_t need = 4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(int32_t) * 2;
     for (const HostProb& hp : h->probs)
         need += sizeof(double) * (kNumScalars + 2 * (size_t)hp.n) + sizeof(uint64_t) +
@@ -979,6 +1083,7 @@ sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len) {
 sa_status sa_restore(sa_handle* h, const void* buf, size_t len) {
     if (!h || !buf) return SA_EINVAL;
     if (h->failed != SA_OK) return SA_ESTATE;
+    if (h->da) return SA_EINVAL;
     const unsigned char* p = static_cast<const unsigned char*>(buf);
     const unsigned char* end = p + len;
     auto get = [&p, end](void* dst, size_t n) {
@@ -1053,7 +1158,7 @@ sa_status sa_create_batch(const sa_problem* problems, const sa_box* boxes, const
                           sa_handle** out) {
     if (out) *out = nullptr;
     if (!problems || !boxes || !n || !chains || !out || num_problems < 1 || L < 1) return SA_EINVAL;
-    if (check_schedule(schedule) != SA_OK) return SA_EINVAL;
+    if (check_schedule(schedule) != SA_OK || schedule->surrogate) return SA_EINVAL;
     for (int p = 0; p < num_problems; ++p)
         if (check_problem(problems[p], boxes[p], n[p], chains[p], *schedule) != SA_OK) return SA_EINVAL;
     sa_handle* h = new (std::nothrow) sa_handle();

@@ -1,6 +1,7 @@
 // sa_internal.h -- descriptors shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace sa {
@@ -64,6 +65,7 @@ struct ProbDev {
     unsigned int* rot_done;  // last-block-done counter of the restart transform
     double* rot_part;     // [ceil(n / 128)] its partial sums
     float qmax;           // max |Q_ij| rounded up to FP32
+    float ymax;           // bound on |(Q x)_i| over the box: max_i sum_j |Q_ij| max(|l_j|, |u_j|)
 };
 
 // Device-resident run state shared by all problems of a handle.
@@ -95,6 +97,7 @@ struct SweepArgs {
     int32_t trace_levels;
     int32_t full_level;    // level whose every chain is re-evaluated in FP64 and stored (-1: none)
     int32_t boundary;      // 0 reflect then clip, 1 clip
+    int32_t cost_repeat;   // rotated costs: evaluations of each energy difference (1; more only to emulate costlier f)
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
     uint32_t rk[20];       // sweep key of each Philox round r: (rk[2r], rk[2r+1]) (kernel-parameter operands)
@@ -120,6 +123,14 @@ cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStrea
 cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
                                  int* status, cudaStream_t s);
 int* gemm_status_ptr();
+// Surrogate layers on the tensor-core GEMM: out = gelu(A B^T + bias) as BF16 (Z = the
+// pre-activation, FP32, optional); and part[row][t] = sum over the 128 columns of tile t
+// of gelu(A B^T + bias) w (N a multiple of 128).
+cudaError_t launch_gemm_bias_gelu(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const float* bias,
+                                  void* out_bf16, int ldo, float* Z, int ldz, int* status, cudaStream_t s);
+cudaError_t launch_gemm_bias_gelu_dot(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                                      const float* bias, const float* w, float* part, float* Z, int ldz, int* status,
+                                      cudaStream_t s);
 cudaError_t launch_gather(const float* X32, const double* X64, int64_t x_base, int64_t chains, int n, const int64_t* idx,
                           int k, double* out, cudaStream_t s);
 cudaError_t launch_polish_update(ProbDev* probs, int problem, const double* xs, const double* fs, int k, cudaStream_t s);
@@ -132,6 +143,104 @@ cudaError_t launch_rot_restart(const ProbDev* d_prob, int n, cudaStream_t s);
 int rot_restart_blocks(int n);
 cudaError_t launch_rot_level0(const ProbDev* d_prob, const ProbDev& host_prob, const SweepArgs& a, float* x0, float2* y0,
                               cudaStream_t s);
+
+// ---- the learned surrogate (mlp.cu) ----------------------------------------
+constexpr int kMlpHidden = 512;
+
+// Offsets (elements) of the blocks of the flat FP32 parameter vector.
+struct MlpOffsets {
+    int64_t W1, b1, W2, b2, w3, b3, total;
+};
+__host__ __device__ inline MlpOffsets mlp_offsets(int n) {
+    MlpOffsets o;
+    o.W1 = 0;
+    o.b1 = (int64_t)kMlpHidden * n;
+    o.W2 = o.b1 + kMlpHidden;
+    o.b2 = o.W2 + (int64_t)kMlpHidden * kMlpHidden;
+    o.w3 = o.b2 + kMlpHidden;
+    o.b3 = o.w3 + kMlpHidden;
+    o.total = o.b3 + 1;
+    return o;
+}
+
+struct MlpDev {
+    int n, np;        // input dimension and its padding to a multiple of 64
+    float* p;         // FP32 parameters
+    __nv_bfloat16* W1b;        // BF16 [512 x np]
+    __nv_bfloat16* W2b;        // BF16 [512 x 512]
+    __nv_bfloat16* W2tb;       // BF16 W2^T [512 x 512]
+};
+
+// Per-batch workspace (rows padded to Bp, a multiple of 128).
+struct MlpWork {
+    __nv_bfloat16* Xb; // BF16 [Bp x np] inputs
+    __nv_bfloat16* XT; // BF16 [np x Bp]
+    float* Z1;        // [Bp x 512] first pre-activation (nullptr: not stored)
+    __nv_bfloat16* A1; // BF16 [Bp x 512]
+    __nv_bfloat16* A1T; // BF16 [512 x Bp]
+    float* Z2;        // [Bp x 512] second pre-activation (nullptr: not stored)
+    __nv_bfloat16* dZ2b; // BF16 [Bp x 512]
+    __nv_bfloat16* dZ2T; // BF16 [512 x Bp]
+    float* dA1;       // [Bp x 512]
+    __nv_bfloat16* dZ1b; // BF16 [Bp x 512]
+    __nv_bfloat16* dZ1T; // BF16 [512 x Bp]
+    float* y;         // [Bp]
+    float* dy;        // [Bp]
+    float* part;      // [Bp x 4] partial output sums
+    float* dW1;       // [512 x np]
+};
+
+cudaError_t mlp_cast(const MlpDev& m, cudaStream_t s);
+cudaError_t mlp_init(float* p, int n, uint64_t seed, cudaStream_t s);
+cudaError_t mlp_forward(const MlpDev& m, const void* Xb, int Bp, MlpWork& w, float* part, int* status, cudaStream_t s);
+cudaError_t mlp_finish_y(const MlpDev& m, const float* part, int B, float* y, cudaStream_t s);
+cudaError_t mlp_loss_grad(const MlpDev& m, const void* Xb, int B, int Bp, const float* t, MlpWork& w, float* grad,
+                          float* loss, int* status, cudaStream_t s);
+cudaError_t mlp_adam(float* p, const float* g, float* mo, float* vo, int64_t count, int step, float lr, float b1, float b2,
+                     float eps, cudaStream_t s);
+cudaError_t mlp_pack(const float* X, int B, int n, int Bp, int np, void* Xb, cudaStream_t s);
+size_t mlp_work_bytes(int Bp, int np);
+void mlp_work_carve(void* base, int Bp, int np, MlpWork& w);
+
+// ---- delayed acceptance with the surrogate (da.cu) -----------------------------
+struct DaDev {
+    int problem;             // index of the (rotated) problem in the handle
+    int np, Cp;              // padded input width and chain count (multiples of 64 / 128)
+    int64_t cap;             // ring buffer rows (a multiple of the chain count)
+    int batch;               // training batch rows
+    float* xf;               // [C][n] current states
+    float* yh;               // [C][n] Q x as pairs
+    float* yl;
+    __nv_bfloat16* xs;       // [Cp][np] standardised states, the network's input rows
+    double* Fa;              // [C] F of the current state (tracked)
+    double* Ea;              // [C] bound on the error of Fa
+    float* fts;              // [C] f~ of the current state
+    float* part;             // [Cp][4] the output head's partial sums
+    __nv_bfloat16* A1;       // [Cp][512] hidden activations of the inference GEMMs
+    float* ms;               // [2] mean and standard deviation of the targets (frozen per level)
+    float* mid;              // [n] input standardisation (x - mid) / half
+    float* inv_half;         // [n]
+    const float* b3;         // the output bias inside the parameters
+    float* trace_ft0;        // [trace_levels][C] f~ at the level's start states (or NULL)
+    float* trace_ftp;        // [trace_levels][L][C] f~ at every proposal (or NULL)
+    unsigned long long* evals;  // true energy differences evaluated (stage-1 survivors)
+    float* rx;               // [cap][n] ring buffer of states
+    float* rf;               // [cap] and of their values
+    float* bt;               // [batch] standardised training targets
+    float* grad;             // [params] gradient of the training loss
+    float* m;                // [params] Adam moments
+    float* v;
+    int* adam_step;          // Adam steps taken (device)
+    int* train_on;           // 1 once the buffer holds pairs (device)
+    uint32_t dkey0, dkey1;   // Philox key of stream tag 3 (stage-1 uniforms)
+    uint32_t tkey0, tkey1;   // Philox key of stream tag 4 (training batches)
+    MlpDev mlp;
+    MlpWork work;            // training workspace (batch rows)
+};
+
+cudaError_t da_run_start(const DaDev& D, uint64_t seed, cudaStream_t s);
+cudaError_t launch_da_level(const SweepArgs& A, const DaDev& D, int64_t chains, int L, int train_steps, float lr,
+                            int* status, cudaStream_t s);
 
 constexpr int kArgminThreads = 256;
 constexpr int kArgminPerThread = 8;

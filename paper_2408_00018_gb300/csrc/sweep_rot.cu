@@ -26,6 +26,7 @@
 #include <cstdint>
 #include <math_constants.h>
 
+#include "rot_step.cuh"
 #include "sa_device.cuh"
 #include "sa_internal.h"
 
@@ -34,37 +35,7 @@ namespace {
 
 constexpr int kWarpsR = 4;
 constexpr int kBlockR = 32 * kWarpsR;
-constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float wsumf(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-__device__ __forceinline__ double wsumd(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-// sin(pi a) for |pi a| < 1/2: Taylor polynomial to degree 7 (truncation below
-// 1.1e-8 relative).
-__device__ __forceinline__ float sinpi_small(float a) {
-    const float x = 3.14159265358979f * a;
-    const float x2 = x * x;
-    const float p = fmaf(x2, fmaf(x2, fmaf(x2, -1.98412698e-4f, 8.33333333e-3f), -1.66666667e-1f), 1.0f);
-    return x * p;
-}
-// sin(2 pi r) for |r| < 2^22: r - rint(r) is exact, the SFU sine then runs on [-pi, pi].
-__device__ __forceinline__ float sin2pi(float r) {
-    const float f = r - rintf(r);
-    return __sinf(6.28318530717958648f * f);
-}
-
-template <int COST>
-__device__ __forceinline__ double g64_rot(double y) {
-    return COST == kRotRastrigin ? g64_rastrigin(y) : h64_schwefel(y);
-}
 template <int COST>
 __device__ __forceinline__ double f_from_sum(double s, int n) {
     return COST == kRotRastrigin ? 10.0 * (double)n + s : -(s / (double)n);
@@ -95,9 +66,9 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
             const float2 v = yr[k];
             yh[k] = v.x;
             yl[k] = v.y;
-            part += g64_rot<COST>((double)v.x + (double)v.y);
+            part += rot_g64<COST>((double)v.x + (double)v.y);
         }
-        Fs = f_from_sum<COST>(wsumd(part), n);
+        Fs = f_from_sum<COST>(rot_wsumd(part), n);
     } else {
         for (int k = lane; k < n; k += 32) {
             x[k] = P.x_best32[k];
@@ -113,77 +84,23 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
     const float tau_abs = (float)(T * 4.0e-7);
     const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
-    const float qmax_pi = P.qmax * 3.14159265f;
-    const float inv_n = 1.0f / (float)n;
-    const float nsum = ((float)((n + 31) / 32) + 6.0f) * 1.2e-7f;  // summation rounding per unit of sum |t_i|
     double dS = 0.0, e = 0.0;
     unsigned nacc = 0, nre = 0, bw = 0;
     for (int s = 0; s < A.L; ++s) {
         // randomness of step s (the same block in every lane)
         const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), A.key0, A.key1);
-        const int d = coord_of(w.x, n);
-        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u23f(w.y)));
-        const float z = -r * __cosf(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
-        const float tau = neg_T_ln2 * __log2f(u23f(w.w));
-        const float xo = x[d];
-        float xp = fmaf(sig, z, xo);
-        if (A.boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);
-        xp = fminf(fmaxf(xp, lo), hi);
-        // delta = xp - xo exactly, as dh + dl (TwoSum)
-        const float dh = xp - xo;
-        const float bb = dh - xp;
-        const float dl = (xp - (dh - bb)) + (-xo - bb);
+        const RotMove mv = rot_propose(w, x, n, sig, lo, hi, A.boundary, neg_T_ln2);
+        const int d = mv.d;
+        const float xo = mv.xo, xp = mv.xp, dh = mv.dh, dl = mv.dl, tau = mv.tau;
         // ---- FP32 energy difference and its error bound
-        const float* qcol = P.qt_hi + (size_t)d * n;
-        float sum = 0.0f, sabs = 0.0f, bnd = 0.0f;
-        if (COST == kRotRastrigin) {
-            const bool any_big = fabsf(dh) * qmax_pi >= 0.5f;  // some |pi Delta_i| may reach 1/2
-            for (int i = lane; i < n; i += 32) {
-                const float yv = yh[i];
-                const float Dl = dh * qcol[i];
-                const float m = (yv - rintf(yv)) + fmaf(0.5f, Dl, yl[i]);  // y + Delta/2 modulo 1
-                const float s1 = sin2pi(m);
-                float s2 = sinpi_small(Dl);
-                float c = 2.0e-4f;
-                if (any_big && fabsf(Dl) * 3.14159265f >= 0.5f) {
-                    s2 = sin2pi(0.5f * Dl);
-                    c = 5.0e-4f;
-                }
-                const float t = fmaf(Dl, fmaf(2.0f, yv, Dl), 20.0f * s1 * s2);
-                sum += t;
-                sabs += fabsf(t);
-                const float aD = fabsf(Dl);
-                bnd = fmaf(aD, fmaf(fabsf(yv), 9.0e-7f, fmaf(aD, 6.0e-5f, c)), bnd);
-            }
-        } else {
-            for (int i = lane; i < n; i += 32) {
-                const float yv = yh[i];
-                const float Dl = dh * qcol[i];
-                const float yp = fmaf(dh, qcol[i], yv);
-                const float ro = sqrt_approx(fabsf(yv)), rp = sqrt_approx(fabsf(yp));
-                const float t = yp * sin_reduced(rp) - yv * sin_reduced(ro);
-                sum += t;
-                sabs += fabsf(t);
-                const float ay = fabsf(yv), ap = fabsf(yp);
-                // evaluation of both terms, then their arguments' errors times |h'| <= 1 + sqrt|t|/2
-                const float ev = ay * fmaf(ro, 4.8e-7f, 2.6e-6f) + ap * fmaf(rp, 4.8e-7f, 2.6e-6f);
-                const float ar = fmaf(0.5f, rp, 1.0f) * (6.0e-8f * (ap + ay) + 1.8e-7f * fabsf(Dl)) +
-                                 fmaf(0.5f, ro, 1.0f) * 6.0e-8f * ay;
-                bnd += 1.5f * (ev + ar);
-            }
-        }
-        sum = wsumf(sum);
-        sabs = wsumf(sabs);
-        bnd = wsumf(bnd);
         float dF, B;
-        if (COST == kRotRastrigin) {
-            dF = sum;
-            B = bnd + nsum * sabs;
-        } else {
-            dF = -sum * inv_n;
-            B = (bnd + nsum * sabs) * inv_n + 2.4e-7f * fabsf(dF);
+        rot_eval32<COST>(P, yh, yl, d, dh, n, lane, dF, B);
+        for (int rep = 1; rep < A.cost_repeat; ++rep) {  // the expensive-cost knob: the same evaluation again
+            float dF2, B2;
+            rot_eval32<COST>(P, yh, yl, d, dh + opaque_zero(), n, lane, dF2, B2);
+            asm volatile("" ::"f"(dF2), "f"(B2));
         }
-        B = 1.01f * B + 1.0e-6f * fabsf(tau) + tau_abs;  // with the error of tau
+        B += 1.0e-6f * fabsf(tau) + tau_abs;  // with the error of tau
         bool acc;
         double dF_used = (double)dF;
         double e_step = (double)B;
@@ -193,47 +110,14 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
             acc = false;
         } else {
             // ---- FP64 re-check of a decision inside the bound
-            const double d64 = (double)xp - (double)xo;
-            const double* q64 = P.qt64 + (size_t)d * n;
-            double s64 = 0.0, a64 = 0.0;
-            for (int i = lane; i < n; i += 32) {
-                const double y64 = (double)yh[i] + (double)yl[i];
-                const double gn = g64_rot<COST>(y64 + d64 * q64[i]), go = g64_rot<COST>(y64);
-                s64 += gn - go;
-                a64 += fabs(gn) + fabs(go);
-            }
-            s64 = wsumd(s64);
-            a64 = wsumd(a64);
-            const double dF64 = COST == kRotRastrigin ? s64 : -(s64 / (double)n);
+            const double dF64 = rot_eval64<COST>(P, yh, yl, d, xp, xo, n, lane, e_step);
             acc = (dF64 <= 0.0) || (u23d(w.w) < exp(-dF64 / T));
             dF_used = dF64;
-            // FP64 evaluation and summation error (4 ulp per term, the rest per addition)
-            e_step = 2.3e-16 * ((double)((n + 31) / 32) + 10.0) * a64 / (COST == kRotRastrigin ? 1.0 : (double)n);
             ++nre;
         }
         if (acc) {
             if (lane == 0) x[d] = xp;
-            const float* qlcol = P.qt_lo + (size_t)d * n;
-            for (int i = lane; i < n; i += 32) {
-                // (yh, yl) += (dh + dl)(qh + ql), compensated (TwoProd by FMA, TwoSum)
-                const float qh = qcol[i], ql = qlcol[i];
-                const float ph = dh * qh;
-                const float pl = fmaf(dh, qh, -ph);
-                const float corr = fmaf(dh, ql, dl * qh);
-                const float a = yh[i];
-                const float sh = a + ph;
-                const float t2 = sh - a;
-                const float err = (a - (sh - t2)) + (ph - t2);
-                const float lo2 = yl[i] + (pl + corr + err);
-                const float nh = sh + lo2;
-                yh[i] = nh;
-                yl[i] = lo2 - (nh - sh);
-                // the pair moves by at most 2^-45 (|y'| + |Delta|) from the exact
-                // update; F by |g'| times that
-                const float an = fabsf(nh);
-                const float gp = COST == kRotRastrigin ? fmaf(2.0f, an, 64.0f) : fmaf(0.5f, sqrt_approx(an), 1.0f) * inv_n;
-                edrift = fmaf(gp, (an + fabsf(ph)) * 2.9e-14f, edrift);
-            }
+            rot_update<COST>(P, yh, yl, d, dh, dl, n, lane, edrift);
             dS += dF_used;
             e += e_step;
             ++nacc;
@@ -247,7 +131,7 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
     }
     RotEnd r;
     r.Fa = Fs + dS;
-    r.ec = e + (double)wsumf(edrift) + 1e-13 * (fabs(Fs) + fabs(dS) + 1.0);
+    r.ec = e + (double)rot_wsumf(edrift) + 1e-13 * (fabs(Fs) + fabs(dS) + 1.0);
     r.nacc = nacc;
     r.nre = nre;
     return r;
@@ -263,8 +147,8 @@ __device__ void rot_finish(const SweepArgs& A, const ProbDev& P, int64_t c, int 
     const bool finite = isfinite(r.Fa);
     if (finite && (tracing || level == A.full_level || r.Fa - r.ec <= M)) {
         double part = 0.0;
-        for (int i = lane; i < n; i += 32) part += g64_rot<COST>((double)yh[i] + (double)yl[i]);
-        part = wsumd(part);
+        for (int i = lane; i < n; i += 32) part += rot_g64<COST>((double)yh[i] + (double)yl[i]);
+        part = rot_wsumd(part);
         if (lane == 0) A.F[gc] = f_from_sum<COST>(part, n);
         float* dst = A.X32 + P.x_base + c;
         for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = x[k];

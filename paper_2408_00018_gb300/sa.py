@@ -40,14 +40,14 @@ class _Schedule(ctypes.Structure):
     _fields_ = [("T0", ctypes.c_double), ("rho", ctypes.c_double), ("T_min", ctypes.c_double),
                 ("levels", ctypes.c_int32), ("sigma_frac", ctypes.c_double), ("boundary", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("surrogate", ctypes.c_int32), ("polish_k", ctypes.c_int32),
-                ("trace_levels", ctypes.c_int32)]
+                ("trace_levels", ctypes.c_int32), ("cost_repeat", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("accepts", ctypes.c_int64), ("levels_done", ctypes.c_int32),
                 ("levels_total", ctypes.c_int32), ("f_level", ctypes.c_double), ("argmin", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
-                ("rechecks", ctypes.c_int64)]
+                ("rechecks", ctypes.c_int64), ("true_evals", ctypes.c_int64)]
 
 
 _lib = None
@@ -79,6 +79,13 @@ SIGNATURES = {
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
     "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
+    "sa_da_trace": (ctypes.c_int, [_V, _I32, _V, _V]),
+    "sa_mlp_param_count": (_I64, [_I32]),
+    "sa_mlp_init": (ctypes.c_int, [_V, _I32, _U64, _V]),
+    "sa_mlp_forward": (ctypes.c_int, [_V, _I32, _V, _I32, _V, _V]),
+    "sa_mlp_loss_grad": (ctypes.c_int, [_V, _I32, _V, _V, _I32, _V, _V, _V]),
+    "sa_mlp_adam": (ctypes.c_int, [_V, _V, _V, _V, _I64, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, _V]),
 }
 
 # Largest input of sa_argmin_f64_static (SA_ARGMIN_STATIC_MAX_COUNT in include/sa.h).
@@ -134,10 +141,13 @@ class Schedule:
     precision: str = "fp64"
     trace_levels: int = 0
     polish_k: int = 0
+    surrogate: int = 0
+    cost_repeat: int = 1
 
     def _c(self) -> _Schedule:
         return _Schedule(self.T0, self.rho, self.T_min, self.levels, self.sigma_frac, BOUNDARY[self.boundary],
-                         PRECISION[self.precision], 0, self.polish_k, self.trace_levels)
+                         PRECISION[self.precision], self.surrogate, self.polish_k, self.trace_levels,
+                         self.cost_repeat)
 
 
 def levels_for(T0: float, rho: float, T_min: float) -> int:
@@ -220,6 +230,13 @@ class Handle:
         F = np.zeros(self.chains)
         _check(load().sa_trace_states(self._ptr, level, X.ctypes.data, F.ctypes.data), "sa_trace_states")
         return X, F
+
+    def da_trace(self, level: int):
+        """Surrogate values of a traced delayed-acceptance level: (ft0 [chains], ftp [L, chains])."""
+        ft0 = np.zeros(self.chains, np.float32)
+        ftp = np.zeros((self.L, self.chains), np.float32)
+        _check(load().sa_da_trace(self._ptr, level, ft0.ctypes.data, ftp.ctypes.data), "sa_da_trace")
+        return ft0, ftp
 
     def checkpoint(self) -> bytes:
         lib = load()
@@ -374,3 +391,42 @@ def argmin_f64_static(F):
     _check(load().sa_argmin_f64_static(ctypes.c_void_p(F.data_ptr()), F.numel(), ctypes.c_void_p(idx.data_ptr()),
                                        ctypes.c_void_p(val.data_ptr()), _current_stream()), "sa_argmin_f64_static")
     return idx, val
+
+
+# ---------------------------------------------------------------- surrogate network
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_param_count(n: int) -> int:
+    """Parameters of the surrogate for inputs of dimension n (sa_mlp_param_count)."""
+    return int(load().sa_mlp_param_count(n))
+
+
+def mlp_init(params, n: int, seed: int = 0) -> None:
+    """sa_mlp_init on a float32 CUDA tensor of mlp_param_count(n) elements."""
+    _check(load().sa_mlp_init(_ptr(params), n, seed, _current_stream()), "sa_mlp_init")
+
+
+def mlp_forward(params, n: int, X):
+    """sa_mlp_forward: surrogate values of the rows of a float32 CUDA tensor X [B x n]."""
+    import torch
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(load().sa_mlp_forward(_ptr(params), n, _ptr(X), X.shape[0], _ptr(y), _current_stream()), "sa_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params, n: int, X, t):
+    """sa_mlp_loss_grad: (loss, gradient) of the mean squared error on rows X [B x n], targets t [B]."""
+    import torch
+    g = torch.empty_like(params)
+    loss = torch.empty((), dtype=torch.float32, device=X.device)
+    _check(load().sa_mlp_loss_grad(_ptr(params), n, _ptr(X), _ptr(t), X.shape[0], _ptr(g), _ptr(loss),
+                                   _current_stream()), "sa_mlp_loss_grad")
+    return loss, g
+
+
+def mlp_adam(params, grad, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> None:
+    """sa_mlp_adam: one in-place Adam step of float32 CUDA tensors."""
+    _check(load().sa_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), step, lr, beta1, beta2, eps,
+                              _current_stream()), "sa_mlp_adam")
