@@ -247,6 +247,30 @@ sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_
 sa_status sa_da_trace(sa_handle* h, int32_t level, float* ft0_out, float* ftp_out);
 
 /*
+ * Chains sharded over several solvers (e.g. one per GPU), with the exchange of
+ * Sec. 2.2.2 done by the caller between levels:
+ *   sa_set_chain_offset  before the first level: this handle's chains are the
+ *                        global chains offset .. offset + chains - 1 (Philox
+ *                        counter word 2 = global index), so a sharded run
+ *                        draws exactly the numbers of the unsharded one.
+ *                        Single-problem handles; offset + chains <= 2^32.
+ *   sa_restart_point     after a level: this shard's restart point (the
+ *                        lowest-F chain of the shard, x_out host [n], may be
+ *                        NULL) and its FP64 value.
+ *   sa_set_restart       after the exchange: make (x, f) -- the lowest f over
+ *                        all shards, lowest global index `argmin` on ties --
+ *                        the restart point of the next level, update the
+ *                        incumbent and the level log.  x must lie in the box.
+ * With these, running the shards level by level and exchanging the (f, index)
+ * minimum gives the unsharded run's levels bit for bit.  All three
+ * synchronise the handle's stream.  Errors: SA_EINVAL on a bad argument,
+ * SA_ESTATE before the first level (restart calls) or after it (offset).
+ */
+sa_status sa_set_chain_offset(sa_handle* h, int64_t offset);
+sa_status sa_restart_point(sa_handle* h, int32_t problem, double* x_out, double* f_out);
+sa_status sa_set_restart(sa_handle* h, int32_t problem, const double* x, double f, int64_t argmin);
+
+/*
  * Serialise the state between levels (restart point, incumbent, level index,
  * counters) into buf.  With buf == NULL, *len receives the size needed.
  * Errors: SA_EINVAL if *len is too small.  Synchronises.

@@ -116,7 +116,7 @@ __global__ void da_patch_kernel(SweepArgs A, DaDev D, int s) {
     const int n = P.n;
     const double T = A.T_tab[level];
     const float sig = P.sig_u * (float)A.s_tab[level];
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), A.key0, A.key1);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
     const RotMove mv = rot_propose(w, D.xf + (size_t)c * n, n, sig, P.lo_u, P.hi_u, A.boundary,
                                    (float)(-T * 0.69314718055994531));
     D.xs[(size_t)c * D.np + mv.d] = std_bf16(mv.xp, D.mid[mv.d], D.inv_half[mv.d]);
@@ -132,7 +132,7 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     float* x = D.xf + (size_t)c * n;
     float* yh = D.yh + (size_t)c * n;
     float* yl = D.yl + (size_t)c * n;
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), A.key0, A.key1);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
     const float neg_T_ln2 = (float)(-T * 0.69314718055994531);
     const RotMove mv = rot_propose(w, x, n, sig, P.lo_u, P.hi_u, A.boundary, neg_T_ln2);
     // surrogate at the proposal (fixed summation order) and at the current state
@@ -143,7 +143,7 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     if (tracing && D.trace_ftp && lane == 0) D.trace_ftp[((size_t)level * A.L + s) * P.chains + c] = ftp;
     // ---- stage 1 (surrogate only), decided in FP64
     const double dFs = (double)ftp - (double)ftc;
-    const uint4 wd = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), D.dkey0, D.dkey1);
+    const uint4 wd = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), D.dkey0, D.dkey1);
     const bool pass1 = dFs <= 0.0 || u23d(wd.x) < exp(-dFs / T);
     bool acc = false;
     if (pass1) {

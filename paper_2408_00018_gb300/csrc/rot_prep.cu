@@ -29,7 +29,7 @@ __global__ void rot_init_kernel(const ProbDev* pp, uint32_t ikey0, uint32_t ikey
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = t / nq;
         const int k = (int)(t - c * nq) * 4;
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c, P.pid), ikey0, ikey1);
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c + P.cid0, P.pid), ikey0, ikey1);
         const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

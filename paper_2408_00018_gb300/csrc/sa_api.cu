@@ -954,6 +954,73 @@ sa_status sa_best(sa_handle* h, int32_t problem, double* x_out, double* f_out, s
     return SA_OK;
 }
 
+sa_status sa_set_chain_offset(sa_handle* h, int64_t offset) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (h->probs.size() != 1 || offset < 0 || offset + h->probs[0].chains > ((int64_t)1 << 32)) return SA_EINVAL;
+    if (h->levels_done != 0) return SA_ESTATE;
+    h->pd[0].cid0 = (uint32_t)offset;
+    h->probs[0].dev.cid0 = (uint32_t)offset;
+    if (h2d(h, h->d_probs, h->pd.data(), h->pd.size()) != SA_OK || cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
+sa_status sa_restart_point(sa_handle* h, int32_t problem, double* x_out, double* f_out) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (problem < 0 || problem >= (int)h->probs.size()) return SA_EINVAL;
+    if (h->levels_done == 0) return SA_ESTATE;
+    sa_status st = device_status(h);
+    if (st != SA_OK) return st;
+    const HostProb& hp = h->probs[problem];
+    if (x_out) {
+        if (h->precision == SA_FP64) {
+            if (cudaMemcpy(x_out, hp.dev.x_best64, sizeof(double) * hp.n, cudaMemcpyDeviceToHost)) return fail(h, SA_ECUDA);
+        } else {
+            std::vector<float> xf(hp.n);
+            if (cudaMemcpy(xf.data(), hp.dev.x_best32, sizeof(float) * hp.n, cudaMemcpyDeviceToHost)) return fail(h, SA_ECUDA);
+            for (int k = 0; k < hp.n; ++k) x_out[k] = xf[k];
+        }
+        h->d2h_bytes += (int64_t)(sizeof(double) * hp.n);
+    }
+    if (f_out && cudaMemcpy(f_out, hp.dev.scal + kFBest, sizeof(double), cudaMemcpyDeviceToHost)) return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
+sa_status sa_set_restart(sa_handle* h, int32_t problem, const double* x, double f, int64_t argmin) {
+    if (!h || !x) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (problem < 0 || problem >= (int)h->probs.size() || !std::isfinite(f)) return SA_EINVAL;
+    if (h->levels_done == 0) return SA_ESTATE;
+    HostProb& hp = h->probs[problem];
+    for (int k = 0; k < hp.n; ++k)
+        if (!(x[k] >= hp.lo[k] && x[k] <= hp.hi[k])) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    const ProbDev& d = hp.dev;
+    double finc = 0.0;
+    if (cudaMemcpy(&finc, d.scal + kFInc, sizeof(double), cudaMemcpyDeviceToHost)) return fail(h, SA_ECUDA);
+    std::vector<float> xf(hp.n);
+    for (int k = 0; k < hp.n; ++k) xf[k] = (float)x[k];
+    const int l = h->levels_done - 1;
+    const double fi = f < finc ? f : finc;
+    if (cudaMemcpy(d.x_best64, x, sizeof(double) * hp.n, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d.x_best32, xf.data(), sizeof(float) * hp.n, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d.scal + kFBest, &f, sizeof(double), cudaMemcpyHostToDevice) ||
+        (f < finc && (cudaMemcpy(d.x_inc, x, sizeof(double) * hp.n, cudaMemcpyHostToDevice) ||
+                      cudaMemcpy(d.scal + kFInc, &f, sizeof(double), cudaMemcpyHostToDevice))) ||
+        cudaMemcpy(d.log_argmin + l, &argmin, sizeof(int64_t), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d.log_f + l, &f, sizeof(double), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d.log_finc + l, &fi, sizeof(double), cudaMemcpyHostToDevice))
+        return fail(h, SA_ECUDA);
+    h->h2d_bytes += (int64_t)(sizeof(double) * hp.n * 2 + sizeof(float) * hp.n);
+    // rotated costs: the next level starts from y_best = Q x_best
+    if (is_rot(hp.cost) && (launch_rot_restart(h->d_probs + problem, hp.n, h->stream) != cudaSuccess ||
+                            cudaStreamSynchronize(h->stream) != cudaSuccess))
+        return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
 sa_status sa_da_trace(sa_handle* h, int32_t level, float* ft0_out, float* ftp_out) {
     if (!h) return SA_EINVAL;
     if (h->failed != SA_OK) return SA_ESTATE;

@@ -27,6 +27,7 @@ struct ProbDev {
     int64_t chain_base;   // offset of this problem's chains in per-chain arrays
     int64_t x_base;       // offset (elements) of this problem's [n][chains] state block
     uint32_t pid;         // Philox counter word 3
+    uint32_t cid0;        // global id of chain 0 (Philox counter word 2 = cid0 + chain; a shard's offset)
     int32_t nblk_argmin;  // blocks of the argmin kernel for this problem
     int32_t uniform;      // 1: every coordinate has the same [lo, hi] (scalars below are used)
     int32_t unroll;       // steps evaluated together per chain in the FP32 sweep (1, 2 or 4)

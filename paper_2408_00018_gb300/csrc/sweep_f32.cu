@@ -252,7 +252,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     if (level == 0) {
         if (active) {
             for (int k = 0; k < n; k += 4) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c, P.pid), A.ikey0, A.ikey1);
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c + P.cid0, P.pid), A.ikey0, A.ikey1);
                 const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -299,7 +299,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     C.boundary = A.boundary;
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
     C.level = (uint32_t)level;
-    C.chain = (uint32_t)c;
+    C.chain = (uint32_t)c + P.cid0;
     C.pid = P.pid;
     C.key0 = A.key0;
     C.key1 = A.key1;

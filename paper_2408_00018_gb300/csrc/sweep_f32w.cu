@@ -156,7 +156,7 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
     // ---- state at the start of the level
     if (level == 0) {
         for (int k = 4 * lane; k < n; k += 128) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c, P.pid), A.ikey0, A.ikey1);
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c + P.cid0, P.pid), A.ikey0, A.ikey1);
             const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -238,7 +238,7 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
     uint32_t rk[20];
 #pragma unroll
     for (int i = 0; i < 20; ++i) rk[i] = opaque(A.rk[i]);
-    C.pf = philox_prep((uint32_t)level, (uint32_t)c, P.pid, rk);
+    C.pf = philox_prep((uint32_t)level, (uint32_t)c + P.cid0, P.pid, rk);
     C.rk = rk;
     const float kappa = P.kappa;
 

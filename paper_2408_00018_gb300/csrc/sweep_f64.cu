@@ -58,7 +58,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     if (level == 0) {
         if (active) {
             for (int k = 0; k < n; k += 4) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c, P.pid), A.ikey0, A.ikey1);
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c + P.cid0, P.pid), A.ikey0, A.ikey1);
                 const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
@@ -76,7 +76,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
         double F = full_cost<COST>(xcol, B, n, -1, 0.0);
         uint32_t bw = 0;
         for (int s = 0; s < A.L; ++s) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c, P.pid), A.key0, A.key1);
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
             const int d = coord_of(w.x, n);
             const double u1 = u23d(w.y), u2 = u23d(w.z), u3 = u23d(w.w);
             const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);

@@ -80,6 +80,9 @@ SIGNATURES = {
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
     "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
     "sa_da_trace": (ctypes.c_int, [_V, _I32, _V, _V]),
+    "sa_set_chain_offset": (ctypes.c_int, [_V, _I64]),
+    "sa_restart_point": (ctypes.c_int, [_V, _I32, _V, _V]),
+    "sa_set_restart": (ctypes.c_int, [_V, _I32, _V, _D, _I64]),
     "sa_mlp_param_count": (_I64, [_I32]),
     "sa_mlp_init": (ctypes.c_int, [_V, _I32, _U64, _V]),
     "sa_mlp_forward": (ctypes.c_int, [_V, _I32, _V, _I32, _V, _V]),
@@ -230,6 +233,22 @@ class Handle:
         F = np.zeros(self.chains)
         _check(load().sa_trace_states(self._ptr, level, X.ctypes.data, F.ctypes.data), "sa_trace_states")
         return X, F
+
+    def set_chain_offset(self, offset: int) -> None:
+        """sa_set_chain_offset: this handle's chains are global chains offset .. offset + chains - 1."""
+        _check(load().sa_set_chain_offset(self._ptr, offset), "sa_set_chain_offset")
+
+    def restart_point(self, problem: int = 0):
+        """sa_restart_point: (x, f) of this handle's restart point after the last level."""
+        x = np.zeros(self.n)
+        f = ctypes.c_double()
+        _check(load().sa_restart_point(self._ptr, problem, x.ctypes.data, ctypes.byref(f)), "sa_restart_point")
+        return x, f.value
+
+    def set_restart(self, x, f: float, argmin: int, problem: int = 0) -> None:
+        """sa_set_restart: the exchanged restart point of the next level."""
+        x = np.ascontiguousarray(x, np.float64)
+        _check(load().sa_set_restart(self._ptr, problem, x.ctypes.data, float(f), int(argmin)), "sa_set_restart")
 
     def da_trace(self, level: int):
         """Surrogate values of a traced delayed-acceptance level: (ft0 [chains], ftp [L, chains])."""
