@@ -157,8 +157,22 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except FileNotFoundError:
             self.proc = None
+            return
+        # wait for the first sample, so that nvidia-smi's start-up is over before any timing
+        t0 = time.perf_counter()
+        while self.lines() == 0 and time.perf_counter() - t0 < 10.0:
+            time.sleep(0.05)
 
-    def stop(self):
+    def lines(self) -> int:
+        try:
+            with open(self.path) as fh:
+                return sum(1 for _ in fh)
+        except OSError:
+            return 0
+
+    def stop(self, window=None):
+        """Median SM clock and active throttle reasons over the samples taken inside
+        window = (first line, last line) (plus one sample on each side), else all."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         time.sleep(0.25)
@@ -173,6 +187,8 @@ class ClockSampler:
             if len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.path)
+        if window is not None:
+            rows = rows[max(0, window[0] - 1):window[1] + 1]
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -284,6 +300,8 @@ def run_ours(args, rank, world, local_rank):
     h = w.create(sa)
     groups = h.describe()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    sampler = ClockSampler(gpu_id_for(local_rank))
+    sampler.start()  # before the warm-up: its start-up must not overlap the timed region
     # W warm-up runs, continued until at least WARMUP_MIN_S of device work has
     # passed: the first seconds of work after idle run ~20% slower on this GPU.
     t_warm, warm_runs = time.perf_counter(), 0
@@ -295,14 +313,12 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
 
-    sampler = ClockSampler(gpu_id_for(local_rank))
-    sampler.start()
-    time.sleep(0.3)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    line0 = sampler.lines()
     e0.record(stream)
     for k in range(args.steps):
         flush.fill_(k & 0xFF)   # L2 flush between runs
@@ -312,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop((line0, sampler.lines()))
     ms = e0.elapsed_time(e1)
     bests = [h.best(p) for p in range(len(w.problems))]
     logs = [h.level_log(p) for p in range(len(w.problems))]

@@ -125,8 +125,8 @@ int32_t sa_levels_for(double T0, double rho, double T_min);
  * Errors: SA_EINVAL if n < 1, chains < 1, L < 1, lo[k] > hi[k] or not finite,
  * T0 <= 0, rho not in (0,1), levels < 0, levels == 0 and T_min not in
  * (0, T0), sigma_frac <= 0, unknown cost/boundary/precision, a rotated cost
- * without Q, with a non-finite Q entry, with n^2 > 2^28, with precision other
- * than SA_FP32 or with polish_k != 0, surrogate != 0, or chains > 2^31 - 1;
+ * without Q, with a non-finite Q entry, with n^2 > 2^28 or with precision other
+ * than SA_FP32, surrogate not 0 or 1 (1: rotated costs only), or chains > 2^31 - 1;
  * SA_ENOMEM / SA_ECUDA on allocation or copy failure.  *out is NULL on error.
  */
 sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains,
@@ -297,10 +297,12 @@ const char* sa_strerror(sa_status s);
  * projected gradient's infinity norm is below tol, when no step decreases
  * f, or after max_iter iterations.  Writes the final points to x_out (host
  * [k*n]), their values to f_out (host [k]) and the iteration counts to
- * iters_out (host [k], may be NULL).  Separable costs only (Q must be NULL).
+ * iters_out (host [k], may be NULL).  Rotated costs take Q (host, n x n
+ * row-major) and use grad f = Q^T g'(Q x); separable costs need Q == NULL.
  * Allocates its device buffers stream-ordered; synchronises `stream`.
  * Errors: SA_EINVAL on n < 1, k not in [1, 1024], a bad box, max_iter < 0,
- * tol < 0, a NULL array or a rotated cost; SA_ENOMEM; SA_ECUDA.
+ * tol < 0, a NULL array, Q missing for a rotated cost (or given for a
+ * separable one), a non-finite Q entry or n^2 > 2^28; SA_ENOMEM; SA_ECUDA.
  */
 sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
                     const double* x0, int32_t max_iter, double tol, double* x_out, double* f_out,

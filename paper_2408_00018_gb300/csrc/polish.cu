@@ -38,9 +38,33 @@ __device__ __forceinline__ double dh64_schwefel(double t) {
     return sin(r) + 0.5 * r * cos(r);
 }
 
-// f at x (warp-cooperative, lanes over coordinates); every lane gets the value.
-__device__ double pcost(int cost, int n, const double* x) {
+__device__ __forceinline__ double rot_term(int cost, double y) {
+    return cost == kRotRastrigin ? g64_rastrigin(y) : h64_schwefel(y);
+}
+
+// y = Q x (Q row-major [n x n]); lanes own rows, each row summed in index order.
+__device__ void protate(int n, const double* __restrict__ Q, const double* x, double* y) {
     const int lane = threadIdx.x & 31;
+    for (int i = lane; i < n; i += 32) {
+        const double* q = Q + (size_t)i * n;
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s = fma(q[j], x[j], s);
+        y[i] = s;
+    }
+    __syncwarp();
+}
+
+// f at x (warp-cooperative, lanes over coordinates); every lane gets the value.
+// Rotated costs evaluate the formula at y = Q x (y: n doubles of workspace).
+__device__ double pcost(int cost, int n, const double* x, const double* Q, double* y) {
+    const int lane = threadIdx.x & 31;
+    if (cost == kRotRastrigin || cost == kRotSchwefel) {
+        protate(n, Q, x, y);
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s += rot_term(cost, y[i]);
+        s = warp_sum(s);
+        return cost == kRotRastrigin ? 10.0 * (double)n + s : -(s / (double)n);
+    }
     double s1 = 0.0, s2 = 0.0;
     for (int k = lane; k < n; k += 32) {
         const double t = x[k];
@@ -57,9 +81,25 @@ __device__ double pcost(int cost, int n, const double* x) {
     return s1;
 }
 
-// gradient of f at x into g (warp-cooperative).
-__device__ void pgrad(int cost, int n, const double* x, double* g) {
+// gradient of f at x into g (warp-cooperative); rotated costs: Q^T g'(y), y = Q x
+// (y, gy: n doubles of workspace each).
+__device__ void pgrad(int cost, int n, const double* x, double* g, const double* Q, double* y, double* gy) {
     const int lane = threadIdx.x & 31;
+    if (cost == kRotRastrigin || cost == kRotSchwefel) {
+        protate(n, Q, x, y);
+        for (int i = lane; i < n; i += 32) {
+            const double t = y[i];
+            gy[i] = cost == kRotRastrigin ? 2.0 * t + 20.0 * CUDART_PI * sin(6.283185307179586 * t)
+                                          : -dh64_schwefel(t) / (double)n;
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s = fma(Q[(size_t)i * n + j], gy[i], s);
+            g[j] = s;
+        }
+        return;
+    }
     if (cost == kAckley) {
         double s1 = 0.0, s2 = 0.0;
         for (int k = lane; k < n; k += 32) { s1 += x[k] * x[k]; s2 += cos(6.283185307179586 * x[k]); }
@@ -86,24 +126,28 @@ __device__ void pgrad(int cost, int n, const double* x, double* g) {
     }
 }
 
-// One warp polishes one start point.  smem per warp: 3 n doubles (x, g, x_new).
-__global__ void pgd_kernel(int cost, int n, const double* __restrict__ lo, const double* __restrict__ hi, int k_points,
-                           const double* __restrict__ x0, double* __restrict__ x_out, double* __restrict__ f_out,
-                           int* __restrict__ it_out, int max_iter, double tol, double armijo_c, int max_halvings) {
+// One warp polishes one start point.  smem per warp: 5 n doubles (x, g, x_new and,
+// for rotated costs, y and g'(y)).
+__global__ void pgd_kernel(int cost, int n, const double* __restrict__ lo, const double* __restrict__ hi,
+                           const double* __restrict__ Q, int k_points, const double* __restrict__ x0,
+                           double* __restrict__ x_out, double* __restrict__ f_out, int* __restrict__ it_out,
+                           int max_iter, double tol, double armijo_c, int max_halvings) {
     extern __shared__ double psm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + warp;
     if (w >= k_points) return;
-    double* x = psm + (size_t)warp * 3 * n;
+    double* x = psm + (size_t)warp * 5 * n;
     double* g = x + n;
     double* xn = g + n;
+    double* y = xn + n;
+    double* gy = y + n;
     for (int k = lane; k < n; k += 32) x[k] = fmin(fmax(x0[(size_t)w * n + k], lo[k]), hi[k]);
     __syncwarp();
-    double f = pcost(cost, n, x);
+    double f = pcost(cost, n, x, Q, y);
     double alpha_next = 1.0;  // first search from 1, later ones from twice the last accepted step
     int it = 0;
     for (; it < max_iter; ++it) {
-        pgrad(cost, n, x, g);
+        pgrad(cost, n, x, g, Q, y, gy);
         __syncwarp();
         double pg = 0.0;
         for (int k = lane; k < n; k += 32) pg = fmax(pg, fabs(fmin(fmax(x[k] - g[k], lo[k]), hi[k]) - x[k]));
@@ -119,7 +163,7 @@ __global__ void pgd_kernel(int cost, int n, const double* __restrict__ lo, const
             }
             slope = warp_sum(slope);
             __syncwarp();
-            fn = pcost(cost, n, xn);
+            fn = pcost(cost, n, xn, Q, y);
             if (fn <= f + armijo_c * slope) { ok = true; break; }
             alpha = 0.5 * alpha;
             __syncwarp();
@@ -197,16 +241,16 @@ __global__ void polish_update_kernel(ProbDev* probs, int problem, const double* 
 
 }  // namespace
 
-size_t pgd_smem_bytes(int n, int warps) { return (size_t)warps * 3 * (size_t)n * sizeof(double); }
+size_t pgd_smem_bytes(int n, int warps) { return (size_t)warps * 5 * (size_t)n * sizeof(double); }
 
-cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, int k, const double* x0, double* x_out,
-                       double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s) {
-    const int warps = 4;
+cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, const double* Q, int k, const double* x0,
+                       double* x_out, double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s) {
+    const int warps = n > 1024 ? 1 : 4;  // 5 n doubles per warp
     const size_t smem = pgd_smem_bytes(n, warps);
     cudaError_t e = cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    pgd_kernel<<<(k + warps - 1) / warps, 32 * warps, smem, s>>>(cost, n, lo, hi, k, x0, x_out, f_out, it_out, max_iter,
-                                                                  tol, 1e-4, 30);
+    pgd_kernel<<<(k + warps - 1) / warps, 32 * warps, smem, s>>>(cost, n, lo, hi, Q, k, x0, x_out, f_out, it_out,
+                                                                  max_iter, tol, 1e-4, 30);
     return cudaGetLastError();
 }
 

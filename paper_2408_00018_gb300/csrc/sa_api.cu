@@ -175,8 +175,8 @@ sa_status check_problem(const sa_problem& pr, const sa_box& box, int32_t n, int6
     if (pr.cost < SA_SCHWEFEL || pr.cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
     if (sch.surrogate && (!is_rot(pr.cost) || n > 4096)) return SA_EINVAL;
     if (is_rot(pr.cost)) {
-        // rotated costs run the FP32 rank-1 sweep; the hybrid polish covers separable costs
-        if (!pr.Q || sch.precision != SA_FP32 || sch.polish_k != 0) return SA_EINVAL;
+        // rotated costs run the FP32 rank-1 sweep
+        if (!pr.Q || sch.precision != SA_FP32) return SA_EINVAL;
         if ((int64_t)n * n > ((int64_t)1 << 28)) return SA_EINVAL;
         for (size_t k = 0; k < (size_t)n * n; ++k)
             if (!std::isfinite(pr.Q[k])) return SA_EINVAL;
@@ -372,8 +372,8 @@ sa_status run_polish(sa_handle* h) {
             launch_topk(h->d_Fcopy, hp.chains, k, h->d_topk, h->stream) != cudaSuccess ||
             launch_gather(h->d_X32, h->d_X64, hp.x_base, hp.chains, hp.n, h->d_topk, k, h->d_px0, h->stream) !=
                 cudaSuccess ||
-            launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, k, h->d_px0, h->d_px, h->d_pf, h->d_pit, 1000, 1e-10,
-                       h->stream) != cudaSuccess ||
+            launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.q64, k, h->d_px0, h->d_px, h->d_pf, h->d_pit, 1000,
+                       1e-10, h->stream) != cudaSuccess ||
             launch_polish_update(h->d_probs, (int)p, h->d_px, h->d_pf, k, h->stream) != cudaSuccess)
             return fail(h, SA_ECUDA);
     }
@@ -886,29 +886,36 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
                     void* stream) {
     if (n < 1 || k < 1 || k > 1024 || !lo || !hi || !x0 || !x_out || !f_out || max_iter < 0 || !(tol >= 0.0))
         return SA_EINVAL;
-    if (cost < SA_SCHWEFEL || cost > SA_ROSENBROCK || Q) return SA_EINVAL;  // rotated costs: not in this call yet
+    if (cost < SA_SCHWEFEL || cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
+    const bool rot = is_rot(cost);
+    if (rot != (Q != nullptr) || (rot && (int64_t)n * n > ((int64_t)1 << 28))) return SA_EINVAL;
     for (int d = 0; d < n; ++d)
         if (!std::isfinite(lo[d]) || !std::isfinite(hi[d]) || lo[d] > hi[d]) return SA_EINVAL;
+    if (rot)
+        for (size_t e = 0; e < (size_t)n * n; ++e)
+            if (!std::isfinite(Q[e])) return SA_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    double *dlo = nullptr, *dhi = nullptr, *dx0 = nullptr, *dx = nullptr, *df = nullptr;
+    double *dlo = nullptr, *dhi = nullptr, *dx0 = nullptr, *dx = nullptr, *df = nullptr, *dq = nullptr;
     int* dit = nullptr;
     const size_t kn = (size_t)k * n;
     sa_status st = SA_OK;
-    if (cudaMallocAsync(&dlo, n * sizeof(double), s) || cudaMallocAsync(&dhi, n * sizeof(double), s) ||
+    if ((rot && cudaMallocAsync(&dq, (size_t)n * n * sizeof(double), s)) ||
+        cudaMallocAsync(&dlo, n * sizeof(double), s) || cudaMallocAsync(&dhi, n * sizeof(double), s) ||
         cudaMallocAsync(&dx0, kn * sizeof(double), s) || cudaMallocAsync(&dx, kn * sizeof(double), s) ||
         cudaMallocAsync(&df, k * sizeof(double), s) || cudaMallocAsync(&dit, k * sizeof(int), s))
         st = SA_ENOMEM;
     if (st == SA_OK &&
-        (cudaMemcpyAsync(dlo, lo, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
+        ((rot && cudaMemcpyAsync(dq, Q, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+         cudaMemcpyAsync(dlo, lo, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
          cudaMemcpyAsync(dhi, hi, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
          cudaMemcpyAsync(dx0, x0, kn * sizeof(double), cudaMemcpyHostToDevice, s) ||
-         launch_pgd(cost, n, dlo, dhi, k, dx0, dx, df, dit, max_iter, tol, s) ||
+         launch_pgd(cost, n, dlo, dhi, dq, k, dx0, dx, df, dit, max_iter, tol, s) ||
          cudaMemcpyAsync(x_out, dx, kn * sizeof(double), cudaMemcpyDeviceToHost, s) ||
          cudaMemcpyAsync(f_out, df, k * sizeof(double), cudaMemcpyDeviceToHost, s) ||
          (iters_out && cudaMemcpyAsync(iters_out, dit, k * sizeof(int), cudaMemcpyDeviceToHost, s)) ||
          cudaStreamSynchronize(s)))
         st = SA_ECUDA;
-    for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit})
+    for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit, (void*)dq})
         if (p) cudaFreeAsync(p, s);
     cudaGetLastError();
     return st;

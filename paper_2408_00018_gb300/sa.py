@@ -363,8 +363,9 @@ def create_batch(problems, L, schedule: Schedule | None = None, seed: int = 0, s
     return BatchHandle(out, ns.tolist(), cs.tolist(), L, schedule)
 
 
-def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, stream=None):
-    """sa_polish: box-projected gradient descent from each row of x0 (k x n); returns (x, f, iters)."""
+def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, Q=None, stream=None):
+    """sa_polish: box-projected gradient descent from each row of x0 (k x n); returns (x, f, iters).
+    Rotated costs take Q (n x n)."""
     x0 = np.ascontiguousarray(np.atleast_2d(np.asarray(x0, np.float64)))
     k, n = x0.shape
     lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
@@ -373,8 +374,10 @@ def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, stream=No
     f = np.zeros(k)
     it = np.zeros(k, np.int32)
     s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
     _check(load().sa_polish(COSTS[cost] if isinstance(cost, str) else int(cost), n, lo.ctypes.data, hi.ctypes.data,
-                            None, k, x0.ctypes.data, max_iter, tol, x.ctypes.data, f.ctypes.data, it.ctypes.data, s),
+                            None if Qa is None else Qa.ctypes.data, k, x0.ctypes.data, max_iter, tol, x.ctypes.data,
+                            f.ctypes.data, it.ctypes.data, s),
            "sa_polish")
     return x, f, it
 

@@ -310,3 +310,20 @@ def test_pgd_polishes_to_closed_form_minima():
     pg = np.clip(x - g, 0.6, 5.0) - x
     # Armijo stops once f can no longer decrease in FP64 (curvature ~ 400 here)
     assert np.abs(pg).max() < 1e-6
+
+
+def test_pgd_rotated_reduces_to_unrotated():
+    """Rotated PGD with Q = I is the unrotated PGD; with a permutation Q it is the
+    unrotated PGD of the permuted problem (Rastrigin is separable and symmetric)."""
+    rng = np.random.default_rng(9)
+    n = 6
+    lo, hi = np.full(n, -5.12), np.full(n, 5.12)
+    x0 = rng.uniform(-1.0, 1.0, n)
+    xa, fa, ia = oracle.pgd("rot_rastrigin", x0, lo, hi, Q=np.eye(n))
+    xb, fb, ib = oracle.pgd("rastrigin", x0, lo, hi)
+    assert fa == fb and np.array_equal(xa, xb) and ia == ib
+    perm = rng.permutation(n)
+    P = np.eye(n)[perm]
+    xc, fc, _ = oracle.pgd("rot_rastrigin", x0, lo, hi, Q=P)
+    xd, fd, _ = oracle.pgd("rastrigin", x0[perm], lo, hi)
+    assert abs(fc - fd) <= 1e-12 and np.allclose(xc[perm], xd, atol=1e-12, rtol=0)
