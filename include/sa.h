@@ -236,9 +236,10 @@ sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_
  * f~(x))) / T)) using the sweep's u3.  f~ = mu + sigma MLP((x - mid) / half),
  * the network of sa_mlp_*, is re-initialised at level 0 of every run (seed of
  * the handle), trained before each later level by 128 Adam steps (batches of
- * 4096 drawn from a ring buffer of the last ~2^20 chain states -- taken 4 times
- * per level, evenly spaced -- and their values, targets standardised by the
- * buffer's mean and deviation) and frozen
+ * 4096, half drawn from a ring buffer of the last ~2^20 chain states -- taken 4
+ * times per level, evenly spaced -- and half from the previous level's states,
+ * with their values; targets standardised by the buffer's mean and deviation)
+ * and frozen
  * during the level.  sa_da_trace returns, for a traced completed level, the
  * surrogate's value at every chain's start state (ft0_out: host [chains]) and
  * at every proposal (ftp_out: host [L * chains], step-major); either may be

@@ -115,9 +115,8 @@ __global__ void da_patch_kernel(SweepArgs A, DaDev D, int s) {
     const int level = A.run->level;
     const int n = P.n;
     const double T = A.T_tab[level];
-    const float sig = P.sig_u * (float)A.s_tab[level];
     const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
-    const RotMove mv = rot_propose(w, D.xf + (size_t)c * n, n, sig, P.lo_u, P.hi_u, A.boundary,
+    const RotMove mv = rot_propose(w, D.xf + (size_t)c * n, P, (float)A.s_tab[level], A.boundary,
                                    (float)(-T * 0.69314718055994531));
     D.xs[(size_t)c * D.np + mv.d] = std_bf16(mv.xp, D.mid[mv.d], D.inv_half[mv.d]);
 }
@@ -128,13 +127,12 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     const int lane = threadIdx.x & 31;
     const int n = P.n;
     const double T = A.T_tab[level];
-    const float sig = P.sig_u * (float)A.s_tab[level];
     float* x = D.xf + (size_t)c * n;
     float* yh = D.yh + (size_t)c * n;
     float* yl = D.yl + (size_t)c * n;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
     const float neg_T_ln2 = (float)(-T * 0.69314718055994531);
-    const RotMove mv = rot_propose(w, x, n, sig, P.lo_u, P.hi_u, A.boundary, neg_T_ln2);
+    const RotMove mv = rot_propose(w, x, P, (float)A.s_tab[level], A.boundary, neg_T_ln2);
     // surrogate at the proposal (fixed summation order) and at the current state
     const float* q = D.part + (size_t)c * 4;
     const float ftp = D.ms[0] + D.ms[1] * (((q[0] + q[1]) + q[2]) + q[3] + D.b3[0]);
@@ -335,12 +333,16 @@ __global__ void da_stats_kernel(SweepArgs A, DaDev D) {
     }
 }
 
-// One training batch: rows drawn uniformly from the filled buffer (Philox stream
-// tag 4, counter (row, epoch step, level, problem)), standardised inputs and targets.
+// One training batch (Philox stream tag 4, counter (row, epoch step, level,
+// problem)): even rows uniformly from the filled buffer, odd rows from the states
+// the previous level inserted (the region the chains are in now); standardised
+// inputs and targets.
 __global__ void da_sample_kernel(SweepArgs A, DaDev D, int e) {
     const ProbDev& P = A.probs[D.problem];
     const int level = A.run->level;
     const int64_t filled = min((int64_t)level * kDaInserts * P.chains, (int64_t)D.cap);
+    const int64_t recent = min((int64_t)kDaInserts * P.chains, filled);
+    const int64_t recent0 = ((int64_t)(level > 0 ? level - 1 : 0) * kDaInserts * P.chains) % D.cap;
     const int n = P.n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)D.batch * D.np;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -349,7 +351,8 @@ __global__ void da_sample_kernel(SweepArgs A, DaDev D, int e) {
         int64_t j = 0;
         if (filled > 0) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)e, (uint32_t)level, P.pid), D.tkey0, D.tkey1);
-            j = (int64_t)((((uint64_t)w.y << 32) | w.x) % (uint64_t)filled);
+            const uint64_t r = ((uint64_t)w.y << 32) | w.x;
+            j = (b & 1) ? (recent0 + (int64_t)(r % (uint64_t)recent)) % D.cap : (int64_t)(r % (uint64_t)filled);
             if (k < n) v = (D.rx[(size_t)j * n + k] - D.mid[k]) * D.inv_half[k];
         }
         D.work.Xb[t] = __float2bfloat16_rn(v);

@@ -92,35 +92,56 @@ __global__ void head_bwd_kernel(const float* __restrict__ y, const float* __rest
     (void)Bp;
 }
 
-// Column reductions over the batch, in row order: dw3_j = sum_b dy_b g(Z2_bj),
-// db2_j = sum_b dy_b w3_j g'(Z2_bj), and (second call) db1_j = sum_b dA1_bj g'(Z1_bj)
-// together with dZ1 = dA1 o g'(Z1) as BF16.
-__global__ void col_head_kernel(const float* __restrict__ Z2, const float* __restrict__ dy, const float* __restrict__ w3,
-                                int Bp, float* dw3, float* db2) {
+// Column reductions over the batch: rows are split into chunks of kRowChunk
+// (one block column of threads per chunk, rows in order inside a chunk), and a
+// second pass adds the chunks' partial sums in chunk order, so the result does
+// not depend on scheduling.
+//   head:  dw3_j = sum_b dy_b g(Z2_bj),  db2_j = sum_b dy_b w3_j g'(Z2_bj)
+//   layer 1:  db1_j = sum_b dA1_bj g'(Z1_bj)
+constexpr int kRowChunk = 64;
+
+__global__ void col_head_part_kernel(const float* __restrict__ Z2, const float* __restrict__ dy,
+                                     const float* __restrict__ w3, int Bp, float* part) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
     if (j >= kH) return;
     float s3 = 0.0f, s2 = 0.0f;
-    for (int b = 0; b < Bp; ++b) {
+    const int b1 = min(Bp, (chunk + 1) * kRowChunk);
+    for (int b = chunk * kRowChunk; b < b1; ++b) {
         const float z = Z2[(size_t)b * kH + j];
         s3 = fmaf(dy[b], gelu(z), s3);
         s2 = fmaf(dy[b] * w3[j], gelu_grad(z), s2);
     }
-    dw3[j] = s3;
-    db2[j] = s2;
+    part[((size_t)chunk * 2 + 0) * kH + j] = s3;
+    part[((size_t)chunk * 2 + 1) * kH + j] = s2;
+}
+
+__global__ void col_b1_part_kernel(const float* __restrict__ dA1, const float* __restrict__ Z1, int Bp, float* part) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    if (j >= kH) return;
+    float s = 0.0f;
+    const int b1 = min(Bp, (chunk + 1) * kRowChunk);
+    for (int b = chunk * kRowChunk; b < b1; ++b) s = fmaf(dA1[(size_t)b * kH + j], gelu_grad(Z1[(size_t)b * kH + j]), s);
+    part[(size_t)chunk * kH + j] = s;
+}
+
+// out_v[j] = sum over chunks (in order) of part[(chunk * stride + v) * kH + j], for v < nv.
+__global__ void col_finish_kernel(const float* __restrict__ part, int chunks, int stride, int nv, float* out0,
+                                  float* out1) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kH) return;
+    for (int v = 0; v < nv; ++v) {
+        float s = 0.0f;
+        for (int c = 0; c < chunks; ++c) s += part[((size_t)c * stride + v) * kH + j];
+        (v == 0 ? out0 : out1)[j] = s;
+    }
 }
 
 __global__ void dz1_kernel(const float* __restrict__ dA1, const float* __restrict__ Z1, int Bp, __nv_bfloat16* dZ1b) {
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < (int64_t)Bp * kH;
          u += (int64_t)gridDim.x * blockDim.x)
         dZ1b[u] = __float2bfloat16_rn(dA1[u] * gelu_grad(Z1[u]));
-}
-
-__global__ void col_b1_kernel(const float* __restrict__ dA1, const float* __restrict__ Z1, int Bp, float* db1) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= kH) return;
-    float s = 0.0f;
-    for (int b = 0; b < Bp; ++b) s = fmaf(dA1[(size_t)b * kH + j], gelu_grad(Z1[(size_t)b * kH + j]), s);
-    db1[j] = s;
 }
 
 // W1's gradient: the first n of the np columns of dW1full; the loss and db3 (one block).
@@ -228,7 +249,9 @@ cudaError_t mlp_loss_grad(const MlpDev& m, const void* Xb, int B, int Bp, const 
     if (e == cudaSuccess) e = mlp_finish_y(m, w.part, Bp, w.y, s);
     if (e != cudaSuccess) return e;
     head_bwd_kernel<<<Bp, 128, 0, s>>>(w.y, t, B, Bp, w.Z2, m.p + o.w3, w.dy, w.dZ2b);
-    col_head_kernel<<<kH / 128, 128, 0, s>>>(w.Z2, w.dy, m.p + o.w3, Bp, grad + o.w3, grad + o.b2);
+    const int chunks = (Bp + kRowChunk - 1) / kRowChunk;
+    col_head_part_kernel<<<dim3(kH / 128, chunks), 128, 0, s>>>(w.Z2, w.dy, m.p + o.w3, Bp, w.colpart);
+    col_finish_kernel<<<kH / 128, 128, 0, s>>>(w.colpart, chunks, 2, 2, grad + o.w3, grad + o.b2);
     loss_kernel<<<1, 256, 0, s>>>(w.y, t, w.dy, B, Bp, loss, grad + o.b3);
     const dim3 tb(32, 8);
     transpose_kernel<<<dim3(kH / 32, Bp / 32), tb, 0, s>>>(w.dZ2b, Bp, kH, w.dZ2T);
@@ -241,7 +264,8 @@ cudaError_t mlp_loss_grad(const MlpDev& m, const void* Xb, int B, int Bp, const 
     if (e == cudaSuccess) e = launch_gemm_bf16_f32(w.dZ2b, kH, m.W2tb, kH, w.dA1, kH, Bp, kH, kH, status, s);
     if (e != cudaSuccess) return e;
     dz1_kernel<<<grid_for((int64_t)Bp * kH), 256, 0, s>>>(w.dA1, w.Z1, Bp, w.dZ1b);
-    col_b1_kernel<<<kH / 128, 128, 0, s>>>(w.dA1, w.Z1, Bp, grad + o.b1);
+    col_b1_part_kernel<<<dim3(kH / 128, chunks), 128, 0, s>>>(w.dA1, w.Z1, Bp, w.colpart);
+    col_finish_kernel<<<kH / 128, 128, 0, s>>>(w.colpart, chunks, 1, 1, grad + o.b1, nullptr);
     transpose_kernel<<<dim3(kH / 32, Bp / 32), tb, 0, s>>>(w.dZ1b, Bp, kH, w.dZ1T);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // dW1 = dZ1^T X (K = batch), then its first n columns
@@ -265,8 +289,9 @@ cudaError_t mlp_pack(const float* X, int B, int n, int Bp, int np, void* Xb, cud
 
 size_t mlp_work_bytes(int Bp, int np) {
     const size_t b = (size_t)Bp;
+    const size_t chunks = (b + kRowChunk - 1) / kRowChunk;
     return b * np * 2 * 2 + b * kH * (4 + 2 + 2 + 4 + 2 + 2 + 4 + 2 + 2) + b * (4 + 4 + 4 * 4) + (size_t)kH * np * 4 +
-           16 * 256;
+           chunks * 2 * kH * 4 + 16 * 256;
 }
 
 void mlp_work_carve(void* base, int Bp, int np, MlpWork& w) {
@@ -291,6 +316,7 @@ void mlp_work_carve(void* base, int Bp, int np, MlpWork& w) {
     w.dy = static_cast<float*>(take(b * 4));
     w.part = static_cast<float*>(take(b * 4 * 4));
     w.dW1 = static_cast<float*>(take((size_t)kH * np * 4));
+    w.colpart = static_cast<float*>(take(((b + kRowChunk - 1) / kRowChunk) * 2 * kH * 4));
 }
 
 }  // namespace sa

@@ -65,10 +65,15 @@ struct RotMove {
     float xo, xp, dh, dl, tau;
     uint32_t w3;  // the word of u3
 };
-__device__ __forceinline__ RotMove rot_propose(uint4 w, const float* x, int n, float sig, float lo, float hi, int boundary,
+// P: the box (uniform scalars, or per coordinate when P.uniform == 0); sl = sqrt(T / T0).
+__device__ __forceinline__ RotMove rot_propose(uint4 w, const float* x, const ProbDev& P, float sl, int boundary,
                                                float neg_T_ln2) {
     RotMove m;
+    const int n = P.n;
     m.d = coord_of(w.x, n);
+    float sig, lo, hi;
+    if (P.uniform) { sig = P.sig_u * sl; lo = P.lo_u; hi = P.hi_u; }
+    else { sig = P.sig32[m.d] * sl; lo = P.lo32[m.d]; hi = P.hi32[m.d]; }
     const float r = sqrt_approx(-1.3862943611198906f * __log2f(u23f(w.y)));
     const float z = -r * __cosf(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
     m.tau = neg_T_ln2 * __log2f(u23f(w.w));

@@ -189,6 +189,7 @@ struct MlpWork {
     float* dy;        // [Bp]
     float* part;      // [Bp x 4] partial output sums
     float* dW1;       // [512 x np]
+    float* colpart;   // [ceil(Bp / 64) x 2 x 512] partial column sums
 };
 
 cudaError_t mlp_cast(const MlpDev& m, cudaStream_t s);

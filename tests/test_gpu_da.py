@@ -39,12 +39,16 @@ def _create(sa, cost, n, C, L, K, T0, rho, seed, Q, trace_levels=0, surrogate=1,
     return sa.create(cost, lo, hi, n, C, L, sch, seed=seed, Q=Q)
 
 
-@pytest.mark.parametrize("cost,n,C", [("rot_schwefel", 64, 256), ("rot_rastrigin", 40, 130)])
-def test_da_decisions_match_oracle_replay(sa, cost, n, C):
+@pytest.mark.parametrize("cost,n,C,box", [("rot_schwefel", 64, 256, "uniform"), ("rot_rastrigin", 40, 130, "uniform"),
+                                          ("rot_schwefel", 24, 70, "per-coordinate")])
+def test_da_decisions_match_oracle_replay(sa, cost, n, C, box):
     L, K, T0, rho, seed = 150, 3, 30.0, 0.6, 4
     Q = inputs.rotation(n, 2)
-    h = _create(sa, cost, n, C, L, K, T0, rho, seed, Q, trace_levels=K)
     lo, hi = inputs.box(cost, n)
+    if box != "uniform":
+        lo, hi = lo * np.linspace(0.4, 1.0, n), hi * np.linspace(1.0, 0.6, n)
+    sch = sa.Schedule(T0=T0, rho=rho, levels=K, sigma_frac=0.1, precision="fp32", trace_levels=K, surrogate=1)
+    h = sa.create(cost, lo, hi, n, C, L, sch, seed=seed, Q=Q)
     p = oracle.Problem(cost, n, lo, hi, chains=C, L=L, T0=T0, rho=rho, seed=seed, Q=Q, mode=1)
     start = lambda c: p.init_point(c).astype(np.float32).astype(np.float64)
     total_full = total = 0
@@ -82,7 +86,7 @@ def test_trained_surrogate_predicts_true_differences(sa):
     for level in range(K):
         h.run(1)
         X, F = h.trace_states(level)
-        if level in (0, K - 1):
+        if level in (0, K - 2, K - 1):
             ft0, ftp = h.da_trace(level)
             a, b = [], []
             for c in range(0, C, 8):
@@ -100,7 +104,8 @@ def test_trained_surrogate_predicts_true_differences(sa):
             corr[level] = float(np.corrcoef(a, b)[0, 1])
         pstar = int(h.level_log()["argmin"][level])
         start = lambda c, xr=X[pstar].copy(): xr
-    assert corr[K - 1] > 0.35 and corr[K - 1] > corr[0] + 0.3, corr
+    trained = 0.5 * (corr[K - 2] + corr[K - 1])
+    assert trained > 0.3 and min(corr[K - 2], corr[K - 1]) > corr[0] + 0.25, corr
 
 
 def test_surrogate_saves_true_evaluations_against_plain(sa):

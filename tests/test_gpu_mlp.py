@@ -56,7 +56,7 @@ def test_forward_matches_oracle(env, n, B):
     assert not b1.any() and not b2.any() and b3[0] == 0.0
 
 
-@pytest.mark.parametrize("n,B", [(128, 512), (20, 300)])
+@pytest.mark.parametrize("n,B", [(128, 512), (20, 300), (128, 4096)])
 def test_loss_and_gradient_match_oracle(env, n, B):
     sa, torch = env
     P = sa.mlp_param_count(n)

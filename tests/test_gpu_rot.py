@@ -172,3 +172,38 @@ def test_rot_rejects_bad_arguments(sa):
     Qn[2, 3] = np.nan
     with pytest.raises(sa.SAError):
         sa.create("rot_rastrigin", lo, hi, n, 64, 10, sa.Schedule(precision="fp32"), Q=Qn)
+
+
+def _level0_vs_oracle(sa, cost, n, C, L, T0, seed, Q, lo, hi, boundary="reflect"):
+    sch = sa.Schedule(T0=T0, rho=0.5, levels=1, sigma_frac=0.1, precision="fp32", trace_levels=1, boundary=boundary)
+    h = sa.create(cost, lo, hi, n, C, L, sch, seed=seed, Q=Q)
+    h.run()
+    X, F = h.trace_states(0)
+    p = oracle.Problem(cost, n, lo, hi, chains=C, L=L, T0=T0, rho=0.5, seed=seed, Q=Q, mode=1, boundary=boundary)
+    full = _check_level(p, 0, X, F, h.trace(0), L, lambda c: p.init_point(c).astype(np.float32).astype(np.float64),
+                        range(C))
+    assert int(h.level_log()["argmin"][0]) == int(np.argmin(F))
+    assert (X >= lo).all() and (X <= hi).all()
+    return full
+
+
+@pytest.mark.parametrize("cost", ["rot_rastrigin", "rot_schwefel"])
+def test_rot_per_coordinate_box(sa, cost):
+    """A box with a different interval per coordinate (the proposal scale and the
+    reflection follow the coordinate's own interval)."""
+    n, C, L = 20, 96, 150
+    base_lo, base_hi = inputs.box(cost, n)
+    lo = base_lo * np.linspace(0.3, 1.0, n)
+    hi = base_hi * np.linspace(1.0, 0.5, n)
+    full = _level0_vs_oracle(sa, cost, n, C, L, 20.0, 3, inputs.rotation(n, 5), lo, hi)
+    assert full >= 0.9 * C
+
+
+@pytest.mark.parametrize("cost", ["rot_rastrigin", "rot_schwefel"])
+def test_rot_degenerate_shapes(sa, cost):
+    # n = 1 (Q = [-1]), a single chain with a single step, and the clip-only boundary
+    lo1, hi1 = inputs.box(cost, 1)
+    assert _level0_vs_oracle(sa, cost, 1, 33, 50, 10.0, 1, -np.eye(1), lo1, hi1) >= 0.9 * 33
+    lo, hi = inputs.box(cost, 7)
+    assert _level0_vs_oracle(sa, cost, 7, 1, 1, 10.0, 2, inputs.rotation(7, 1), lo, hi) == 1
+    assert _level0_vs_oracle(sa, cost, 7, 70, 120, 50.0, 4, inputs.rotation(7, 2), lo, hi, boundary="clip") >= 63
