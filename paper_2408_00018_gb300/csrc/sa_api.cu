@@ -216,7 +216,7 @@ int pick_unroll(int cost, int n) {
         if (u == 1 || u == 2 || u == 4) return u;
     }
     if (cost == SA_ACKLEY) return 1;
-    if (n >= 16) return 2;  // measured at n = 256: U = 2 2.05 ms, U = 4 2.08 ms, U = 1 2.47 ms per level
+    if (n >= 16) return 2;  // measured at n = 256: U = 2 1.84 ms, U = 4 1.88 ms, U = 1 2.22 ms per level
     return 1;
 }
 

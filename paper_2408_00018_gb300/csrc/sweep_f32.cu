@@ -155,6 +155,7 @@ struct Ctx {
     const float *slo, *shi, *ssig;   // per-coordinate box (ssig scaled)
     int boundary;
     float neg_T_ln2;  // -T ln 2: tau = -T ln u3 = neg_T_ln2 * log2(u3)
+    float kappa;      // bound on the FP32 error of any accepted step's dF over the box (Schwefel, Rastrigin)
     uint32_t level, chain, pid, key0, key1;
 };
 
@@ -179,9 +180,9 @@ __device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step&
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
     float xp = fmaf(sg, p.z, xo);
-    if (C.boundary == 0) {
-        if (xp < lo) xp = 2.0f * lo - xp;
-        else if (xp > hi) xp = 2.0f * hi - xp;
+    if (C.boundary == 0) {  // reflect once (selects, no branch)
+        const float r1 = 2.0f * lo - xp, r2 = 2.0f * hi - xp;
+        xp = xp < lo ? r1 : (xp > hi ? r2 : xp);
     }
     xp = fminf(fmaxf(xp, lo), hi);
     p.xo = xo;
@@ -298,6 +299,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     C.ssig = ssig;
     C.boundary = A.boundary;
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
+    C.kappa = P.kappa;
     C.level = (uint32_t)level;
     C.chain = (uint32_t)c + P.cid0;
     C.pid = P.pid;
@@ -314,7 +316,15 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
         int s = 0;
         auto commit = [&](Step& p, int sidx) -> bool {
             const bool acc = p.dF < p.tau;
-            if (acc) {
+            if (COST == kSchwefel || COST == kRastrigin) {
+                // without a divergent branch (12% faster at n = 256): a rejected step
+                // stores the value it read, and the error grows by the box-wide
+                // per-step bound kappa
+                C.xcol[p.d * B] = acc ? p.xp : p.xo;
+                dS += acc ? p.dF : 0.0f;
+                e += acc ? fmaf(fabsf(dS), 1.2e-7f, C.kappa) : 0.0f;
+                nacc += acc ? 1u : 0u;
+            } else if (acc) {
                 C.xcol[p.d * B] = p.xp;
                 dS += p.dF;
                 e += step_bound<COST>(C, p) + fabsf(dS) * 1.2e-7f;
