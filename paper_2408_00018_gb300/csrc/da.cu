@@ -139,10 +139,21 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     const float ftc = D.fts[c];
     const bool tracing = level < A.trace_levels;
     if (tracing && D.trace_ftp && lane == 0) D.trace_ftp[((size_t)level * A.L + s) * P.chains + c] = ftp;
-    // ---- stage 1 (surrogate only), decided in FP64
+    // ---- stage 1 (surrogate only): u < exp(-dFs/T), i.e. dFs < tau1 = -T ln u, taken in
+    // FP32 with a margin for the error of tau1 and in FP64 inside the margin (the
+    // same decision as the FP64 test, without an FP64 exp per lane and step)
     const double dFs = (double)ftp - (double)ftc;
     const uint4 wd = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), D.dkey0, D.dkey1);
-    const bool pass1 = dFs <= 0.0 || u23d(wd.x) < exp(-dFs / T);
+    bool pass1;
+    if (dFs <= 0.0) {
+        pass1 = true;
+    } else {
+        const double tau1 = (double)(neg_T_ln2 * __log2f(u23f(wd.x)));
+        const double m1 = 1.0e-6 * tau1 + 4.0e-7 * T;
+        if (dFs < tau1 - m1) pass1 = true;
+        else if (dFs > tau1 + m1) pass1 = false;
+        else pass1 = u23d(wd.x) < exp(-dFs / T);
+    }
     bool acc = false;
     if (pass1) {
         ++nev;
@@ -171,7 +182,6 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
         if (acc) {
             float edrift = 0.0f;
             rot_update<COST>(P, yh, yl, mv.d, mv.dh, mv.dl, n, lane, edrift);
-            edrift = rot_wsumf(edrift);
             if (lane == 0) {
                 x[mv.d] = mv.xp;
                 D.Fa[c] += dF_used;

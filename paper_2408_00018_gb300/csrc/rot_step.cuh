@@ -107,7 +107,7 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
                                            int lane, float& dF, float& B) {
     const float* qcol = P.qt_hi + (size_t)d * n;
     const float nsum = ((float)((n + 31) / 32) + 6.0f) * 1.2e-7f;  // summation rounding per unit of sum |t_i|
-    float sum = 0.0f, sabs = 0.0f, bnd = 0.0f;
+    float sum = 0.0f, bnd = 0.0f;
     if (COST == kRotRastrigin) {
         const bool any_big = fabsf(dh) * P.qmax * 3.14159265f >= 0.5f;  // some |pi Delta_i| may reach 1/2
         for (int i = lane; i < n; i += 32) {
@@ -123,15 +123,14 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
             }
             const float t = fmaf(Dl, fmaf(2.0f, yv, Dl), 20.0f * s1 * s2);
             sum += t;
-            sabs += fabsf(t);
             const float aD = fabsf(Dl);
-            bnd = fmaf(aD, fmaf(fabsf(yv), 9.0e-7f, fmaf(aD, 6.0e-5f, c)), bnd);
+            // the term's error plus its share of the summation's rounding
+            bnd = fmaf(aD, fmaf(fabsf(yv), 9.0e-7f, fmaf(aD, 6.0e-5f, c)), fmaf(nsum, fabsf(t), bnd));
         }
         sum = rot_wsumf(sum);
-        sabs = rot_wsumf(sabs);
         bnd = rot_wsumf(bnd);
         dF = sum;
-        B = 1.01f * (bnd + nsum * sabs);
+        B = 1.01f * bnd;
     } else {
         // caps of the square roots' argument errors, valid for every coordinate of
         // this move (|y| <= ymax over the box, |Delta_i| <= |dh| qmax):
@@ -156,7 +155,6 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
             const float y2S2 = 2.0f * yv * S2;
             const float t = fmaf(Dl, Sa, y2S2 * C);
             sum += t;
-            sabs += fabsf(t);
             // errors of a and b from their arguments' errors (the pair's low part,
             // the rounding of y', the rounding of the move) and of the square roots
             const float ep = 6.0e-8f * (ap + ay) + 1.8e-7f * fabsf(Dl);
@@ -169,14 +167,13 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
             const float eS2 = eD + (small ? 2.4e-7f * fabsf(hh) : 2.0e-6f);
             const float e1 = fabsf(Dl) * (2.4e-6f + ea);
             const float e2 = 2.0f * ay * (fabsf(S2) * (2.0e-6f + 0.5f * (ea + eb)) + eS2);
-            bnd += 1.5f * (e1 + e2) + 3.6e-7f * (fabsf(Dl * Sa) + fabsf(y2S2));
+            bnd += fmaf(nsum, fabsf(t), 1.5f * (e1 + e2) + 3.6e-7f * (fabsf(Dl * Sa) + fabsf(y2S2)));
         }
         sum = rot_wsumf(sum);
-        sabs = rot_wsumf(sabs);
         bnd = rot_wsumf(bnd);
         const float inv_n = 1.0f / (float)n;
         dF = -sum * inv_n;
-        B = 1.01f * ((bnd + nsum * sabs) * inv_n + 2.4e-7f * fabsf(dF));
+        B = 1.01f * (bnd * inv_n + 2.4e-7f * fabsf(dF));
     }
 }
 
@@ -200,15 +197,19 @@ __device__ __forceinline__ double rot_eval64(const ProbDev& P, const float* yh, 
     return COST == kRotRastrigin ? s64 : -(s64 / (double)n);
 }
 
-// (yh, yl) += (dh + dl)(Q_hi + Q_lo)[:, d]; edrift accumulates (per lane) a bound
-// on the change of F caused by the update's rounding (2^-45 (|y'| + |Delta|) per
-// coordinate times |g'|).
+// (yh, yl) += (dh + dl)(Q_hi + Q_lo)[:, d]; edrift (every lane) grows by a bound
+// on the change of F caused by the update's rounding: 2^-45 (|y'| + |Delta|) per
+// coordinate times |g'|, taken at |y| <= ymax, |Delta| <= |dh| qmax over the n
+// coordinates.
 template <int COST>
 __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* yl, int d, float dh, float dl, int n,
                                            int lane, float& edrift) {
     const float* qcol = P.qt_hi + (size_t)d * n;
     const float* qlcol = P.qt_lo + (size_t)d * n;
-    const float inv_n = 1.0f / (float)n;
+    const float ym = P.ymax, dm = fabsf(dh) * P.qmax;
+    const float gmax = COST == kRotRastrigin ? fmaf(2.0f, ym + dm, 64.0f)
+                                             : fmaf(0.5f, sqrt_approx(ym + dm), 1.0f) / (float)n;
+    edrift = fmaf((float)n * gmax, (ym + 2.0f * dm) * 2.9e-14f, edrift);
     for (int i = lane; i < n; i += 32) {
         const float qh = qcol[i], ql = qlcol[i];
         const float ph = dh * qh;
@@ -222,9 +223,6 @@ __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* y
         const float nh = sh + lo2;
         yh[i] = nh;
         yl[i] = lo2 - (nh - sh);
-        const float an = fabsf(nh);
-        const float gp = COST == kRotRastrigin ? fmaf(2.0f, an, 64.0f) : fmaf(0.5f, sqrt_approx(an), 1.0f) * inv_n;
-        edrift = fmaf(gp, (an + fabsf(ph)) * 2.9e-14f, edrift);
     }
 }
 

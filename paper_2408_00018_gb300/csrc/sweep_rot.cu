@@ -56,7 +56,7 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
 
     // ---- state at the start of the level
     double Fs;
-    float edrift = 0.0f;  // bound on the FP64 value drift of the pair updates (per lane)
+    float edrift = 0.0f;  // bound on the FP64 value drift of the pair updates (the same in every lane)
     if (level == 0) {
         const float* xr = P.x0 + (size_t)c * n;
         const float2* yr = P.y0 + (size_t)c * n;
@@ -130,7 +130,7 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
     }
     RotEnd r;
     r.Fa = Fs + dS;
-    r.ec = e + (double)rot_wsumf(edrift) + 1e-13 * (fabs(Fs) + fabs(dS) + 1.0);
+    r.ec = e + (double)edrift + 1e-13 * (fabs(Fs) + fabs(dS) + 1.0);
     r.nacc = nacc;
     r.nre = nre;
     return r;
