@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--workload", choices=WORKLOADS, default="schwefel_n256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling runs only)")
+    ap.add_argument("--independent", action="store_true",
+                    help="asynchronous chains (no exchange between levels; the paper's V1), single-problem workloads")
     return ap.parse_args()
 
 
@@ -72,9 +74,10 @@ def parse():
 class Workload:
     """One workload: how to build its handle and what one run amounts to."""
 
-    def __init__(self, name, levels_override=0):
+    def __init__(self, name, levels_override=0, independent=False):
         from paper_2408_00018_gb300 import inputs
         self.name = name
+        self.independent = bool(independent)
         if name in ("schwefel_n256", "schwefel_n2") or name in ROT_WORKLOADS:
             if name in ROT_WORKLOADS:
                 cfg = dict(getattr(inputs, ROT_WORKLOADS[name]))
@@ -103,7 +106,7 @@ class Workload:
 
     def schedule(self, sa):
         return sa.Schedule(T0=self.T0, rho=self.rho, levels=self.K, sigma_frac=self.sigma_frac,
-                           precision=self.precision)
+                           precision=self.precision, independent=1 if self.independent else 0)
 
     def create(self, sa, tune=True):
         if self.batch:
@@ -123,8 +126,9 @@ class Workload:
         return 1 + 2 * rot + self.K * (groups + 2 + rot)
 
     def config(self):
-        c = {"workload": self.tag, "L": self.L, "levels": self.K, "T0": self.T0, "rho": self.rho, "seed": self.seed,
-             "steps_per_run": self.steps_per_run, "argmin": "f64"}
+        c = {"workload": self.tag + ("_async" if self.independent else ""), "L": self.L, "levels": self.K,
+             "T0": self.T0, "rho": self.rho, "seed": self.seed, "steps_per_run": self.steps_per_run, "argmin": "f64",
+             "exchange": "none (asynchronous chains)" if self.independent else "restart from the level's best"}
         if self.batch:
             c.update({"problems": len(self.problems), "chains_total": sum(p["chains"] for p in self.problems),
                       "n_range": [min(p["n"] for p in self.problems), max(p["n"] for p in self.problems)],
@@ -268,7 +272,7 @@ def oracle_sample(w, budget_steps, threads):
             steps = chains * w.L * levels
         op = oracle.Problem(p["cost"], p["n"], p["lo"], p["hi"], chains=chains, L=w.L, T0=w.T0, rho=w.rho,
                             sigma_frac=w.sigma_frac, seed=w.seed, problem=p_idx, mode=mode, threads=threads,
-                            Q=p.get("Q"))
+                            Q=p.get("Q"), independent=w.independent)
         op.run(levels)
         done += steps
         descr.append(p_idx)
@@ -296,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     sa.load()
-    w = Workload(args.workload, args.levels)
+    w = Workload(args.workload, args.levels, args.independent)
     h = w.create(sa)
     groups = h.describe()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
@@ -408,7 +412,7 @@ def run_ours(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = Workload(args.workload, args.levels)
+    w = Workload(args.workload, args.levels, args.independent)
     threads = os.cpu_count() or 1
     budget = 6.5e7 / (w.problems[0]["n"] / 4 if any(w.rotated) else 1)
     for _ in range(args.warmup):

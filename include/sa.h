@@ -85,6 +85,10 @@ typedef struct {
     int32_t trace_levels; /* record accept bits of the first trace_levels levels (0 = off) */
     int32_t cost_repeat;  /* rotated costs: evaluate each energy difference this many times
                              (0 or 1 = once; more only to emulate a costlier f, results unchanged) */
+    int32_t independent;  /* 0: synchronous (Sec. 2.2.2: every level restarts all chains from the
+                             best one); 1: asynchronous (Sec. 2.2.1: no exchange, every chain
+                             continues from its own state; the levels' minima still give the
+                             incumbent).  One chain is the sequential algorithm (Sec. 2.1). */
 } sa_schedule;
 
 typedef struct {
@@ -126,7 +130,8 @@ int32_t sa_levels_for(double T0, double rho, double T_min);
  * T0 <= 0, rho not in (0,1), levels < 0, levels == 0 and T_min not in
  * (0, T0), sigma_frac <= 0, unknown cost/boundary/precision, a rotated cost
  * without Q, with a non-finite Q entry, with n^2 > 2^28 or with precision other
- * than SA_FP32, surrogate not 0 or 1 (1: rotated costs only), or chains > 2^31 - 1;
+ * than SA_FP32, surrogate not 0 or 1 (1: rotated costs only), independent not 0
+ * or 1 (or 1 with a surrogate), or chains > 2^31 - 1;
  * SA_ENOMEM / SA_ECUDA on allocation or copy failure.  *out is NULL on error.
  */
 sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains,
@@ -274,7 +279,9 @@ sa_status sa_set_restart(sa_handle* h, int32_t problem, const double* x, double 
 /*
  * Serialise the state between levels (restart point, incumbent, level index,
  * counters) into buf.  With buf == NULL, *len receives the size needed.
- * Errors: SA_EINVAL if *len is too small.  Synchronises.
+ * Errors: SA_EINVAL if *len is too small, or for handles whose chains carry
+ * their own state across levels (independent) or that use the surrogate.
+ * Synchronises.
  */
 sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len);
 

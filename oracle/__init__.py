@@ -50,7 +50,8 @@ class Cfg(ctypes.Structure):
                 ("boundary", ctypes.c_int32), ("mode", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("problem", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("T0", ctypes.c_double),
                 ("rho", ctypes.c_double), ("sigma_frac", ctypes.c_double),
-                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p)]
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("independent", ctypes.c_int32)]
 
 
 class Out(ctypes.Structure):
@@ -152,7 +153,7 @@ class Problem:
     """A box-constrained problem plus the schedule of one synchronous SA run."""
 
     def __init__(self, cost, n, lo, hi, chains, L, T0=100.0, rho=0.9, sigma_frac=0.1,
-                 boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0):
+                 boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0, independent=False):
         self.cost = COSTS[cost] if isinstance(cost, str) else int(cost)
         self.n = int(n)
         self.lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.n,)))
@@ -162,11 +163,12 @@ class Problem:
         self.T0, self.rho, self.sigma_frac = float(T0), float(rho), float(sigma_frac)
         self.boundary = {"reflect": 0, "clip": 1}[boundary] if isinstance(boundary, str) else int(boundary)
         self.seed, self.problem, self.mode, self.threads = int(seed), int(problem), int(mode), int(threads)
+        self.independent = 1 if independent else 0
 
     def cfg(self, K=0, level0=0) -> Cfg:
         return Cfg(self.cost, self.n, self.chains, self.L, K, level0, self.boundary, self.mode,
                    self.threads, self.problem, self.seed, self.T0, self.rho, self.sigma_frac,
-                   _p(self.lo), _p(self.hi), _p(self.Q))
+                   _p(self.lo), _p(self.hi), _p(self.Q), self.independent)
 
     def init_point(self, c: int) -> np.ndarray:
         x = np.zeros(self.n)

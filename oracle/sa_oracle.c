@@ -212,6 +212,10 @@ typedef struct {
     const double* lo;
     const double* hi;
     const double* Q; /* row-major n x n, rotated costs only */
+    int32_t independent; /* 0: synchronous (Sec. 2.2.2: every level restarts all chains from
+                            the best one); 1: asynchronous (Sec. 2.2.1: no exchange, each chain
+                            continues from its own state; the levels' minima still give the
+                            incumbent).  Independent runs start at level 0. */
 } sao_cfg;
 
 typedef struct {
@@ -468,6 +472,7 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
         !cfg->lo || !cfg->hi || !out->x_best || !out->f_best || !out->x_inc || !out->f_inc)
         return -1;
     if (cfg->cost >= SAO_ROT_RASTRIGIN && !cfg->Q) return -1;
+    if (cfg->independent && cfg->level0 != 0) return -1;
     const int n = cfg->n;
     const int64_t C = cfg->chains;
     const int words = (cfg->L + 31) / 32;
@@ -488,7 +493,8 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
         for (int64_t c = 0; c < C; ++c) {
             double* x = X + (size_t)c * n;
             if (level == 0) sao_init_point(cfg, c, x);
-            else memcpy(x, out->x_best, sizeof(double) * (size_t)n);
+            else if (!cfg->independent) memcpy(x, out->x_best, sizeof(double) * (size_t)n);
+            /* independent: x is the chain's own state after the previous level */
             F[c] = sao_chain_level(cfg, level, c, x, bits ? bits + (size_t)c * words : NULL, &A[c]);
         }
         /* Reduction over the chains' final values, lowest index on ties (Sec. 2.2.2). */

@@ -99,6 +99,7 @@ struct SweepArgs {
     int32_t full_level;    // level whose every chain is re-evaluated in FP64 and stored (-1: none)
     int32_t boundary;      // 0 reflect then clip, 1 clip
     int32_t cost_repeat;   // rotated costs: evaluations of each energy difference (1; more only to emulate costlier f)
+    int32_t independent;   // 1: asynchronous chains (no restart from the best; each continues its own state)
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
     uint32_t rk[20];       // sweep key of each Philox round r: (rk[2r], rk[2r+1]) (kernel-parameter operands)

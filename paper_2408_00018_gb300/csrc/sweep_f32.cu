@@ -266,6 +266,9 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
                 }
             }
         }
+    } else if (A.independent) {  // asynchronous: the chain's own state after the previous level
+        if (active)
+            for (int k = 0; k < n; ++k) xs[k * B + t] = A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
     } else {
         for (int k = 0; k < n; ++k) xs[k * B + t] = P.x_best32[k];
     }
@@ -274,7 +277,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     double Fs = 0.0;
     float es = 0.0f;
     SepState st{0.0f, 0.0f, 0.0f};
-    if (level == 0) {
+    if (level == 0 || A.independent) {
         if (active) Fs = (double)start_value32<COST>(xs, B, n, t, inv_n, es, st);
     } else {
         Fs = P.scal[kFBest];
@@ -385,7 +388,11 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     const double M = red[64];
     const bool is_cand = finite && (tracing || level == A.full_level || lo_c <= M);
     if (is_cand) cand[atomicAdd(ncand, 1)] = t;
-    else if (active) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+    else if (active) {
+        A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+        if (A.independent)  // asynchronous: every chain keeps its state for the next level
+            for (int k = 0; k < n; ++k) A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c] = xs[k * B + t];
+    }
     __syncthreads();
     // One warp per candidate: lane-strided partial sums in index order, then a
     // fixed butterfly, so the FP64 value does not depend on the block shape

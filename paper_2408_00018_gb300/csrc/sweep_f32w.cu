@@ -167,6 +167,8 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
                 }
             }
         }
+    } else if (A.independent) {  // asynchronous: the chain's own state after the previous level
+        for (int k = lane; k < n; k += 32) xw[k] = A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
     } else {
         for (int k = lane; k < n; k += 32) xw[k] = P.x_best32[k];
     }
@@ -178,8 +180,8 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
 
     double Fs;
     float es = 0.0f;
-    if (level == 0) {
-        // FP32 value of f at the initial point with a bound on its error
+    if (level == 0 || A.independent) {
+        // FP32 value of f at the start point with a bound on its error
         float sum = 0.0f, sabs = 0.0f, e = 0.0f;
         for (int k = lane; k < n; k += 32) {
             const float x = xw[k];
@@ -343,8 +345,12 @@ __device__ void warp_chain_finish(const SweepArgs& A, const ProbDev& P, int64_t 
         }
         float* dst = A.X32 + P.x_base + c;
         for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xw[k];
-    } else if (lane == 0) {
-        A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+    } else {
+        if (lane == 0) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+        if (A.independent) {  // asynchronous: every chain keeps its state for the next level
+            float* dst = A.X32 + P.x_base + c;
+            for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xw[k];
+        }
     }
     if (lane == 0) atomicAdd(block_acc, nacc);
 }

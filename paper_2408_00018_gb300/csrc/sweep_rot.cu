@@ -57,7 +57,7 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
     // ---- state at the start of the level
     double Fs;
     float edrift = 0.0f;  // bound on the FP64 value drift of the pair updates (the same in every lane)
-    if (level == 0) {
+    if (level == 0 || A.independent) {  // asynchronous levels continue from the chain's own x, y
         const float* xr = P.x0 + (size_t)c * n;
         const float2* yr = P.y0 + (size_t)c * n;
         double part = 0.0;
@@ -153,6 +153,14 @@ __device__ void rot_finish(const SweepArgs& A, const ProbDev& P, int64_t c, int 
         for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = x[k];
     } else if (lane == 0) {
         A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+    }
+    if (A.independent) {  // asynchronous: every chain's x and y pair start its next level
+        float* xr = const_cast<float*>(P.x0) + (size_t)c * n;
+        float2* yr = const_cast<float2*>(P.y0) + (size_t)c * n;
+        for (int k = lane; k < n; k += 32) {
+            xr[k] = x[k];
+            yr[k] = make_float2(yh[k], yl[k]);
+        }
     }
 }
 

@@ -327,3 +327,24 @@ def test_pgd_rotated_reduces_to_unrotated():
     xc, fc, _ = oracle.pgd("rot_rastrigin", x0, lo, hi, Q=P)
     xd, fd, _ = oracle.pgd("rastrigin", x0[perm], lo, hi)
     assert abs(fc - fd) <= 1e-12 and np.allclose(xc[perm], xd, atol=1e-12, rtol=0)
+
+
+def test_independent_chains_follow_their_own_states():
+    """Asynchronous version (Sec. 2.2.1): with the exchange off, chain c after K levels is
+    chain c run alone through levels 0..K-1 from its own states; one chain is the
+    synchronous run; the incumbent is the lowest of the levels' minima."""
+    lo, hi = np.full(3, -500.0), np.full(3, 500.0)
+    K, C, L = 4, 9, 30
+    p = oracle.Problem("schwefel", 3, lo, hi, chains=C, L=L, T0=50.0, rho=0.8, seed=4, mode=0, independent=True)
+    r = p.run(K, want_final=True)
+    mins = []
+    for c in range(C):
+        x = p.init_point(c)
+        for level in range(K):
+            F, x, _, _ = p.chain_level(level, c, x)
+        assert np.array_equal(x, r["X_final"][c]) and F == r["F_final"][c]
+    assert r["f_level"][K - 1] == r["F_final"].min() and r["argmin"][K - 1] == int(np.argmin(r["F_final"]))
+    assert r["f_inc"] == min(r["f_level"])
+    q1 = oracle.Problem("schwefel", 3, lo, hi, chains=1, L=L, T0=50.0, rho=0.8, seed=4, mode=0, independent=True).run(K)
+    q2 = oracle.Problem("schwefel", 3, lo, hi, chains=1, L=L, T0=50.0, rho=0.8, seed=4, mode=0).run(K)
+    assert np.array_equal(q1["f_level"], q2["f_level"]) and q1["f_inc"] == q2["f_inc"]
