@@ -89,6 +89,8 @@ typedef struct {
                              best one); 1: asynchronous (Sec. 2.2.1: no exchange, every chain
                              continues from its own state; the levels' minima still give the
                              incumbent).  One chain is the sequential algorithm (Sec. 2.1). */
+    int32_t exchange_every; /* m > 1: synchronous exchange only after levels m-1, 2m-1, ...; the
+                               chains continue their own states in between (0 or 1: every level) */
 } sa_schedule;
 
 typedef struct {
@@ -131,7 +133,8 @@ int32_t sa_levels_for(double T0, double rho, double T_min);
  * (0, T0), sigma_frac <= 0, unknown cost/boundary/precision, a rotated cost
  * without Q, with a non-finite Q entry, with n^2 > 2^28 or with precision other
  * than SA_FP32, surrogate not 0 or 1 (1: rotated costs only), independent not 0
- * or 1 (or 1 with a surrogate), or chains > 2^31 - 1;
+ * or 1, exchange_every < 0, a surrogate with independent or exchange_every > 1,
+ * or chains > 2^31 - 1;
  * SA_ENOMEM / SA_ECUDA on allocation or copy failure.  *out is NULL on error.
  */
 sa_status sa_create(const sa_problem* problem, const sa_box* box, int32_t n, int64_t chains,
@@ -280,7 +283,8 @@ sa_status sa_set_restart(sa_handle* h, int32_t problem, const double* x, double 
  * Serialise the state between levels (restart point, incumbent, level index,
  * counters) into buf.  With buf == NULL, *len receives the size needed.
  * Errors: SA_EINVAL if *len is too small, or for handles whose chains carry
- * their own state across levels (independent) or that use the surrogate.
+ * their own state across levels (independent, exchange_every > 1) or that use
+ * the surrogate.
  * Synchronises.
  */
 sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len);

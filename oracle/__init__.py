@@ -51,7 +51,7 @@ class Cfg(ctypes.Structure):
                 ("problem", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("T0", ctypes.c_double),
                 ("rho", ctypes.c_double), ("sigma_frac", ctypes.c_double),
                 ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p),
-                ("independent", ctypes.c_int32)]
+                ("independent", ctypes.c_int32), ("exchange_every", ctypes.c_int32)]
 
 
 class Out(ctypes.Structure):
@@ -153,7 +153,8 @@ class Problem:
     """A box-constrained problem plus the schedule of one synchronous SA run."""
 
     def __init__(self, cost, n, lo, hi, chains, L, T0=100.0, rho=0.9, sigma_frac=0.1,
-                 boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0, independent=False):
+                 boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0, independent=False,
+                 exchange_every=1):
         self.cost = COSTS[cost] if isinstance(cost, str) else int(cost)
         self.n = int(n)
         self.lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.n,)))
@@ -164,11 +165,12 @@ class Problem:
         self.boundary = {"reflect": 0, "clip": 1}[boundary] if isinstance(boundary, str) else int(boundary)
         self.seed, self.problem, self.mode, self.threads = int(seed), int(problem), int(mode), int(threads)
         self.independent = 1 if independent else 0
+        self.exchange_every = int(exchange_every)
 
     def cfg(self, K=0, level0=0) -> Cfg:
         return Cfg(self.cost, self.n, self.chains, self.L, K, level0, self.boundary, self.mode,
                    self.threads, self.problem, self.seed, self.T0, self.rho, self.sigma_frac,
-                   _p(self.lo), _p(self.hi), _p(self.Q), self.independent)
+                   _p(self.lo), _p(self.hi), _p(self.Q), self.independent, self.exchange_every)
 
     def init_point(self, c: int) -> np.ndarray:
         x = np.zeros(self.n)

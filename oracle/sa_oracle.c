@@ -216,6 +216,8 @@ typedef struct {
                             the best one); 1: asynchronous (Sec. 2.2.1: no exchange, each chain
                             continues from its own state; the levels' minima still give the
                             incumbent).  Independent runs start at level 0. */
+    int32_t exchange_every; /* > 1: the exchange (restart from the best) only after levels
+                               m-1, 2m-1, ...; chains continue their own states in between */
 } sao_cfg;
 
 typedef struct {
@@ -472,7 +474,8 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
         !cfg->lo || !cfg->hi || !out->x_best || !out->f_best || !out->x_inc || !out->f_inc)
         return -1;
     if (cfg->cost >= SAO_ROT_RASTRIGIN && !cfg->Q) return -1;
-    if (cfg->independent && cfg->level0 != 0) return -1;
+    const int periodic = cfg->exchange_every > 1;
+    if ((cfg->independent || periodic) && cfg->level0 != 0) return -1;
     const int n = cfg->n;
     const int64_t C = cfg->chains;
     const int words = (cfg->L + 31) / 32;
@@ -492,9 +495,10 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
 #endif
         for (int64_t c = 0; c < C; ++c) {
             double* x = X + (size_t)c * n;
+            const int own = cfg->independent || (periodic && level % cfg->exchange_every != 0);
             if (level == 0) sao_init_point(cfg, c, x);
-            else if (!cfg->independent) memcpy(x, out->x_best, sizeof(double) * (size_t)n);
-            /* independent: x is the chain's own state after the previous level */
+            else if (!own) memcpy(x, out->x_best, sizeof(double) * (size_t)n);
+            /* own start: x is the chain's own state after the previous level */
             F[c] = sao_chain_level(cfg, level, c, x, bits ? bits + (size_t)c * words : NULL, &A[c]);
         }
         /* Reduction over the chains' final values, lowest index on ties (Sec. 2.2.2). */

@@ -166,6 +166,7 @@ sa_status check_schedule(const sa_schedule* s) {
     if ((s->surrogate != 0 && s->surrogate != 1) || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
     if (s->cost_repeat < 0 || s->cost_repeat > 4096) return SA_EINVAL;
     if ((s->independent != 0 && s->independent != 1) || (s->independent && s->surrogate)) return SA_EINVAL;
+    if (s->exchange_every < 0 || (s->exchange_every > 1 && s->surrogate)) return SA_EINVAL;
     if (s->trace_levels < 0) return SA_EINVAL;
     return SA_OK;
 }
@@ -709,6 +710,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
 
     a.cost_repeat = h->sch.cost_repeat > 1 ? h->sch.cost_repeat : 1;
     a.independent = h->sch.independent;
+    a.exchange_every = h->sch.exchange_every > 1 ? h->sch.exchange_every : 1;
     if (h->sch.surrogate && (st = setup_da(h))) return st;
 
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return SA_ECUDA;
@@ -1105,7 +1107,7 @@ sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_
 sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len) {
     if (!h || !len) return SA_EINVAL;
     if (h->failed != SA_OK) return SA_ESTATE;
-    if (h->da || h->sch.independent) return SA_EINVAL;  // the surrogate's and the chains' states are not part of a checkpoint
+    if (h->da || keep_states(h->args)) return SA_EINVAL;  // the surrogate's and the chains' states are not part of a checkpoint
     size_t need = 4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(int32_t) * 2;
     for (const HostProb& hp : h->probs)
         need += sizeof(double) * (kNumScalars + 2 * (size_t)hp.n) + sizeof(uint64_t) +
@@ -1159,7 +1161,7 @@ sa_status sa_checkpoint(sa_handle* h, void* buf, size_t* len) {
 sa_status sa_restore(sa_handle* h, const void* buf, size_t len) {
     if (!h || !buf) return SA_EINVAL;
     if (h->failed != SA_OK) return SA_ESTATE;
-    if (h->da || h->sch.independent) return SA_EINVAL;
+    if (h->da || keep_states(h->args)) return SA_EINVAL;
     const unsigned char* p = static_cast<const unsigned char*>(buf);
     const unsigned char* end = p + len;
     auto get = [&p, end](void* dst, size_t n) {

@@ -100,10 +100,20 @@ struct SweepArgs {
     int32_t boundary;      // 0 reflect then clip, 1 clip
     int32_t cost_repeat;   // rotated costs: evaluations of each energy difference (1; more only to emulate costlier f)
     int32_t independent;   // 1: asynchronous chains (no restart from the best; each continues its own state)
+    int32_t exchange_every;  // > 1: restart from the best only after every exchange_every-th level
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
     uint32_t rk[20];       // sweep key of each Philox round r: (rk[2r], rk[2r+1]) (kernel-parameter operands)
 };
+
+// Does level `level` start each chain from its own state (rather than from the
+// best state of the previous level)?  Asynchronous chains never exchange; with a
+// period m > 1 the exchange follows levels m-1, 2m-1, ... (Sec. 2.2.1-2.2.2).
+__host__ __device__ inline bool own_start(const SweepArgs& a, int level) {
+    return level > 0 && (a.independent || (a.exchange_every > 1 && level % a.exchange_every != 0));
+}
+// Must every chain keep its state at the end of a level (for the next level's own start)?
+__host__ __device__ inline bool keep_states(const SweepArgs& a) { return a.independent || a.exchange_every > 1; }
 
 // Launch wrappers (one per translation unit).
 cudaError_t launch_sweep_f32(const SweepArgs& a, int num_items, int block, size_t smem, cudaStream_t s);

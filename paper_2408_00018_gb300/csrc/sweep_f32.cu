@@ -266,7 +266,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
                 }
             }
         }
-    } else if (A.independent) {  // asynchronous: the chain's own state after the previous level
+    } else if (own_start(A, level)) {  // the chain's own state (no exchange before this level)
         if (active)
             for (int k = 0; k < n; ++k) xs[k * B + t] = A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
     } else {
@@ -277,7 +277,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     double Fs = 0.0;
     float es = 0.0f;
     SepState st{0.0f, 0.0f, 0.0f};
-    if (level == 0 || A.independent) {
+    if (level == 0 || own_start(A, level)) {
         if (active) Fs = (double)start_value32<COST>(xs, B, n, t, inv_n, es, st);
     } else {
         Fs = P.scal[kFBest];
@@ -390,7 +390,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     if (is_cand) cand[atomicAdd(ncand, 1)] = t;
     else if (active) {
         A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
-        if (A.independent)  // asynchronous: every chain keeps its state for the next level
+        if (keep_states(A))  // every chain keeps its state for the next level
             for (int k = 0; k < n; ++k) A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c] = xs[k * B + t];
     }
     __syncthreads();

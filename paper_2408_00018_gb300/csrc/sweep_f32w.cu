@@ -167,7 +167,7 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
                 }
             }
         }
-    } else if (A.independent) {  // asynchronous: the chain's own state after the previous level
+    } else if (own_start(A, level)) {  // the chain's own state (no exchange before this level)
         for (int k = lane; k < n; k += 32) xw[k] = A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
     } else {
         for (int k = lane; k < n; k += 32) xw[k] = P.x_best32[k];
@@ -180,7 +180,7 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
 
     double Fs;
     float es = 0.0f;
-    if (level == 0 || A.independent) {
+    if (level == 0 || own_start(A, level)) {
         // FP32 value of f at the start point with a bound on its error
         float sum = 0.0f, sabs = 0.0f, e = 0.0f;
         for (int k = lane; k < n; k += 32) {
@@ -347,7 +347,7 @@ __device__ void warp_chain_finish(const SweepArgs& A, const ProbDev& P, int64_t 
         for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xw[k];
     } else {
         if (lane == 0) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
-        if (A.independent) {  // asynchronous: every chain keeps its state for the next level
+        if (keep_states(A)) {  // every chain keeps its state for the next level
             float* dst = A.X32 + P.x_base + c;
             for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xw[k];
         }

@@ -65,7 +65,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
                     if (k + j < n) xcol[(k + j) * B] = P.lo[k + j] + u23d(ww[j]) * (P.hi[k + j] - P.lo[k + j]);
             }
         }
-    } else if (A.independent) {  // asynchronous: the chain's own state after the previous level
+    } else if (own_start(A, level)) {  // the chain's own state (no exchange before this level)
         if (active)
             for (int k = 0; k < n; ++k) xcol[k * B] = A.X64[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
     } else {

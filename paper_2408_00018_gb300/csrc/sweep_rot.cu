@@ -57,7 +57,7 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
     // ---- state at the start of the level
     double Fs;
     float edrift = 0.0f;  // bound on the FP64 value drift of the pair updates (the same in every lane)
-    if (level == 0 || A.independent) {  // asynchronous levels continue from the chain's own x, y
+    if (level == 0 || own_start(A, level)) {  // own-start levels continue from the chain's own x, y
         const float* xr = P.x0 + (size_t)c * n;
         const float2* yr = P.y0 + (size_t)c * n;
         double part = 0.0;
@@ -154,7 +154,7 @@ __device__ void rot_finish(const SweepArgs& A, const ProbDev& P, int64_t c, int 
     } else if (lane == 0) {
         A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
     }
-    if (A.independent) {  // asynchronous: every chain's x and y pair start its next level
+    if (keep_states(A)) {  // every chain's x and y pair may start its next level
         float* xr = const_cast<float*>(P.x0) + (size_t)c * n;
         float2* yr = const_cast<float2*>(P.y0) + (size_t)c * n;
         for (int k = lane; k < n; k += 32) {

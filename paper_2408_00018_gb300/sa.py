@@ -40,7 +40,8 @@ class _Schedule(ctypes.Structure):
     _fields_ = [("T0", ctypes.c_double), ("rho", ctypes.c_double), ("T_min", ctypes.c_double),
                 ("levels", ctypes.c_int32), ("sigma_frac", ctypes.c_double), ("boundary", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("surrogate", ctypes.c_int32), ("polish_k", ctypes.c_int32),
-                ("trace_levels", ctypes.c_int32), ("cost_repeat", ctypes.c_int32), ("independent", ctypes.c_int32)]
+                ("trace_levels", ctypes.c_int32), ("cost_repeat", ctypes.c_int32), ("independent", ctypes.c_int32),
+                ("exchange_every", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -147,11 +148,12 @@ class Schedule:
     surrogate: int = 0
     cost_repeat: int = 1
     independent: int = 0
+    exchange_every: int = 1
 
     def _c(self) -> _Schedule:
         return _Schedule(self.T0, self.rho, self.T_min, self.levels, self.sigma_frac, BOUNDARY[self.boundary],
                          PRECISION[self.precision], self.surrogate, self.polish_k, self.trace_levels,
-                         self.cost_repeat, self.independent)
+                         self.cost_repeat, self.independent, self.exchange_every)
 
 
 def levels_for(T0: float, rho: float, T_min: float) -> int:

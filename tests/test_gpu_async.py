@@ -77,3 +77,18 @@ def test_fp32_asynchronous_level1_from_each_chains_own_state(sa, cost, n, warp, 
     assert int(h.level_log()["argmin"][1]) == int(np.argmin(F1))
     with pytest.raises(sa.SAError):
         h.checkpoint()
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_fp64_periodic_exchange_is_the_oracles(sa, m):
+    n, C, L, K = 2, 257, 50, 6
+    lo, hi = inputs.box("schwefel", n)
+    sch = sa.Schedule(T0=80.0, rho=0.85, levels=K, precision="fp64", exchange_every=m)
+    h = sa.create("schwefel", lo, hi, n, C, L, sch, seed=5)
+    h.run()
+    log = h.level_log()
+    ref = oracle.Problem("schwefel", n, lo, hi, chains=C, L=L, T0=80.0, rho=0.85, seed=5, mode=0,
+                         exchange_every=m).run(K)
+    assert np.array_equal(log["argmin"], ref["argmin"])
+    assert np.allclose(log["f_level"], ref["f_level"], rtol=1e-12, atol=0)
+    assert abs(h.best()[1] - ref["f_inc"]) <= 1e-12 * abs(ref["f_inc"])

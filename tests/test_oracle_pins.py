@@ -348,3 +348,20 @@ def test_independent_chains_follow_their_own_states():
     q1 = oracle.Problem("schwefel", 3, lo, hi, chains=1, L=L, T0=50.0, rho=0.8, seed=4, mode=0, independent=True).run(K)
     q2 = oracle.Problem("schwefel", 3, lo, hi, chains=1, L=L, T0=50.0, rho=0.8, seed=4, mode=0).run(K)
     assert np.array_equal(q1["f_level"], q2["f_level"]) and q1["f_inc"] == q2["f_inc"]
+
+
+def test_periodic_exchange_between_the_two_extremes():
+    """Exchange every m levels: m = 1 is the synchronous run, m >= K the asynchronous
+    one; with m = 2 the levels after an exchange equal a synchronous level from the
+    best state, the others continue each chain's own state."""
+    lo, hi = np.full(3, -500.0), np.full(3, 500.0)
+    K, C, L = 5, 11, 25
+    mk = lambda **kw: oracle.Problem("schwefel", 3, lo, hi, chains=C, L=L, T0=60.0, rho=0.8, seed=2, mode=0, **kw)
+    sync, asyn = mk().run(K), mk(independent=True).run(K)
+    assert np.array_equal(mk(exchange_every=1).run(K)["f_level"], sync["f_level"])
+    assert np.array_equal(mk(exchange_every=K).run(K)["f_level"], asyn["f_level"])
+    per = mk(exchange_every=2).run(K)
+    assert np.array_equal(per["f_level"][:2], asyn["f_level"][:2])  # levels 0, 1: no exchange yet
+    # level 2 restarts every chain from level 1's best: a synchronous level from that state
+    r = mk().run(1, level0=2, x_best=mk(exchange_every=2).run(2)["x_best"])
+    assert r["f_level"][0] == per["f_level"][2]
