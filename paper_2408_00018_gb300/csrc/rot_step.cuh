@@ -110,6 +110,7 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
     float sum = 0.0f, bnd = 0.0f;
     if (COST == kRotRastrigin) {
         const bool any_big = fabsf(dh) * P.qmax * 3.14159265f >= 0.5f;  // some |pi Delta_i| may reach 1/2
+        #pragma unroll 4
         for (int i = lane; i < n; i += 32) {
             const float yv = yh[i];
             const float Dl = dh * qcol[i];
@@ -137,6 +138,7 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
         // |sqrt u - sqrt v| <= sqrt|u - v|
         const float capA = 1.01f * sqrt_approx(fmaf(1.2e-7f, P.ymax, 2.4e-7f * fabsf(dh) * P.qmax)) + 1e-15f;
         const float capB = 1.01f * sqrt_approx(6.0e-8f * P.ymax) + 1e-15f;
+        #pragma unroll 4
         for (int i = lane; i < n; i += 32) {
             const float yv = yh[i];
             const float Dl = dh * qcol[i];
@@ -184,7 +186,8 @@ __device__ __forceinline__ double rot_eval64(const ProbDev& P, const float* yh, 
     const double d64 = (double)xp - (double)xo;
     const double* q64 = P.qt64 + (size_t)d * n;
     double s64 = 0.0, a64 = 0.0;
-    for (int i = lane; i < n; i += 32) {
+        #pragma unroll 4
+        for (int i = lane; i < n; i += 32) {
         const double y64 = (double)yh[i] + (double)yl[i];
         const double gn = rot_g64<COST>(y64 + d64 * q64[i]), go = rot_g64<COST>(y64);
         s64 += gn - go;
@@ -210,7 +213,8 @@ __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* y
     const float gmax = COST == kRotRastrigin ? fmaf(2.0f, ym + dm, 64.0f)
                                              : fmaf(0.5f, sqrt_approx(ym + dm), 1.0f) / (float)n;
     edrift = fmaf((float)n * gmax, (ym + 2.0f * dm) * 2.9e-14f, edrift);
-    for (int i = lane; i < n; i += 32) {
+        #pragma unroll 4
+        for (int i = lane; i < n; i += 32) {
         const float qh = qcol[i], ql = qlcol[i];
         const float ph = dh * qh;
         const float pl = fmaf(dh, qh, -ph);
