@@ -11,7 +11,9 @@ Pins: the tests under ``tests/test_oracle_*.py`` check this oracle against
 published Philox4x32-10 known-answer vectors, the closed-form normalised
 Schwefel minimum, brute-force grids, schedule/evaluation-count identities
 printed with Table 1, and Metropolis invariants (acceptance 1 on a constant
-cost, zero uphill moves as T -> 0, Boltzmann histogram at fixed T).
+cost, zero uphill moves as T -> 0, Boltzmann histogram at fixed T); the
+Nelder-Mead of the hybrid SA is pinned iteration for iteration against scipy's
+implementation of the same method.
 """
 from __future__ import annotations
 
@@ -96,6 +98,8 @@ def lib():
             L.sao_level_chains.restype = ctypes.c_int
             L.sao_pgd.argtypes = [i32, i32, vp, vp, vp, vp, i32, f64, f64, i32, vp, vp]
             L.sao_pgd.restype = ctypes.c_int
+            L.sao_nelder_mead.argtypes = [i32, i32, vp, vp, vp, vp, f64, i32, f64, f64, vp, vp]
+            L.sao_nelder_mead.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -294,4 +298,20 @@ def pgd(name_or_id, x0, lo, hi, Q=None, max_iter=1000, tol=1e-10, armijo_c=1e-4,
     rc = lib().sao_pgd(cid, n, _p(lo), _p(hi), _p(Qa), _p(x), max_iter, tol, armijo_c, max_halvings, _p(f), _p(it))
     if rc != 0:
         raise ValueError("sao_pgd failed")
+    return x, float(f[0]), int(it[0])
+
+
+def nelder_mead(name_or_id, x0, lo, hi, Q=None, step_frac=0.05, max_iter=20000, ftol=1e-12, xtol=1e-10):
+    """Nelder-Mead with box clipping from x0; returns (x, f, iterations)."""
+    cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
+    x = np.array(x0, np.float64)
+    n = x.size
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (n,)))
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    f = np.zeros(1)
+    it = np.zeros(1, np.int32)
+    rc = lib().sao_nelder_mead(cid, n, _p(lo), _p(hi), _p(Qa), _p(x), step_frac, max_iter, ftol, xtol, _p(f), _p(it))
+    if rc != 0:
+        raise ValueError("sao_nelder_mead failed")
     return x, float(f[0]), int(it[0])

@@ -26,6 +26,9 @@
  *   - acceptance: dF <= 0 or u3 < exp(-dF / T).
  *   - tie-break of the reduction: lowest chain index.
  *   - the answer returned is the incumbent: the best level minimum seen.
+ *   - local minimisers of the hybrid SA (Sec. 4.2, Table 10): the paper's
+ *     Nelder-Mead in the standard form (coefficients 1, 2, 1/2, 1/2; trial
+ *     points clipped into the box), and box-projected gradient descent.
  *
  * Compiled with -ffp-contract=off so that every product and sum is rounded
  * exactly as written, on every host architecture.
@@ -605,5 +608,122 @@ int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const d
     free(yw);
     if (f_out) *f_out = f;
     if (iters_out) *iters_out = it;
+    return 0;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Nelder-Mead (the paper's local minimiser of the hybrid SA, Sec. 4.2 and    */
+/* Table 10), in the standard form of Lagarias, Reeds, Wright & Wright (SIAM  */
+/* J. Optim. 1998): reflection 1, expansion 2, contraction 1/2, shrink 1/2.  */
+/* Box constraints: every trial point is clipped into the box.  Vertices are */
+/* ordered by (f, slot); the initial simplex is x0 and x0 + delta_k e_k,     */
+/* delta_k = step_frac (u_k - l_k) (or minus, if that leaves the box).       */
+/* Stops when both f_worst - f_best <= ftol max(1, |f_best|) and every       */
+/* vertex is within xtol (u_i - l_i) of the best in every coordinate i, or   */
+/* after max_iter iterations.  x: in start point, out best vertex.           */
+/* ------------------------------------------------------------------------ */
+static void nm_clip(int n, const double* lo, const double* hi, double* x) {
+    for (int i = 0; i < n; ++i) x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
+}
+
+int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, double* x,
+                    double step_frac, int32_t max_iter, double ftol, double xtol, double* f_out,
+                    int32_t* iters_out) {
+    const int m = n + 1;
+    double* V = (double*)malloc(sizeof(double) * (size_t)m * n);
+    double* F = (double*)malloc(sizeof(double) * (size_t)m);
+    double* xc = (double*)malloc(sizeof(double) * (size_t)n);
+    double* xr = (double*)malloc(sizeof(double) * (size_t)n);
+    double* xt = (double*)malloc(sizeof(double) * (size_t)n);
+    double* yw = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!V || !F || !xc || !xr || !xt || !yw) {
+        free(V); free(F); free(xc); free(xr); free(xt); free(yw);
+        return -2;
+    }
+    nm_clip(n, lo, hi, x);
+    for (int j = 0; j < m; ++j) {
+        double* v = V + (size_t)j * n;
+        memcpy(v, x, sizeof(double) * (size_t)n);
+        if (j > 0) {
+            const int k = j - 1;
+            const double d = step_frac * (hi[k] - lo[k]);
+            v[k] = (v[k] + d <= hi[k]) ? v[k] + d : v[k] - d;
+            nm_clip(n, lo, hi, v);
+        }
+        F[j] = sao_cost_ws(cost, n, v, Q, yw);
+    }
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        /* best l, worst h, second worst s in the order (f, slot) */
+        int l = 0, h = 0;
+        for (int j = 1; j < m; ++j) {
+            if (F[j] < F[l]) l = j;
+            if (F[j] >= F[h]) h = j;
+        }
+        int sw = (h == 0) ? 1 : 0;
+        for (int j = 0; j < m; ++j)
+            if (j != h && F[j] >= F[sw]) sw = j;
+        if (F[h] - F[l] <= ftol * fmax(1.0, fabs(F[l]))) {
+            int small = 1;
+            for (int j = 0; j < m && small; ++j)
+                for (int i = 0; i < n; ++i)
+                    if (fabs(V[(size_t)j * n + i] - V[(size_t)l * n + i]) > xtol * (hi[i] - lo[i])) { small = 0; break; }
+            if (small) break;
+        }
+        /* centroid of every vertex but the worst, summed in slot order */
+        for (int i = 0; i < n; ++i) {
+            double a = 0.0;
+            for (int j = 0; j < m; ++j)
+                if (j != h) a += V[(size_t)j * n + i];
+            xc[i] = a / (double)n;
+        }
+        const double* vh = V + (size_t)h * n;
+        for (int i = 0; i < n; ++i) xr[i] = xc[i] + (xc[i] - vh[i]);
+        nm_clip(n, lo, hi, xr);
+        const double fr = sao_cost_ws(cost, n, xr, Q, yw);
+        int accept = 0;
+        double fa = fr;
+        const double* xa = xr;
+        if (fr < F[l]) {
+            for (int i = 0; i < n; ++i) xt[i] = xc[i] + 2.0 * (xr[i] - xc[i]);
+            nm_clip(n, lo, hi, xt);
+            const double fe = sao_cost_ws(cost, n, xt, Q, yw);
+            accept = 1;
+            if (fe < fr) { fa = fe; xa = xt; }
+        } else if (fr < F[sw]) {
+            accept = 1;
+        } else if (fr < F[h]) {
+            for (int i = 0; i < n; ++i) xt[i] = xc[i] + 0.5 * (xr[i] - xc[i]);
+            nm_clip(n, lo, hi, xt);
+            const double fo = sao_cost_ws(cost, n, xt, Q, yw);
+            if (fo <= fr) { accept = 1; fa = fo; xa = xt; }
+        } else {
+            for (int i = 0; i < n; ++i) xt[i] = xc[i] - 0.5 * (xc[i] - vh[i]);
+            nm_clip(n, lo, hi, xt);
+            const double fi = sao_cost_ws(cost, n, xt, Q, yw);
+            if (fi < F[h]) { accept = 1; fa = fi; xa = xt; }
+        }
+        if (accept) {
+            memcpy(V + (size_t)h * n, xa, sizeof(double) * (size_t)n);
+            F[h] = fa;
+        } else { /* shrink towards the best vertex */
+            const double* vl = V + (size_t)l * n;
+            for (int j = 0; j < m; ++j) {
+                if (j == l) continue;
+                double* v = V + (size_t)j * n;
+                for (int i = 0; i < n; ++i) v[i] = vl[i] + 0.5 * (v[i] - vl[i]);
+                nm_clip(n, lo, hi, v);
+                F[j] = sao_cost_ws(cost, n, v, Q, yw);
+            }
+        }
+    }
+    int l = 0;
+    for (int j = 1; j < m; ++j)
+        if (F[j] < F[l]) l = j;
+    memcpy(x, V + (size_t)l * n, sizeof(double) * (size_t)n);
+    if (f_out) *f_out = F[l];
+    if (iters_out) *iters_out = it;
+    free(V); free(F); free(xc); free(xr); free(xt); free(yw);
     return 0;
 }
