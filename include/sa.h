@@ -57,6 +57,7 @@ typedef enum {
 
 enum { SA_REFLECT = 0, SA_CLIP = 1 };                 /* box handling of a move */
 enum { SA_FP64 = 0, SA_FP32 = 1, SA_MIXED_BF16 = 2 }; /* arithmetic of the sweep */
+enum { SA_POLISH_PGD = 0, SA_POLISH_NELDER_MEAD = 1 };  /* local minimiser of the hybrid SA */
 
 typedef struct {
     int32_t cost;    /* sa_cost */
@@ -80,8 +81,8 @@ typedef struct {
     int32_t surrogate;  /* 0: Metropolis; 1: delayed acceptance with the learned surrogate
                            (rotated costs, SA_FP32, sa_create only; see sa_da_trace) */
     int32_t polish_k;   /* hybrid SA: after the last level, polish the polish_k best final
-                           states (0..1024) with sa_polish's method; the best polished point
-                           becomes the incumbent if it is lower (0 = off) */
+                           states (0..1024) with the method polish_method names; the best
+                           polished point becomes the incumbent if it is lower (0 = off) */
     int32_t trace_levels; /* record accept bits of the first trace_levels levels (0 = off) */
     int32_t cost_repeat;  /* rotated costs: evaluate each energy difference this many times
                              (0 or 1 = once; more only to emulate a costlier f, results unchanged) */
@@ -91,6 +92,10 @@ typedef struct {
                              incumbent).  One chain is the sequential algorithm (Sec. 2.1). */
     int32_t exchange_every; /* m > 1: synchronous exchange only after levels m-1, 2m-1, ...; the
                                chains continue their own states in between (0 or 1: every level) */
+    int32_t polish_method;  /* SA_POLISH_PGD: sa_polish (max_iter 1000, tol 1e-10);
+                               SA_POLISH_NELDER_MEAD: sa_nelder_mead with step_frac = sigma_frac
+                               sqrt(T_last / T0) (the last level's step scale), max_iter
+                               200 (n + 1), ftol 1e-12, xtol 1e-10 (n <= 4096) */
 } sa_schedule;
 
 typedef struct {
@@ -319,6 +324,34 @@ const char* sa_strerror(sa_status s);
 sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
                     const double* x0, int32_t max_iter, double tol, double* x_out, double* f_out,
                     int32_t* iters_out, void* stream);
+
+/*
+ * Nelder-Mead, the local minimiser of the paper's hybrid SA (Sec. 4.2, Table
+ * 10), in the standard form (Lagarias, Reeds, Wright & Wright, SIAM J. Optim.
+ * 1998): reflection 1, expansion 2, outside and inside contraction 1/2,
+ * shrink 1/2 towards the best vertex; every trial point is clipped into the
+ * box.  From each of k start points x0[j*n .. j*n+n) (host) the simplex is
+ * x0 and x0 + delta_i e_i, delta_i = step_frac (u_i - l_i) (minus that if plus
+ * leaves the box); vertices rank by (f, slot) -- best = lowest f, then lowest
+ * slot; worst and second worst = highest f, then highest slot.  Stops when
+ * f_worst - f_best <= ftol max(1, |f_best|) and every vertex is within
+ * xtol (u_i - l_i) of the best in every coordinate i, or after max_iter
+ * iterations.  FP64.  Writes the best vertices to x_out (host [k*n]), their
+ * values to f_out (host [k]) and the iteration counts to iters_out (host [k],
+ * may be NULL).  Rotated costs take Q (host, n x n row-major); separable costs
+ * need Q == NULL.  Device workspace ((n+1) n doubles per start: the simplex)
+ * is allocated stream-ordered; synchronises `stream`.  Above 64 coordinates
+ * the centroid comes from a running vertex sum (summed afresh after a shrink
+ * and every n+1 iterations), so results differ from a sequential
+ * implementation by rounding there as well as in f.
+ * Errors: SA_EINVAL on n < 1 or n > 4096, k not in [1, 1024], a bad box,
+ * step_frac not in (0, 1], max_iter < 0, ftol or xtol negative or NaN, a NULL
+ * array, Q missing for a rotated cost (or given for a separable one), a
+ * non-finite Q entry, or a workspace above 4 GiB; SA_ENOMEM; SA_ECUDA.
+ */
+sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
+                         const double* x0, double step_frac, int32_t max_iter, double ftol, double xtol,
+                         double* x_out, double* f_out, int32_t* iters_out, void* stream);
 
 /*
  * Kernel-level entry point: tensor-core GEMM D = A . B^T with A [M x K] and

@@ -1,5 +1,6 @@
-// polish.cu -- local minimiser of the hybrid SA: box-projected gradient
-// descent with Armijo backtracking, in FP64, one warp per start point.
+// polish.cu -- local minimisers of the hybrid SA, in FP64, one warp per start
+// point: box-projected gradient descent with Armijo backtracking, and the
+// paper's Nelder-Mead (nm_kernel below).
 //
 // The paper stops SA early and hands its point to Nelder-Mead (Sec. 4.2 and
 // Table 10); here the k best final states of the last level are polished by
@@ -10,6 +11,7 @@
 // below tol, when no step of the 30 halvings decreases f, or after max_iter
 // iterations.  Sums over coordinates use a fixed lane-strided order and a
 // butterfly, so results differ from a sequential sum only by rounding.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <math_constants.h>
@@ -181,6 +183,231 @@ __global__ void pgd_kernel(int cost, int n, const double* __restrict__ lo, const
     }
 }
 
+// Nelder-Mead (the paper's local minimiser, Sec. 4.2 / Table 10) in the standard
+// form of Lagarias, Reeds, Wright & Wright (1998): reflection 1, expansion 2,
+// contraction 1/2, shrink 1/2, every trial point clipped into the box.  The
+// simplex starts at x0 and x0 +- step_frac (u_k - l_k) e_k (minus if plus leaves
+// the box); vertices are ranked by (f, slot): best = lowest f then lowest slot,
+// worst and second worst = highest f then highest slot.  Stops when the f spread
+// is <= ftol max(1, |f_best|) and every vertex lies within xtol (u_i - l_i) of the
+// best, or after max_iter iterations.
+//
+// One block per start, threads over coordinates.  The simplex [(n+1) x n] lives
+// in global memory (a vertex per row, so a block reads and writes it coalesced);
+// f of the vertices, the vertex sum S, the centroid, the reflected and the trial
+// point live in shared memory.  Up to kNmExactN coordinates the centroid of all
+// vertices but the worst is summed in slot order every iteration, as written;
+// above, it is (S - v_h) / n, with S updated by each replacement and summed
+// afresh in slot order after a shrink and every n+1 iterations, so an iteration
+// costs O(n) plus its one or two evaluations of f instead of O(n^2).  Rotated
+// costs evaluate y_i = sum_j Q_ij x_j per thread from Q^T (coalesced columns).
+constexpr int kNmMaxN = 4096;
+constexpr int kNmExactN = 64;
+
+__device__ __forceinline__ double clipd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
+
+// (f, slot) order: true when (fa, a) ranks below (fb, b)
+__device__ __forceinline__ bool rank_less(double fa, int a, double fb, int b) { return fa < fb || (fa == fb && a < b); }
+
+// Sum over the block (every thread gets it): butterflies per warp, then the warps' sums
+// in warp order.  red: 32 doubles of shared scratch.
+__device__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();  // red is reused by the next call
+    return s;
+}
+
+// f at x (shared memory, visible to the block); every thread gets the value.
+__device__ double bcost(int cost, int n, const double* x, const double* __restrict__ QT, double* red) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (cost == kRotRastrigin || cost == kRotSchwefel) {
+            double y = 0.0;
+            for (int j = 0; j < n; ++j) y = fma(QT[(size_t)j * n + i], x[j], y);
+            s1 += rot_term(cost, y);
+        } else {
+            const double t = x[i];
+            if (cost == kSchwefel) s1 += h64_schwefel(t);
+            else if (cost == kRastrigin) s1 += g64_rastrigin(t);
+            else if (cost == kAckley) { s1 += t * t; s2 += cos(6.283185307179586 * t); }
+            else if (i + 1 < n) s1 += rosen64(t, x[i + 1]);
+        }
+    }
+    s1 = block_sum(s1, red);
+    if (cost == kAckley) s2 = block_sum(s2, red);
+    if (cost == kSchwefel) return -(s1 / (double)n);
+    if (cost == kRastrigin) return 10.0 * (double)n + s1;
+    if (cost == kAckley) return ackley64(n, s1, s2);
+    if (cost == kRotRastrigin) return 10.0 * (double)n + s1;
+    if (cost == kRotSchwefel) return -(s1 / (double)n);
+    return s1;
+}
+
+// Lowest (f, slot) of F[0..m) (best = true) or highest (best = false) among the slots
+// other than `skip`; (f, slot) is a strict order, so the result does not depend on
+// the reduction's order.  fr/jr: 32 doubles / ints of shared scratch.
+__device__ int nm_pick(const double* F, int m, bool best, int skip, double* fr, int* jr, double* f_out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double fb = best ? CUDART_INF : -CUDART_INF;
+    int jb = best ? m : -1;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        if (j == skip) continue;
+        const double f = F[j];
+        if (best ? rank_less(f, j, fb, jb) : rank_less(fb, jb, f, j)) { fb = f; jb = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double f = __shfl_xor_sync(kFull, fb, o);
+        const int j = __shfl_xor_sync(kFull, jb, o);
+        if (best ? rank_less(f, j, fb, jb) : rank_less(fb, jb, f, j)) { fb = f; jb = j; }
+    }
+    if (lane == 0) { fr[wid] = fb; jr[wid] = jb; }
+    __syncthreads();
+    for (int w = 0; w < nw; ++w)
+        if (best ? rank_less(fr[w], jr[w], fb, jb) : rank_less(fb, jb, fr[w], jr[w])) { fb = fr[w]; jb = jr[w]; }
+    __syncthreads();
+    *f_out = fb;
+    return jb;
+}
+
+__global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double* __restrict__ lo,
+                                                  const double* __restrict__ hi, const double* __restrict__ QT,
+                                                  const double* __restrict__ x0, double* __restrict__ x_out,
+                                                  double* __restrict__ f_out, int* __restrict__ it_out,
+                                                  double step_frac, int max_iter, double ftol, double xtol,
+                                                  double* __restrict__ ws) {
+    extern __shared__ __align__(16) double nsm[];
+    const int t = threadIdx.x, B = blockDim.x, w = blockIdx.x, m = n + 1;
+    double* F = nsm;
+    double* S = F + m;
+    double* xc = S + n;
+    double* xr = xc + n;
+    double* xt = xr + n;
+    double* red = xt + n;                      // 32 doubles
+    int* jred = reinterpret_cast<int*>(red + 32);  // 32 ints
+    double* V = ws + (size_t)w * (size_t)m * (size_t)n;
+
+    for (int i = t; i < n; i += B) {
+        const double v0 = clipd(x0[(size_t)w * n + i], lo[i], hi[i]);
+        for (int j = 0; j < m; ++j) {
+            double v = v0;
+            if (i == j - 1) {
+                const double d = step_frac * (hi[i] - lo[i]);
+                v = clipd(v + d <= hi[i] ? v + d : v - d, lo[i], hi[i]);
+            }
+            V[(size_t)j * n + i] = v;
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        for (int i = t; i < n; i += B) xt[i] = V[(size_t)j * n + i];
+        __syncthreads();
+        const double f = bcost(cost, n, xt, QT, red);
+        if (t == 0) F[j] = f;
+    }
+    auto resum = [&]() {
+        for (int i = t; i < n; i += B) {
+            double a = 0.0;
+            for (int j = 0; j < m; ++j) a += V[(size_t)j * n + i];
+            S[i] = a;
+        }
+    };
+    resum();
+    __syncthreads();
+
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        double fl, fh, fs;
+        const int l = nm_pick(F, m, true, -1, red, jred, &fl);
+        const int h = nm_pick(F, m, false, -1, red, jred, &fh);
+        const int sw = nm_pick(F, m, false, h, red, jred, &fs);
+        if (l >= m || h < 0 || sw < 0) break;  // only if f is NaN at every vertex (never on a finite box)
+        if (fh - fl <= ftol * fmax(1.0, fabs(fl))) {
+            int small = 1;
+            for (int j = 0; j < m; ++j)
+                for (int i = t; i < n; i += B)
+                    if (fabs(V[(size_t)j * n + i] - V[(size_t)l * n + i]) > xtol * (hi[i] - lo[i])) small = 0;
+            if (__syncthreads_and(small)) break;
+        }
+        const double* vh = V + (size_t)h * n;
+        for (int i = t; i < n; i += B) {
+            double a;
+            if (n <= kNmExactN) {
+                a = 0.0;
+                for (int j = 0; j < m; ++j)
+                    if (j != h) a += V[(size_t)j * n + i];
+            } else {
+                a = S[i] - vh[i];
+            }
+            xc[i] = a / (double)n;
+            xr[i] = clipd(xc[i] + (xc[i] - vh[i]), lo[i], hi[i]);
+        }
+        __syncthreads();
+        const double fr = bcost(cost, n, xr, QT, red);
+        bool accept = false, trial = false;
+        double fa = fr;
+        if (fr < fl) {  // expansion
+            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + 2.0 * (xr[i] - xc[i]), lo[i], hi[i]);
+            __syncthreads();
+            const double fe = bcost(cost, n, xt, QT, red);
+            accept = true;
+            if (fe < fr) { fa = fe; trial = true; }
+        } else if (fr < fs) {
+            accept = true;
+        } else if (fr < fh) {  // outside contraction
+            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + 0.5 * (xr[i] - xc[i]), lo[i], hi[i]);
+            __syncthreads();
+            const double fo = bcost(cost, n, xt, QT, red);
+            if (fo <= fr) { accept = true; fa = fo; trial = true; }
+        } else {  // inside contraction
+            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] - 0.5 * (xc[i] - vh[i]), lo[i], hi[i]);
+            __syncthreads();
+            const double fi = bcost(cost, n, xt, QT, red);
+            if (fi < fh) { accept = true; fa = fi; trial = true; }
+        }
+        if (accept) {
+            double* dst = V + (size_t)h * n;
+            for (int i = t; i < n; i += B) {
+                const double a = trial ? xt[i] : xr[i];
+                S[i] += a - dst[i];
+                dst[i] = a;
+            }
+            if (t == 0) F[h] = fa;
+            __syncthreads();
+            if ((it + 1) % m == 0) resum();  // bound the drift of the running sum
+        } else {  // shrink towards the best vertex
+            const double* vl = V + (size_t)l * n;
+            for (int j = 0; j < m; ++j) {
+                if (j == l) continue;
+                double* v = V + (size_t)j * n;
+                for (int i = t; i < n; i += B) {
+                    const double a = clipd(vl[i] + 0.5 * (v[i] - vl[i]), lo[i], hi[i]);
+                    v[i] = a;
+                    xt[i] = a;
+                }
+                __syncthreads();
+                const double f = bcost(cost, n, xt, QT, red);
+                if (t == 0) F[j] = f;
+            }
+            resum();
+        }
+        __syncthreads();
+    }
+    double fl;
+    int l = nm_pick(F, m, true, -1, red, jred, &fl);
+    if (l >= m) l = 0;
+    for (int i = t; i < n; i += B) x_out[(size_t)w * n + i] = V[(size_t)l * n + i];
+    if (t == 0) {
+        f_out[w] = fl;
+        if (it_out) it_out[w] = it;
+    }
+}
+
 // Top-k of the level's FP64 values (lowest value, then lowest index), one block;
 // destroys the copy it works on by marking winners with +inf.
 __global__ void topk_kernel(double* F, int64_t count, int k, int64_t* idx_out) {
@@ -251,6 +478,27 @@ cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, cons
     if (e != cudaSuccess) return e;
     pgd_kernel<<<(k + warps - 1) / warps, 32 * warps, smem, s>>>(cost, n, lo, hi, Q, k, x0, x_out, f_out, it_out,
                                                                   max_iter, tol, 1e-4, 30);
+    return cudaGetLastError();
+}
+
+size_t nm_ws_doubles(int n) { return (size_t)(n + 1) * (size_t)n; }
+
+int nm_max_n() { return kNmMaxN; }
+
+cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, int k, const double* x0,
+                      double* x_out, double* f_out, int* it_out, double step_frac, int max_iter, double ftol,
+                      double xtol, double* ws, cudaStream_t s) {
+    if (n < 1 || n > kNmMaxN) return cudaErrorInvalidValue;
+    const int block = std::min(1024, std::max(32, (n + 31) / 32 * 32));
+    const size_t smem = ((size_t)(n + 1) + 4 * (size_t)n + 32) * sizeof(double) + 32 * sizeof(int);
+    static size_t current = 0;  // the limit only grows
+    if (smem > current) {
+        const cudaError_t e = cudaFuncSetAttribute(nm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        current = smem;
+    }
+    nm_kernel<<<k, block, smem, s>>>(cost, n, lo, hi, QT, x0, x_out, f_out, it_out, step_frac, max_iter, ftol, xtol,
+                                     ws);
     return cudaGetLastError();
 }
 

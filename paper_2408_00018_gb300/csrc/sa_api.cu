@@ -102,6 +102,8 @@ struct sa_handle {
     int64_t* d_topk = nullptr;
     double *d_px0 = nullptr, *d_px = nullptr, *d_pf = nullptr;
     int* d_pit = nullptr;
+    double* d_nmws = nullptr;  // Nelder-Mead workspace (polish_method == SA_POLISH_NELDER_MEAD)
+    double nm_step = 0.0;      // its initial simplex size, as a fraction of the box
     SweepArgs args{};
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
     // delayed acceptance with the surrogate (schedule.surrogate == 1)
@@ -164,6 +166,7 @@ sa_status check_schedule(const sa_schedule* s) {
     if (s->boundary != SA_REFLECT && s->boundary != SA_CLIP) return SA_EINVAL;
     if (s->precision != SA_FP64 && s->precision != SA_FP32) return SA_EINVAL;
     if ((s->surrogate != 0 && s->surrogate != 1) || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
+    if (s->polish_method != SA_POLISH_PGD && s->polish_method != SA_POLISH_NELDER_MEAD) return SA_EINVAL;
     if (s->cost_repeat < 0 || s->cost_repeat > 4096) return SA_EINVAL;
     if ((s->independent != 0 && s->independent != 1) || (s->independent && s->surrogate)) return SA_EINVAL;
     if (s->exchange_every < 0 || (s->exchange_every > 1 && s->surrogate)) return SA_EINVAL;
@@ -362,8 +365,8 @@ sa_status device_status(sa_handle* h) {
 
 // Hybrid SA (after the last level): the polish_k best final states of each
 // problem, by FP64 value with lowest index on ties, are polished by
-// box-projected gradient descent; the best polished point replaces the
-// incumbent if it is lower.
+// box-projected gradient descent or by Nelder-Mead (Sec. 4.2, Table 10); the
+// best polished point replaces the incumbent if it is lower.
 sa_status run_polish(sa_handle* h) {
     if (h->sch.polish_k <= 0) return SA_OK;
     for (size_t p = 0; p < h->probs.size(); ++p) {
@@ -374,8 +377,11 @@ sa_status run_polish(sa_handle* h) {
             launch_topk(h->d_Fcopy, hp.chains, k, h->d_topk, h->stream) != cudaSuccess ||
             launch_gather(h->d_X32, h->d_X64, hp.x_base, hp.chains, hp.n, h->d_topk, k, h->d_px0, h->stream) !=
                 cudaSuccess ||
-            launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.q64, k, h->d_px0, h->d_px, h->d_pf, h->d_pit, 1000,
-                       1e-10, h->stream) != cudaSuccess ||
+            (h->sch.polish_method == SA_POLISH_NELDER_MEAD
+                 ? launch_nm(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.qt64, k, h->d_px0, h->d_px, h->d_pf, h->d_pit,
+                             h->nm_step, 200 * (hp.n + 1), 1e-12, 1e-10, h->d_nmws, h->stream)
+                 : launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.q64, k, h->d_px0, h->d_px, h->d_pf,
+                              h->d_pit, 1000, 1e-10, h->stream)) != cudaSuccess ||
             launch_polish_update(h->d_probs, (int)p, h->d_px, h->d_pf, k, h->stream) != cudaSuccess)
             return fail(h, SA_ECUDA);
     }
@@ -697,6 +703,11 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
             (st = dalloc(h, &h->d_px0, k * n_max)) || (st = dalloc(h, &h->d_px, k * n_max)) ||
             (st = dalloc(h, &h->d_pf, k)) || (st = dalloc(h, &h->d_pit, k)))
             return st;
+        if (h->sch.polish_method == SA_POLISH_NELDER_MEAD) {
+            if (n_max > nm_max_n() || k * nm_ws_doubles(n_max) * sizeof(double) > ((size_t)1 << 32)) return SA_EINVAL;
+            if ((st = dalloc(h, &h->d_nmws, k * nm_ws_doubles(n_max)))) return st;
+            h->nm_step = std::min(1.0, h->sch.sigma_frac * s.back());  // s[l] = sqrt(T_l / T0)
+        }
     }
     a.boundary = h->sch.boundary;
     a.key0 = (uint32_t)h->seed;
@@ -920,6 +931,57 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
          cudaStreamSynchronize(s)))
         st = SA_ECUDA;
     for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit, (void*)dq})
+        if (p) cudaFreeAsync(p, s);
+    cudaGetLastError();
+    return st;
+}
+
+sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
+                         const double* x0, double step_frac, int32_t max_iter, double ftol, double xtol,
+                         double* x_out, double* f_out, int32_t* iters_out, void* stream) {
+    if (n < 1 || k < 1 || k > 1024 || !lo || !hi || !x0 || !x_out || !f_out || max_iter < 0 || !(ftol >= 0.0) ||
+        !(xtol >= 0.0) || !(step_frac > 0.0 && step_frac <= 1.0))
+        return SA_EINVAL;
+    if (cost < SA_SCHWEFEL || cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
+    const bool rot = is_rot(cost);
+    if (rot != (Q != nullptr) || n > nm_max_n()) return SA_EINVAL;
+    const size_t ws = (size_t)k * nm_ws_doubles(n);
+    if (ws * sizeof(double) > ((size_t)1 << 32)) return SA_EINVAL;
+    for (int d = 0; d < n; ++d)
+        if (!std::isfinite(lo[d]) || !std::isfinite(hi[d]) || lo[d] > hi[d]) return SA_EINVAL;
+    std::vector<double> qt;
+    if (rot) {
+        qt.resize((size_t)n * n);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double q = Q[(size_t)i * n + j];
+                if (!std::isfinite(q)) return SA_EINVAL;
+                qt[(size_t)j * n + i] = q;
+            }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *dlo = nullptr, *dhi = nullptr, *dx0 = nullptr, *dx = nullptr, *df = nullptr, *dq = nullptr, *dws = nullptr;
+    int* dit = nullptr;
+    const size_t kn = (size_t)k * n;
+    sa_status st = SA_OK;
+    if ((rot && cudaMallocAsync(&dq, (size_t)n * n * sizeof(double), s)) ||
+        cudaMallocAsync(&dlo, n * sizeof(double), s) || cudaMallocAsync(&dhi, n * sizeof(double), s) ||
+        cudaMallocAsync(&dx0, kn * sizeof(double), s) || cudaMallocAsync(&dx, kn * sizeof(double), s) ||
+        cudaMallocAsync(&df, k * sizeof(double), s) || cudaMallocAsync(&dit, k * sizeof(int), s) ||
+        cudaMallocAsync(&dws, ws * sizeof(double), s))
+        st = SA_ENOMEM;
+    if (st == SA_OK &&
+        ((rot && cudaMemcpyAsync(dq, qt.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+         cudaMemcpyAsync(dlo, lo, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
+         cudaMemcpyAsync(dhi, hi, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
+         cudaMemcpyAsync(dx0, x0, kn * sizeof(double), cudaMemcpyHostToDevice, s) ||
+         launch_nm(cost, n, dlo, dhi, dq, k, dx0, dx, df, dit, step_frac, max_iter, ftol, xtol, dws, s) ||
+         cudaMemcpyAsync(x_out, dx, kn * sizeof(double), cudaMemcpyDeviceToHost, s) ||
+         cudaMemcpyAsync(f_out, df, k * sizeof(double), cudaMemcpyDeviceToHost, s) ||
+         (iters_out && cudaMemcpyAsync(iters_out, dit, k * sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+         cudaStreamSynchronize(s)))
+        st = SA_ECUDA;
+    for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit, (void*)dq, (void*)dws})
         if (p) cudaFreeAsync(p, s);
     cudaGetLastError();
     return st;

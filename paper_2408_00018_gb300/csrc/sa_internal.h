@@ -131,6 +131,13 @@ int sweep_f32w_chains_per_block();
 cudaError_t sweep_f64_set_smem(size_t bytes);
 cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, const double* Q, int k, const double* x0,
                        double* x_out, double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s);
+// Nelder-Mead from k starts (one block each); ws: k * nm_ws_doubles(n) doubles; rotated
+// costs take QT = Q^T (row-major, i.e. Q column-major); n <= nm_max_n().
+size_t nm_ws_doubles(int n);
+int nm_max_n();
+cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, int k, const double* x0,
+                      double* x_out, double* f_out, int* it_out, double step_frac, int max_iter, double ftol,
+                      double xtol, double* ws, cudaStream_t s);
 cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStream_t s);
 cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
                                  int* status, cudaStream_t s);

@@ -20,6 +20,7 @@ SA_OK, SA_EINVAL, SA_ENOMEM, SA_ECUDA, SA_ETIMEOUT, SA_ENUMERIC, SA_ESTATE = ran
 COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "rot_rastrigin": 4, "rot_schwefel": 5}
 BOUNDARY = {"reflect": 0, "clip": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_bf16": 2}
+POLISH = {"pgd": 0, "nelder_mead": 1}
 
 
 class SAError(RuntimeError):
@@ -41,7 +42,7 @@ class _Schedule(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("sigma_frac", ctypes.c_double), ("boundary", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("surrogate", ctypes.c_int32), ("polish_k", ctypes.c_int32),
                 ("trace_levels", ctypes.c_int32), ("cost_repeat", ctypes.c_int32), ("independent", ctypes.c_int32),
-                ("exchange_every", ctypes.c_int32)]
+                ("exchange_every", ctypes.c_int32), ("polish_method", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -76,6 +77,7 @@ SIGNATURES = {
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
     "sa_polish": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _I32, _D, _V, _V, _V, _V]),
+    "sa_nelder_mead": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _D, _I32, _D, _D, _V, _V, _V, _V]),
     "sa_gemm_bf16": (ctypes.c_int, [_V, _I32, _V, _I32, _V, _I32, _I32, _I32, _I32, _V, _V]),
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
@@ -149,11 +151,12 @@ class Schedule:
     cost_repeat: int = 1
     independent: int = 0
     exchange_every: int = 1
+    polish_method: str = "pgd"
 
     def _c(self) -> _Schedule:
         return _Schedule(self.T0, self.rho, self.T_min, self.levels, self.sigma_frac, BOUNDARY[self.boundary],
                          PRECISION[self.precision], self.surrogate, self.polish_k, self.trace_levels,
-                         self.cost_repeat, self.independent, self.exchange_every)
+                         self.cost_repeat, self.independent, self.exchange_every, POLISH[self.polish_method])
 
 
 def levels_for(T0: float, rho: float, T_min: float) -> int:
@@ -382,6 +385,26 @@ def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, Q=None, s
                             None if Qa is None else Qa.ctypes.data, k, x0.ctypes.data, max_iter, tol, x.ctypes.data,
                             f.ctypes.data, it.ctypes.data, s),
            "sa_polish")
+    return x, f, it
+
+
+def nelder_mead(cost, x0, lo, hi, step_frac: float = 0.05, max_iter: int = 20000, ftol: float = 1e-12,
+                xtol: float = 1e-10, Q=None, stream=None):
+    """sa_nelder_mead: Nelder-Mead with box clipping from each row of x0 (k x n); returns (x, f, iters).
+    Rotated costs take Q (n x n)."""
+    x0 = np.ascontiguousarray(np.atleast_2d(np.asarray(x0, np.float64)))
+    k, n = x0.shape
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (n,)))
+    x = np.zeros_like(x0)
+    f = np.zeros(k)
+    it = np.zeros(k, np.int32)
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    _check(load().sa_nelder_mead(COSTS[cost] if isinstance(cost, str) else int(cost), n, lo.ctypes.data,
+                                 hi.ctypes.data, None if Qa is None else Qa.ctypes.data, k, x0.ctypes.data, step_frac,
+                                 max_iter, ftol, xtol, x.ctypes.data, f.ctypes.data, it.ctypes.data, s),
+           "sa_nelder_mead")
     return x, f, it
 
 

@@ -53,7 +53,7 @@ def test_rosenbrock_textbook_start_converges_to_the_minimum():
 
 
 def test_closed_form_minima():
-    xs = 420.968746359982  # the Schwefel term's stationary point, sqrt(t) = the root of tan r = -2r
+    xs = 420.968746359982  # the Schwefel term's stationary point: t = r^2 with tan r = -r/2
     x, f, _ = oracle.nelder_mead("schwefel", np.full(4, 405.0), -500, 500, ftol=1e-15)
     assert np.allclose(x, xs, atol=1e-4)
     assert abs(f - oracle.cost("schwefel", np.full(4, xs))) < 1e-10
