@@ -31,7 +31,10 @@ _lock = threading.Lock()
 _lib = None
 
 COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3,
-         "rot_rastrigin": 4, "rot_schwefel": 5}
+         "rot_rastrigin": 4, "rot_schwefel": 5,
+         "branin": 6, "cosine_mixture": 7, "dekkers_aarts": 8, "easom": 9, "exponential": 10,
+         "goldstein_price": 11, "griewank": 12, "himmelblau": 13, "levy_montalvo": 14, "langerman": 15,
+         "michalewicz": 16, "salomon": 17, "six_hump_camel": 18, "shubert": 19, "shekel": 20, "foxholes": 21}
 TAG_SWEEP, TAG_INIT, TAG_DA = 0, 1, 3
 
 
@@ -53,7 +56,8 @@ class Cfg(ctypes.Structure):
                 ("problem", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("T0", ctypes.c_double),
                 ("rho", ctypes.c_double), ("sigma_frac", ctypes.c_double),
                 ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p),
-                ("independent", ctypes.c_int32), ("exchange_every", ctypes.c_int32)]
+                ("independent", ctypes.c_int32), ("exchange_every", ctypes.c_int32),
+                ("table", ctypes.c_void_p), ("table_rows", ctypes.c_int32)]
 
 
 class Out(ctypes.Structure):
@@ -74,7 +78,7 @@ def lib():
             L.sao_uniform.restype = f64
             L.sao_coord.argtypes = [u32, i32]
             L.sao_coord.restype = u32
-            L.sao_cost.argtypes = [i32, i32, vp, vp]
+            L.sao_cost.argtypes = [i32, i32, vp, vp, vp, i32]
             L.sao_cost.restype = f64
             L.sao_grad.argtypes = [i32, i32, vp, vp, vp]
             L.sao_temperature.argtypes = [f64, f64, i32]
@@ -98,7 +102,7 @@ def lib():
             L.sao_level_chains.restype = ctypes.c_int
             L.sao_pgd.argtypes = [i32, i32, vp, vp, vp, vp, i32, f64, f64, i32, vp, vp]
             L.sao_pgd.restype = ctypes.c_int
-            L.sao_nelder_mead.argtypes = [i32, i32, vp, vp, vp, vp, f64, i32, f64, f64, vp, vp]
+            L.sao_nelder_mead.argtypes = [i32, i32, vp, vp, vp, vp, i32, vp, f64, i32, f64, f64, vp, vp]
             L.sao_nelder_mead.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -129,11 +133,20 @@ def coord(w: int, n: int) -> int:
     return lib().sao_coord(int(w), int(n))
 
 
-def cost(name_or_id, x, Q=None) -> float:
+def _table(table):
+    """(array, rows) of a table of rows (a_i1 .. a_in, c_i), or (None, 0)."""
+    if table is None:
+        return None, 0
+    t = np.ascontiguousarray(np.atleast_2d(np.asarray(table, np.float64)))
+    return t, t.shape[0]
+
+
+def cost(name_or_id, x, Q=None, table=None) -> float:
     cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
     x = np.ascontiguousarray(x, dtype=np.float64)
     Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
-    return lib().sao_cost(cid, x.size, _p(x), _p(Qa))
+    t, rows = _table(table)
+    return lib().sao_cost(cid, x.size, _p(x), _p(Qa), _p(t), rows)
 
 
 def grad(name_or_id, x, Q=None) -> np.ndarray:
@@ -158,7 +171,7 @@ class Problem:
 
     def __init__(self, cost, n, lo, hi, chains, L, T0=100.0, rho=0.9, sigma_frac=0.1,
                  boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0, independent=False,
-                 exchange_every=1):
+                 exchange_every=1, table=None):
         self.cost = COSTS[cost] if isinstance(cost, str) else int(cost)
         self.n = int(n)
         self.lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.n,)))
@@ -170,11 +183,13 @@ class Problem:
         self.seed, self.problem, self.mode, self.threads = int(seed), int(problem), int(mode), int(threads)
         self.independent = 1 if independent else 0
         self.exchange_every = int(exchange_every)
+        self.table, self.table_rows = _table(table)
 
     def cfg(self, K=0, level0=0) -> Cfg:
         return Cfg(self.cost, self.n, self.chains, self.L, K, level0, self.boundary, self.mode,
                    self.threads, self.problem, self.seed, self.T0, self.rho, self.sigma_frac,
-                   _p(self.lo), _p(self.hi), _p(self.Q), self.independent, self.exchange_every)
+                   _p(self.lo), _p(self.hi), _p(self.Q), self.independent, self.exchange_every,
+                   _p(self.table), self.table_rows)
 
     def init_point(self, c: int) -> np.ndarray:
         x = np.zeros(self.n)
@@ -301,7 +316,8 @@ def pgd(name_or_id, x0, lo, hi, Q=None, max_iter=1000, tol=1e-10, armijo_c=1e-4,
     return x, float(f[0]), int(it[0])
 
 
-def nelder_mead(name_or_id, x0, lo, hi, Q=None, step_frac=0.05, max_iter=20000, ftol=1e-12, xtol=1e-10):
+def nelder_mead(name_or_id, x0, lo, hi, Q=None, step_frac=0.05, max_iter=20000, ftol=1e-12, xtol=1e-10,
+                table=None):
     """Nelder-Mead with box clipping from x0; returns (x, f, iterations)."""
     cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
     x = np.array(x0, np.float64)
@@ -311,7 +327,9 @@ def nelder_mead(name_or_id, x0, lo, hi, Q=None, step_frac=0.05, max_iter=20000, 
     Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
     f = np.zeros(1)
     it = np.zeros(1, np.int32)
-    rc = lib().sao_nelder_mead(cid, n, _p(lo), _p(hi), _p(Qa), _p(x), step_frac, max_iter, ftol, xtol, _p(f), _p(it))
+    t, rows = _table(table)
+    rc = lib().sao_nelder_mead(cid, n, _p(lo), _p(hi), _p(Qa), _p(t), rows, _p(x), step_frac, max_iter, ftol, xtol,
+                               _p(f), _p(it))
     if rc != 0:
         raise ValueError("sao_nelder_mead failed")
     return x, float(f[0]), int(it[0])

@@ -46,7 +46,23 @@
 #define SAO_TAG_DA 3u
 
 enum { SAO_SCHWEFEL = 0, SAO_RASTRIGIN = 1, SAO_ACKLEY = 2, SAO_ROSENBROCK = 3,
-       SAO_ROT_RASTRIGIN = 4, SAO_ROT_SCHWEFEL = 5 };
+       SAO_ROT_RASTRIGIN = 4, SAO_ROT_SCHWEFEL = 5,
+       /* the rest of the Appendix's test suite */
+       SAO_BRANIN = 6, SAO_COSINE_MIXTURE = 7, SAO_DEKKERS_AARTS = 8, SAO_EASOM = 9, SAO_EXPONENTIAL = 10,
+       SAO_GOLDSTEIN_PRICE = 11, SAO_GRIEWANK = 12, SAO_HIMMELBLAU = 13, SAO_LEVY_MONTALVO = 14,
+       SAO_LANGERMAN = 15, SAO_MICHALEWICZ = 16, SAO_SALOMON = 17, SAO_SIX_HUMP_CAMEL = 18, SAO_SHUBERT = 19,
+       SAO_SHEKEL = 20, SAO_FOXHOLES = 21, SAO_NUM_COSTS = 22 };
+
+static int is_rot(int32_t cost) { return cost == SAO_ROT_RASTRIGIN || cost == SAO_ROT_SCHWEFEL; }
+/* Costs with a table of rows (a_i, c_i): Tests 11, 18 and 19. */
+static int is_table(int32_t cost) { return cost == SAO_LANGERMAN || cost == SAO_SHEKEL || cost == SAO_FOXHOLES; }
+/* Costs defined for n = 2 only. */
+static int is_2d(int32_t cost) {
+    return cost == SAO_BRANIN || cost == SAO_DEKKERS_AARTS || cost == SAO_EASOM || cost == SAO_GOLDSTEIN_PRICE ||
+           cost == SAO_HIMMELBLAU || cost == SAO_SIX_HUMP_CAMEL;
+}
+/* Costs with a local energy difference in mode 1 (the others recompute f in full). */
+static int has_local(int32_t cost) { return cost <= SAO_ROT_SCHWEFEL; }
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from its definition (Salmon et al. 2011, Sec. 4):   */
@@ -134,8 +150,132 @@ static void rotate(int n, const double* Q, const double* x, double* y) {
     }
 }
 
-/* Full definition of f at x (ywork: n doubles of scratch for rotated costs). */
-double sao_cost_ws(int32_t cost, int32_t n, const double* x, const double* Q, double* ywork) {
+/* ---- the rest of the Appendix (Tests 2-12 and 15-19), x[0] is the paper's x_1 ---- */
+
+/* Test 2, Branin: (x2 - 5.1 x1^2 / (4 pi^2) + 5 x1 / pi - 6)^2 + 10 (1 - 1/(8 pi)) cos x1 + 10. */
+static double f_branin(const double* x) {
+    const double a = x[1] - 5.1 * x[0] * x[0] / (4.0 * M_PI * M_PI) + 5.0 * x[0] / M_PI - 6.0;
+    return a * a + 10.0 * (1.0 - 1.0 / (8.0 * M_PI)) * cos(x[0]) + 10.0;
+}
+/* Test 3, cosine mixture, read as sum x_i^2 - 0.1 sum cos(5 pi x_i): the printed
+ * signs give a minimum of -0.9 n at the corners, not the printed -0.1 n at 0. */
+static double f_cosine_mixture(int n, const double* x) {
+    double c = 0.0, q = 0.0;
+    for (int i = 0; i < n; ++i) { c += cos(5.0 * M_PI * x[i]); q += x[i] * x[i]; }
+    return q - 0.1 * c;
+}
+/* Test 4, Dekkers and Aarts: 1e5 x1^2 + x2^2 - (x1^2 + x2^2)^2 + 1e-5 (x1^2 + x2^2)^4. */
+static double f_dekkers_aarts(const double* x) {
+    const double a = x[0] * x[0], b = x[1] * x[1], r = a + b;
+    return 1e5 * a + b - r * r + 1e-5 * (r * r) * (r * r);
+}
+/* Test 5, Easom: -cos x1 cos x2 exp(-(x1 - pi)^2 - (x2 - pi)^2). */
+static double f_easom(const double* x) {
+    const double u = x[0] - M_PI, v = x[1] - M_PI;
+    return -cos(x[0]) * cos(x[1]) * exp(-u * u - v * v);
+}
+/* Test 6, exponential: -exp(-0.5 sum x_i^2). */
+static double f_exponential(int n, const double* x) {
+    double q = 0.0;
+    for (int i = 0; i < n; ++i) q += x[i] * x[i];
+    return -exp(-0.5 * q);
+}
+/* Test 7, Goldstein and Price. */
+static double f_goldstein_price(const double* x) {
+    const double a = x[0], b = x[1];
+    const double s = a + b + 1.0, t = 2.0 * a - 3.0 * b;
+    const double p = 1.0 + s * s * (19.0 - 14.0 * a + 3.0 * a * a - 14.0 * b + 6.0 * a * b + 3.0 * b * b);
+    const double q = 30.0 + t * t * (18.0 - 32.0 * a + 12.0 * a * a + 48.0 * b - 36.0 * a * b + 27.0 * b * b);
+    return p * q;
+}
+/* Test 8, Griewank, read in its standard form 1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt i)
+ * (the paper prints the product inside the sum), i = 1..n. */
+static double f_griewank(int n, const double* x) {
+    double q = 0.0, p = 1.0;
+    for (int i = 0; i < n; ++i) {
+        q += x[i] * x[i];
+        p *= cos(x[i] / sqrt((double)(i + 1)));
+    }
+    return 1.0 + q / 4000.0 - p;
+}
+/* Test 9, Himmelblau: (x1^2 + x2 - 11)^2 + (x1 + x2^2 - 7)^2. */
+static double f_himmelblau(const double* x) {
+    const double a = x[0] * x[0] + x[1] - 11.0, b = x[0] + x[1] * x[1] - 7.0;
+    return a * a + b * b;
+}
+/* Test 10, Levy and Montalvo: (pi/n) (10 sin^2(pi y_1) + sum_{i<n} (y_i - 1)^2 (1 + 10 sin^2(pi y_{i+1}))
+ * + (y_n - 1)^2), y_i = 1 + (x_i + 1) / 4. */
+static double f_levy_montalvo(int n, const double* x) {
+    double y0 = 1.0 + (x[0] + 1.0) / 4.0;
+    const double s0 = sin(M_PI * y0);
+    double s = 10.0 * s0 * s0;
+    for (int i = 0; i + 1 < n; ++i) {
+        const double yi = 1.0 + (x[i] + 1.0) / 4.0, yn = 1.0 + (x[i + 1] + 1.0) / 4.0;
+        const double sn = sin(M_PI * yn);
+        s += (yi - 1.0) * (yi - 1.0) * (1.0 + 10.0 * sn * sn);
+    }
+    const double yl = 1.0 + (x[n - 1] + 1.0) / 4.0;
+    s += (yl - 1.0) * (yl - 1.0);
+    return M_PI / (double)n * s;
+}
+/* Squared distance of x to row i of a table of rows (a_i1 .. a_in, c_i). */
+static double row_dist2(int n, const double* x, const double* row) {
+    double d = 0.0;
+    for (int j = 0; j < n; ++j) d += (x[j] - row[j]) * (x[j] - row[j]);
+    return d;
+}
+/* Test 11, modified Langerman: -sum_i c_i exp(-D_i / pi) cos(pi D_i), D_i = |x - a_i|^2. */
+static double f_langerman(int n, const double* x, const double* table, int rows) {
+    double s = 0.0;
+    for (int i = 0; i < rows; ++i) {
+        const double* r = table + (size_t)i * (size_t)(n + 1);
+        const double d = row_dist2(n, x, r);
+        s += r[n] * exp(-d / M_PI) * cos(M_PI * d);
+    }
+    return -s;
+}
+/* Test 12, Michalewicz with m = 10: -sum_i sin(x_i) sin(i x_i^2 / pi)^20, i = 1..n. */
+static double f_michalewicz(int n, const double* x) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += sin(x[i]) * pow(sin((double)(i + 1) * x[i] * x[i] / M_PI), 20.0);
+    return -s;
+}
+/* Test 15, Salomon: 1 - cos(2 pi |x|) + 0.1 |x|. */
+static double f_salomon(int n, const double* x) {
+    double q = 0.0;
+    for (int i = 0; i < n; ++i) q += x[i] * x[i];
+    const double r = sqrt(q);
+    return 1.0 - cos(2.0 * M_PI * r) + 0.1 * r;
+}
+/* Test 16, six-hump camel back: (4 - 2.1 x1^2 + x1^4 / 3) x1^2 + x1 x2 + (-4 + 4 x2^2) x2^2. */
+static double f_six_hump_camel(const double* x) {
+    const double a = x[0] * x[0], b = x[1] * x[1];
+    return (4.0 - 2.1 * a + a * a / 3.0) * a + x[0] * x[1] + (-4.0 + 4.0 * b) * b;
+}
+/* Test 17, Shubert: prod_i sum_{j=1..5} j cos((j + 1) x_i + j). */
+static double f_shubert(int n, const double* x) {
+    double p = 1.0;
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 1; j <= 5; ++j) s += (double)j * cos((double)(j + 1) * x[i] + (double)j);
+        p *= s;
+    }
+    return p;
+}
+/* Tests 18 and 19, Shekel and modified Shekel foxholes: -sum_i 1 / (D_i + c_i). */
+static double f_shekel(int n, const double* x, const double* table, int rows) {
+    double s = 0.0;
+    for (int i = 0; i < rows; ++i) {
+        const double* r = table + (size_t)i * (size_t)(n + 1);
+        s += 1.0 / (row_dist2(n, x, r) + r[n]);
+    }
+    return -s;
+}
+
+/* Full definition of f at x.  Q: rotated costs' n x n matrix; table: rows x (n + 1)
+ * (a_i, c_i) of Tests 11, 18, 19; ywork: n doubles of scratch for rotated costs. */
+double sao_cost_tab(int32_t cost, int32_t n, const double* x, const double* Q, const double* table, int32_t rows,
+                    double* ywork) {
     switch (cost) {
     case SAO_SCHWEFEL: return f_schwefel(n, x);
     case SAO_RASTRIGIN: return f_rastrigin(n, x);
@@ -143,12 +283,30 @@ double sao_cost_ws(int32_t cost, int32_t n, const double* x, const double* Q, do
     case SAO_ROSENBROCK: return f_rosenbrock(n, x);
     case SAO_ROT_RASTRIGIN: rotate(n, Q, x, ywork); return f_rastrigin(n, ywork);
     case SAO_ROT_SCHWEFEL: rotate(n, Q, x, ywork); return f_schwefel(n, ywork);
+    case SAO_BRANIN: return f_branin(x);
+    case SAO_COSINE_MIXTURE: return f_cosine_mixture(n, x);
+    case SAO_DEKKERS_AARTS: return f_dekkers_aarts(x);
+    case SAO_EASOM: return f_easom(x);
+    case SAO_EXPONENTIAL: return f_exponential(n, x);
+    case SAO_GOLDSTEIN_PRICE: return f_goldstein_price(x);
+    case SAO_GRIEWANK: return f_griewank(n, x);
+    case SAO_HIMMELBLAU: return f_himmelblau(x);
+    case SAO_LEVY_MONTALVO: return f_levy_montalvo(n, x);
+    case SAO_LANGERMAN: return f_langerman(n, x, table, rows);
+    case SAO_MICHALEWICZ: return f_michalewicz(n, x);
+    case SAO_SALOMON: return f_salomon(n, x);
+    case SAO_SIX_HUMP_CAMEL: return f_six_hump_camel(x);
+    case SAO_SHUBERT: return f_shubert(n, x);
+    case SAO_SHEKEL: case SAO_FOXHOLES: return f_shekel(n, x, table, rows);
     default: return NAN;
     }
 }
-double sao_cost(int32_t cost, int32_t n, const double* x, const double* Q) {
-    double* y = (cost >= SAO_ROT_RASTRIGIN) ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
-    double f = sao_cost_ws(cost, n, x, Q, y);
+double sao_cost_ws(int32_t cost, int32_t n, const double* x, const double* Q, double* ywork) {
+    return sao_cost_tab(cost, n, x, Q, NULL, 0, ywork);
+}
+double sao_cost(int32_t cost, int32_t n, const double* x, const double* Q, const double* table, int32_t rows) {
+    double* y = is_rot(cost) ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+    double f = sao_cost_tab(cost, n, x, Q, table, rows, y);
     free(y);
     return f;
 }
@@ -221,6 +379,8 @@ typedef struct {
                             incumbent).  Independent runs start at level 0. */
     int32_t exchange_every; /* > 1: the exchange (restart from the best) only after levels
                                m-1, 2m-1, ...; chains continue their own states in between */
+    const double* table; /* Tests 11, 18, 19: rows x (n + 1), row i = (a_i1 .. a_in, c_i) */
+    int32_t table_rows;
 } sao_cfg;
 
 typedef struct {
@@ -326,14 +486,14 @@ static double da_fn(const sao_cfg* cfg, const sao_da* da, const double* x, doubl
 static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
                              uint32_t* bits, int64_t* n_accept, double* dF_out, double* tau_out,
                              const sao_da* da, int64_t* n_true) {
-    double* ywork = (cfg->cost >= SAO_ROT_RASTRIGIN) ? (double*)malloc(sizeof(double) * (size_t)cfg->n) : NULL;
+    double* ywork = is_rot(cfg->cost) ? (double*)malloc(sizeof(double) * (size_t)cfg->n) : NULL;
     const int n = cfg->n;
     const double T = sao_temperature(cfg->T0, cfg->rho, level);
     const double s_l = sqrt(T / cfg->T0);
-    const int rot = cfg->cost >= SAO_ROT_RASTRIGIN;
+    const int rot = is_rot(cfg->cost);
     double* y = rot ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
     double* yp = rot ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
-    double F = sao_cost_ws(cfg->cost, n, x, cfg->Q, y);
+    double F = sao_cost_tab(cfg->cost, n, x, cfg->Q, cfg->table, cfg->table_rows, y);
     double S1 = 0.0, S2 = 0.0, G = 0.0;
     if (cfg->mode == 1 && cfg->cost == SAO_ACKLEY)
         for (int i = 0; i < n; ++i) { S1 += x[i] * x[i]; S2 += cos(2.0 * M_PI * x[i]); }
@@ -381,7 +541,7 @@ static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, doubl
         double dF, Fp = 0.0, S1p = 0.0, S2p = 0.0, Gp = 0.0;
         if (cfg->mode == 0) {
             x[d] = xp;
-            Fp = sao_cost_ws(cfg->cost, n, x, cfg->Q, y);
+            Fp = sao_cost_tab(cfg->cost, n, x, cfg->Q, cfg->table, cfg->table_rows, y);
             x[d] = xd;
             dF = Fp - F;
         } else if (cfg->cost == SAO_SCHWEFEL) {
@@ -424,7 +584,7 @@ static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, doubl
             }
         }
     }
-    double Fend = sao_cost_ws(cfg->cost, n, x, cfg->Q, yp ? yp : y);
+    double Fend = sao_cost_tab(cfg->cost, n, x, cfg->Q, cfg->table, cfg->table_rows, yp ? yp : y);
     free(y);
     free(yp);
     free(ywork);
@@ -468,6 +628,15 @@ double sao_chain_level_steps(const sao_cfg* cfg, int32_t level, int64_t c, doubl
     return chain_level(cfg, level, c, x, bits, n_accept, dF_out, tau_out);
 }
 
+/* The cost's own requirements: Q for rotated costs, a table for Tests 11, 18, 19,
+ * n = 2 for the two-variable tests, mode 0 where no local difference is written. */
+static int cost_ok(const sao_cfg* cfg) {
+    if (cfg->cost < 0 || cfg->cost >= SAO_NUM_COSTS || (is_rot(cfg->cost) && !cfg->Q)) return 0;
+    if (is_table(cfg->cost) && (!cfg->table || cfg->table_rows < 1)) return 0;
+    if ((is_2d(cfg->cost) && cfg->n != 2) || (cfg->mode == 1 && !has_local(cfg->cost))) return 0;
+    return 1;
+}
+
 /*
  * Run levels level0 .. level0+K-1 of synchronous parallel SA (Listings 3-4).
  * Returns 0 on success, -1 on a bad argument, -2 on allocation failure.
@@ -476,7 +645,7 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
     if (!cfg || !out || cfg->n < 1 || cfg->chains < 1 || cfg->L < 0 || cfg->K < 0 ||
         !cfg->lo || !cfg->hi || !out->x_best || !out->f_best || !out->x_inc || !out->f_inc)
         return -1;
-    if (cfg->cost >= SAO_ROT_RASTRIGIN && !cfg->Q) return -1;
+    if (!cost_ok(cfg)) return -1;
     const int periodic = cfg->exchange_every > 1;
     if ((cfg->independent || periodic) && cfg->level0 != 0) return -1;
     const int n = cfg->n;
@@ -538,7 +707,7 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
 int sao_level_chains(const sao_cfg* cfg, int32_t level, const double* x_start, int64_t c0,
                      int64_t c1, double* F_out, double* X_out, uint32_t* bits_out,
                      int64_t* acc_out) {
-    if (!cfg || c1 < c0 || (level > 0 && !x_start)) return -1;
+    if (!cfg || c1 < c0 || (level > 0 && !x_start) || !cost_ok(cfg)) return -1;
     const int n = cfg->n;
     const int words = (cfg->L + 31) / 32;
 #ifdef _OPENMP
@@ -569,6 +738,7 @@ int sao_level_chains(const sao_cfg* cfg, int32_t level, const double* x_start, i
 int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
             double* x, int32_t max_iter, double tol, double armijo_c, int32_t max_halvings,
             double* f_out, int32_t* iters_out) {
+    if (!has_local(cost)) return -1; /* gradients are written for Sec. 4.1's and the rotated costs only */
     double* g = (double*)malloc(sizeof(double) * (size_t)n);
     double* xn = (double*)malloc(sizeof(double) * (size_t)n);
     double* yw = (double*)malloc(sizeof(double) * (size_t)n);
@@ -627,9 +797,9 @@ static void nm_clip(int n, const double* lo, const double* hi, double* x) {
     for (int i = 0; i < n; ++i) x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
 }
 
-int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, double* x,
-                    double step_frac, int32_t max_iter, double ftol, double xtol, double* f_out,
-                    int32_t* iters_out) {
+int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
+                    const double* table, int32_t rows, double* x, double step_frac, int32_t max_iter, double ftol,
+                    double xtol, double* f_out, int32_t* iters_out) {
     const int m = n + 1;
     double* V = (double*)malloc(sizeof(double) * (size_t)m * n);
     double* F = (double*)malloc(sizeof(double) * (size_t)m);
@@ -651,7 +821,7 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
             v[k] = (v[k] + d <= hi[k]) ? v[k] + d : v[k] - d;
             nm_clip(n, lo, hi, v);
         }
-        F[j] = sao_cost_ws(cost, n, v, Q, yw);
+        F[j] = sao_cost_tab(cost, n, v, Q, table, rows, yw);
     }
     int it = 0;
     for (; it < max_iter; ++it) {
@@ -681,14 +851,14 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
         const double* vh = V + (size_t)h * n;
         for (int i = 0; i < n; ++i) xr[i] = xc[i] + (xc[i] - vh[i]);
         nm_clip(n, lo, hi, xr);
-        const double fr = sao_cost_ws(cost, n, xr, Q, yw);
+        const double fr = sao_cost_tab(cost, n, xr, Q, table, rows, yw);
         int accept = 0;
         double fa = fr;
         const double* xa = xr;
         if (fr < F[l]) {
             for (int i = 0; i < n; ++i) xt[i] = xc[i] + 2.0 * (xr[i] - xc[i]);
             nm_clip(n, lo, hi, xt);
-            const double fe = sao_cost_ws(cost, n, xt, Q, yw);
+            const double fe = sao_cost_tab(cost, n, xt, Q, table, rows, yw);
             accept = 1;
             if (fe < fr) { fa = fe; xa = xt; }
         } else if (fr < F[sw]) {
@@ -696,12 +866,12 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
         } else if (fr < F[h]) {
             for (int i = 0; i < n; ++i) xt[i] = xc[i] + 0.5 * (xr[i] - xc[i]);
             nm_clip(n, lo, hi, xt);
-            const double fo = sao_cost_ws(cost, n, xt, Q, yw);
+            const double fo = sao_cost_tab(cost, n, xt, Q, table, rows, yw);
             if (fo <= fr) { accept = 1; fa = fo; xa = xt; }
         } else {
             for (int i = 0; i < n; ++i) xt[i] = xc[i] - 0.5 * (xc[i] - vh[i]);
             nm_clip(n, lo, hi, xt);
-            const double fi = sao_cost_ws(cost, n, xt, Q, yw);
+            const double fi = sao_cost_tab(cost, n, xt, Q, table, rows, yw);
             if (fi < F[h]) { accept = 1; fa = fi; xa = xt; }
         }
         if (accept) {
@@ -714,7 +884,7 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
                 double* v = V + (size_t)j * n;
                 for (int i = 0; i < n; ++i) v[i] = vl[i] + 0.5 * (v[i] - vl[i]);
                 nm_clip(n, lo, hi, v);
-                F[j] = sao_cost_ws(cost, n, v, Q, yw);
+                F[j] = sao_cost_tab(cost, n, v, Q, table, rows, yw);
             }
         }
     }

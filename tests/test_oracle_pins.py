@@ -62,11 +62,15 @@ def test_schwefel_brute_force_grid_n2():
     _, fs, _, _ = _schwefel_star()
     t = np.arange(-500.0, 500.0 + 1e-9, 0.05)
     h = t * np.sin(np.sqrt(np.abs(t)))
-    F = -(h[:, None] + h[None, :]) / 2.0
-    i, j = np.unravel_index(np.argmin(F), F.shape)
+    best, i, j = np.inf, -1, -1
+    for r0 in range(0, t.size, 500):  # the 20001 x 20001 grid in slabs of 500 rows
+        F = -(h[r0:r0 + 500, None] + h[None, :]) / 2.0
+        k = int(np.argmin(F))
+        if F.flat[k] < best:
+            best, i, j = float(F.flat[k]), r0 + k // t.size, k % t.size
     assert abs(t[i] - 420.97) < 0.05 and abs(t[j] - 420.97) < 0.05
-    assert fs <= F[i, j] <= fs + 1e-4
-    assert abs(oracle.cost("schwefel", [t[i], t[j]]) - F[i, j]) < 1e-9
+    assert fs <= best <= fs + 1e-4
+    assert abs(oracle.cost("schwefel", [t[i], t[j]]) - best) < 1e-9
 
 
 def test_other_costs_special_values():
