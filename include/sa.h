@@ -45,14 +45,38 @@ typedef enum {
  * f = -(1/n) sum x_i sin sqrt|x_i|); Ackley, Rastrigin and Rosenbrock are the
  * Appendix tests 1, 13 and 14 (Rosenbrock in its standard x_{i+1} - x_i^2
  * form).  The rotated variants evaluate the same formula at y = Q x for an
- * orthogonal Q (an extension: the paper has no rotated costs). */
+ * orthogonal Q (an extension: the paper has no rotated costs).  SA_BRANIN ..
+ * SA_FOXHOLES are the Appendix's Tests 2-12 and 15-19, evaluated in full in
+ * FP64 at every step (SA_FP64 only; no local difference, no gradient).  The
+ * cosine mixture (Test 3) is sum x_i^2 - 0.1 sum cos(5 pi x_i) and Griewank
+ * (Test 8) 1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt i): their standard forms,
+ * which the printed minima fit.  Branin, Dekkers-Aarts, Easom, Goldstein-Price,
+ * Himmelblau and the six-hump camel need n = 2; modified Langerman, Shekel and
+ * the modified Shekel foxholes (Tests 11, 18, 19) take their A and c as a
+ * table (sa_problem.table). */
 typedef enum {
     SA_SCHWEFEL = 0,
     SA_RASTRIGIN = 1,
     SA_ACKLEY = 2,
     SA_ROSENBROCK = 3,
     SA_ROT_RASTRIGIN = 4,
-    SA_ROT_SCHWEFEL = 5
+    SA_ROT_SCHWEFEL = 5,
+    SA_BRANIN = 6,          /* Test 2 */
+    SA_COSINE_MIXTURE = 7,  /* Test 3 */
+    SA_DEKKERS_AARTS = 8,   /* Test 4 */
+    SA_EASOM = 9,           /* Test 5 */
+    SA_EXPONENTIAL = 10,    /* Test 6: -exp(-sum x_i^2 / 2) */
+    SA_GOLDSTEIN_PRICE = 11, /* Test 7 */
+    SA_GRIEWANK = 12,       /* Test 8 */
+    SA_HIMMELBLAU = 13,     /* Test 9 */
+    SA_LEVY_MONTALVO = 14,  /* Test 10 */
+    SA_LANGERMAN = 15,      /* Test 11: -sum_i c_i exp(-D_i / pi) cos(pi D_i), D_i = |x - a_i|^2 */
+    SA_MICHALEWICZ = 16,    /* Test 12, m = 10 */
+    SA_SALOMON = 17,        /* Test 15 */
+    SA_SIX_HUMP_CAMEL = 18, /* Test 16 */
+    SA_SHUBERT = 19,        /* Test 17 */
+    SA_SHEKEL = 20,         /* Test 18: -sum_i 1 / (D_i + c_i) */
+    SA_FOXHOLES = 21        /* Test 19: the same sum over the foxholes table */
 } sa_cost;
 
 enum { SA_REFLECT = 0, SA_CLIP = 1 };                 /* box handling of a move */
@@ -60,8 +84,11 @@ enum { SA_FP64 = 0, SA_FP32 = 1, SA_MIXED_BF16 = 2 }; /* arithmetic of the sweep
 enum { SA_POLISH_PGD = 0, SA_POLISH_NELDER_MEAD = 1 };  /* local minimiser of the hybrid SA */
 
 typedef struct {
-    int32_t cost;    /* sa_cost */
-    const double* Q; /* host, n x n row-major, orthogonal; NULL unless rotated */
+    int32_t cost;        /* sa_cost */
+    const double* Q;     /* host, n x n row-major, orthogonal; NULL unless rotated */
+    const double* table; /* host, table_rows x (n + 1): row i = (a_i1 .. a_in, c_i); NULL unless
+                            SA_LANGERMAN, SA_SHEKEL or SA_FOXHOLES */
+    int32_t table_rows;  /* 1 .. 4096 for those costs, else 0 */
 } sa_problem;
 
 typedef struct {
@@ -338,20 +365,23 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
  * xtol (u_i - l_i) of the best in every coordinate i, or after max_iter
  * iterations.  FP64.  Writes the best vertices to x_out (host [k*n]), their
  * values to f_out (host [k]) and the iteration counts to iters_out (host [k],
- * may be NULL).  Rotated costs take Q (host, n x n row-major); separable costs
- * need Q == NULL.  Device workspace ((n+1) n doubles per start: the simplex)
+ * may be NULL).  Rotated costs take Q (host, n x n row-major), the others
+ * Q == NULL; the table costs take table (host, table_rows x (n + 1), as in
+ * sa_problem), the others table == NULL.  Every cost of sa_cost is accepted.  Device workspace ((n+1) n doubles per start: the simplex)
  * is allocated stream-ordered; synchronises `stream`.  Above 64 coordinates
  * the centroid comes from a running vertex sum (summed afresh after a shrink
  * and every n+1 iterations), so results differ from a sequential
  * implementation by rounding there as well as in f.
  * Errors: SA_EINVAL on n < 1 or n > 4096, k not in [1, 1024], a bad box,
  * step_frac not in (0, 1], max_iter < 0, ftol or xtol negative or NaN, a NULL
- * array, Q missing for a rotated cost (or given for a separable one), a
- * non-finite Q entry, or a workspace above 4 GiB; SA_ENOMEM; SA_ECUDA.
+ * array, Q or the table missing where the cost needs it (or given where it
+ * does not), a non-finite Q or table entry, n != 2 for a two-variable test, or
+ * a workspace above 4 GiB; SA_ENOMEM; SA_ECUDA.
  */
-sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
-                         const double* x0, double step_frac, int32_t max_iter, double ftol, double xtol,
-                         double* x_out, double* f_out, int32_t* iters_out, void* stream);
+sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
+                         const double* table, int32_t table_rows, int32_t k, const double* x0, double step_frac,
+                         int32_t max_iter, double ftol, double xtol, double* x_out, double* f_out,
+                         int32_t* iters_out, void* stream);
 
 /*
  * Kernel-level entry point: tensor-core GEMM D = A . B^T with A [M x K] and

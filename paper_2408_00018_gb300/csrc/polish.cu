@@ -16,6 +16,7 @@
 #include <cstdint>
 #include <math_constants.h>
 
+#include "appendix.cuh"
 #include "sa_device.cuh"
 #include "sa_internal.h"
 
@@ -222,8 +223,86 @@ __device__ double block_sum(double v, double* red) {
     return s;
 }
 
+// Product over the block (every thread gets it), like block_sum.
+__device__ double block_prod(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(kFull, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double p = 1.0;
+    for (int w = 0; w < nw; ++w) p *= red[w];
+    __syncthreads();
+    return p;
+}
+
+struct VecX {
+    const double* v;
+    __device__ __forceinline__ double operator()(int i) const { return v[i]; }
+};
+
+// The Appendix's other tests at x (shared memory): the n-dimensional sums and
+// products are reduced over the block; the two-variable and table costs are
+// evaluated by thread 0 and shared through block_sum (the others add zeros).
+__device__ double bcost_appendix(int cost, int n, const double* x, const double* __restrict__ table, int rows,
+                                 double* red) {
+    constexpr double pi = CUDART_PI;
+    const int t = threadIdx.x, B = blockDim.x;
+    if (cost == kCosineMixture || cost == kExponential || cost == kSalomon || cost == kMichalewicz) {
+        double a = 0.0, b = 0.0;
+        for (int i = t; i < n; i += B) {
+            const double v = x[i];
+            if (cost == kMichalewicz) {
+                a += sin(v) * pow(sin((double)(i + 1) * v * v / pi), 20.0);
+            } else {
+                a += v * v;
+                if (cost == kCosineMixture) b += cos(5.0 * pi * v);
+            }
+        }
+        a = block_sum(a, red);
+        if (cost == kCosineMixture) return a - 0.1 * block_sum(b, red);
+        if (cost == kExponential) return -exp(-0.5 * a);
+        if (cost == kMichalewicz) return -a;
+        const double r = sqrt(a);
+        return 1.0 - cos(2.0 * pi * r) + 0.1 * r;
+    }
+    if (cost == kGriewank || cost == kShubert) {
+        double q = 0.0, p = 1.0;
+        for (int i = t; i < n; i += B) {
+            const double v = x[i];
+            if (cost == kGriewank) {
+                q += v * v;
+                p *= cos(v / sqrt((double)(i + 1)));
+            } else {
+                double s = 0.0;
+                for (int j = 1; j <= 5; ++j) s += (double)j * cos((double)(j + 1) * v + (double)j);
+                p *= s;
+            }
+        }
+        p = block_prod(p, red);
+        if (cost == kShubert) return p;
+        return 1.0 + block_sum(q, red) / 4000.0 - p;
+    }
+    if (cost == kLevyMontalvo) {
+        double s = 0.0;
+        for (int i = t; i + 1 < n; i += B) {
+            const double yi = 1.0 + (x[i] + 1.0) / 4.0, yn = 1.0 + (x[i + 1] + 1.0) / 4.0;
+            const double sn = sin(pi * yn);
+            s += (yi - 1.0) * (yi - 1.0) * (1.0 + 10.0 * sn * sn);
+        }
+        s = block_sum(s, red);
+        const double y0 = 1.0 + (x[0] + 1.0) / 4.0, yl = 1.0 + (x[n - 1] + 1.0) / 4.0;
+        const double s0 = sin(pi * y0);
+        return pi / (double)n * (10.0 * s0 * s0 + s + (yl - 1.0) * (yl - 1.0));
+    }
+    const double v = t == 0 ? appendix_cost_any(cost, n, VecX{x}, table, rows) : 0.0;
+    return block_sum(v, red);
+}
+
 // f at x (shared memory, visible to the block); every thread gets the value.
-__device__ double bcost(int cost, int n, const double* x, const double* __restrict__ QT, double* red) {
+__device__ double bcost(int cost, int n, const double* x, const double* __restrict__ QT, const double* __restrict__ table,
+                        int rows, double* red) {
+    if (cost >= kBranin) return bcost_appendix(cost, n, x, table, rows, red);
     double s1 = 0.0, s2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         if (cost == kRotRastrigin || cost == kRotSchwefel) {
@@ -277,6 +356,7 @@ __device__ int nm_pick(const double* F, int m, bool best, int skip, double* fr, 
 
 __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double* __restrict__ lo,
                                                   const double* __restrict__ hi, const double* __restrict__ QT,
+                                                  const double* __restrict__ table, int rows,
                                                   const double* __restrict__ x0, double* __restrict__ x_out,
                                                   double* __restrict__ f_out, int* __restrict__ it_out,
                                                   double step_frac, int max_iter, double ftol, double xtol,
@@ -307,7 +387,7 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
     for (int j = 0; j < m; ++j) {
         for (int i = t; i < n; i += B) xt[i] = V[(size_t)j * n + i];
         __syncthreads();
-        const double f = bcost(cost, n, xt, QT, red);
+        const double f = bcost(cost, n, xt, QT, table, rows, red);
         if (t == 0) F[j] = f;
     }
     auto resum = [&]() {
@@ -348,13 +428,13 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
             xr[i] = clipd(xc[i] + (xc[i] - vh[i]), lo[i], hi[i]);
         }
         __syncthreads();
-        const double fr = bcost(cost, n, xr, QT, red);
+        const double fr = bcost(cost, n, xr, QT, table, rows, red);
         bool accept = false, trial = false;
         double fa = fr;
         if (fr < fl) {  // expansion
             for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + 2.0 * (xr[i] - xc[i]), lo[i], hi[i]);
             __syncthreads();
-            const double fe = bcost(cost, n, xt, QT, red);
+            const double fe = bcost(cost, n, xt, QT, table, rows, red);
             accept = true;
             if (fe < fr) { fa = fe; trial = true; }
         } else if (fr < fs) {
@@ -362,12 +442,12 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
         } else if (fr < fh) {  // outside contraction
             for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + 0.5 * (xr[i] - xc[i]), lo[i], hi[i]);
             __syncthreads();
-            const double fo = bcost(cost, n, xt, QT, red);
+            const double fo = bcost(cost, n, xt, QT, table, rows, red);
             if (fo <= fr) { accept = true; fa = fo; trial = true; }
         } else {  // inside contraction
             for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] - 0.5 * (xc[i] - vh[i]), lo[i], hi[i]);
             __syncthreads();
-            const double fi = bcost(cost, n, xt, QT, red);
+            const double fi = bcost(cost, n, xt, QT, table, rows, red);
             if (fi < fh) { accept = true; fa = fi; trial = true; }
         }
         if (accept) {
@@ -391,7 +471,7 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
                     xt[i] = a;
                 }
                 __syncthreads();
-                const double f = bcost(cost, n, xt, QT, red);
+                const double f = bcost(cost, n, xt, QT, table, rows, red);
                 if (t == 0) F[j] = f;
             }
             resum();
@@ -485,9 +565,9 @@ size_t nm_ws_doubles(int n) { return (size_t)(n + 1) * (size_t)n; }
 
 int nm_max_n() { return kNmMaxN; }
 
-cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, int k, const double* x0,
-                      double* x_out, double* f_out, int* it_out, double step_frac, int max_iter, double ftol,
-                      double xtol, double* ws, cudaStream_t s) {
+cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, const double* table,
+                      int table_rows, int k, const double* x0, double* x_out, double* f_out, int* it_out,
+                      double step_frac, int max_iter, double ftol, double xtol, double* ws, cudaStream_t s) {
     if (n < 1 || n > kNmMaxN) return cudaErrorInvalidValue;
     const int block = std::min(1024, std::max(32, (n + 31) / 32 * 32));
     const size_t smem = ((size_t)(n + 1) + 4 * (size_t)n + 32) * sizeof(double) + 32 * sizeof(int);
@@ -497,8 +577,8 @@ cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const
         if (e != cudaSuccess) return e;
         current = smem;
     }
-    nm_kernel<<<k, block, smem, s>>>(cost, n, lo, hi, QT, x0, x_out, f_out, it_out, step_frac, max_iter, ftol, xtol,
-                                     ws);
+    nm_kernel<<<k, block, smem, s>>>(cost, n, lo, hi, QT, table, table_rows, x0, x_out, f_out, it_out, step_frac,
+                                     max_iter, ftol, xtol, ws);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,8 @@ struct HostProb {
     int32_t cost, n;
     int64_t chains, chain_base, x_base;
     std::vector<double> lo, hi, Q;
+    std::vector<double> table;  // Tests 11, 18, 19: table_rows x (n + 1)
+    int32_t table_rows = 0;
     ProbDev dev;  // with device pointers
 };
 
@@ -52,6 +54,33 @@ constexpr int64_t kDaBufferRows = (int64_t)1 << 20;
 constexpr uint32_t kTagDa = 3u, kTagTrain = 4u;
 
 bool is_rot(int cost) { return cost == SA_ROT_RASTRIGIN || cost == SA_ROT_SCHWEFEL; }
+// The Appendix's Tests 2-12 and 15-19: FP64 full evaluation only.
+bool is_appendix(int cost) { return cost >= SA_BRANIN && cost <= SA_FOXHOLES; }
+bool is_table(int cost) { return cost == SA_LANGERMAN || cost == SA_SHEKEL || cost == SA_FOXHOLES; }
+bool is_2d(int cost) {
+    return cost == SA_BRANIN || cost == SA_DEKKERS_AARTS || cost == SA_EASOM || cost == SA_GOLDSTEIN_PRICE ||
+           cost == SA_HIMMELBLAU || cost == SA_SIX_HUMP_CAMEL;
+}
+constexpr int kMaxTableRows = 4096;
+// A cost's own requirements on n, Q and the table (shared by the solver and sa_nelder_mead).
+bool cost_args_ok(int cost, int n, const double* Q, const double* table, int rows) {
+    if (cost < SA_SCHWEFEL || cost > SA_FOXHOLES || n < 1) return false;
+    if (is_rot(cost) != (Q != nullptr)) return false;
+    if (is_rot(cost) && (int64_t)n * n > ((int64_t)1 << 28)) return false;
+    if (is_2d(cost) && n != 2) return false;
+    if (is_table(cost) != (table != nullptr)) return false;
+    if (is_table(cost)) {
+        if (rows < 1 || rows > kMaxTableRows || (int64_t)rows * (n + 1) > ((int64_t)1 << 24)) return false;
+        for (size_t e = 0; e < (size_t)rows * (size_t)(n + 1); ++e)
+            if (!std::isfinite(table[e])) return false;
+    } else if (rows != 0) {
+        return false;
+    }
+    if (Q)
+        for (size_t e = 0; e < (size_t)n * n; ++e)
+            if (!std::isfinite(Q[e])) return false;
+    return true;
+}
 struct Group {
     int kind = kSweepF32;
     int n_max = 1;
@@ -177,15 +206,14 @@ sa_status check_schedule(const sa_schedule* s) {
 // Checks of one problem shared by sa_create and sa_create_batch.
 sa_status check_problem(const sa_problem& pr, const sa_box& box, int32_t n, int64_t chains, const sa_schedule& sch) {
     if (n < 1 || chains < 1 || chains > 2147483647LL || !box.lo || !box.hi) return SA_EINVAL;
-    if (pr.cost < SA_SCHWEFEL || pr.cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
+    if (!cost_args_ok(pr.cost, n, pr.Q, pr.table, pr.table_rows)) return SA_EINVAL;
     if (sch.surrogate && (!is_rot(pr.cost) || n > 4096)) return SA_EINVAL;
-    if (is_rot(pr.cost)) {
-        // rotated costs run the FP32 rank-1 sweep
-        if (!pr.Q || sch.precision != SA_FP32) return SA_EINVAL;
-        if ((int64_t)n * n > ((int64_t)1 << 28)) return SA_EINVAL;
-        for (size_t k = 0; k < (size_t)n * n; ++k)
-            if (!std::isfinite(pr.Q[k])) return SA_EINVAL;
-    }
+    // rotated costs run the FP32 rank-1 sweep; the Appendix's other tests the FP64 sweep
+    if (is_rot(pr.cost) && sch.precision != SA_FP32) return SA_EINVAL;
+    if (is_appendix(pr.cost) && sch.precision != SA_FP64) return SA_EINVAL;
+    // no gradient is written for the Appendix's other tests: they polish with Nelder-Mead
+    if (is_appendix(pr.cost) && sch.polish_k > 0 && sch.polish_method == SA_POLISH_PGD) return SA_EINVAL;
+    if (sch.polish_k > 0 && sch.polish_method == SA_POLISH_NELDER_MEAD && n > nm_max_n()) return SA_EINVAL;
     for (int k = 0; k < n; ++k)
         if (!std::isfinite(box.lo[k]) || !std::isfinite(box.hi[k]) || box.lo[k] > box.hi[k]) return SA_EINVAL;
     return SA_OK;
@@ -378,7 +406,8 @@ sa_status run_polish(sa_handle* h) {
             launch_gather(h->d_X32, h->d_X64, hp.x_base, hp.chains, hp.n, h->d_topk, k, h->d_px0, h->stream) !=
                 cudaSuccess ||
             (h->sch.polish_method == SA_POLISH_NELDER_MEAD
-                 ? launch_nm(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.qt64, k, h->d_px0, h->d_px, h->d_pf, h->d_pit,
+                 ? launch_nm(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.qt64, hp.dev.table, hp.dev.table_rows, k,
+                             h->d_px0, h->d_px, h->d_pf, h->d_pit,
                              h->nm_step, 200 * (hp.n + 1), 1e-12, 1e-10, h->d_nmws, h->stream)
                  : launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.q64, k, h->d_px0, h->d_px, h->d_pf,
                               h->d_pit, 1000, 1e-10, h->stream)) != cudaSuccess ||
@@ -518,6 +547,10 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         hp.lo.assign(boxes[p].lo, boxes[p].lo + hp.n);
         hp.hi.assign(boxes[p].hi, boxes[p].hi + hp.n);
         if (is_rot(hp.cost)) hp.Q.assign(problems[p].Q, problems[p].Q + (size_t)hp.n * hp.n);
+        if (is_table(hp.cost)) {
+            hp.table_rows = problems[p].table_rows;
+            hp.table.assign(problems[p].table, problems[p].table + (size_t)hp.table_rows * (hp.n + 1));
+        }
         if (hp.n > n_max) n_max = hp.n;
     }
     h->words = (h->L + 31) / 32;
@@ -643,6 +676,12 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         d.part_val = pval; d.part_idx = pidx; d.log_argmin = la; d.log_f = lf; d.log_finc = lfi; d.log_t = lt;
         d.accepts = acc;
         if (is_rot(hp.cost) && (st = setup_rot(h, hp, d))) return st;
+        if (is_table(hp.cost)) {
+            double* dt;
+            if ((st = dalloc(h, &dt, hp.table.size())) || (st = h2d(h, dt, hp.table.data(), hp.table.size()))) return st;
+            d.table = dt;
+            d.table_rows = hp.table_rows;
+        }
         hp.dev = d;
         pd[p] = d;
         std::vector<double> sc(kNumScalars, 0.0);
@@ -734,6 +773,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     fp = fnv(fp, &h->L, sizeof(h->L));
     for (auto& hp : h->probs) {
         fp = fnv(fp, hp.Q.data(), hp.Q.size() * sizeof(double));
+        fp = fnv(fp, hp.table.data(), hp.table.size() * sizeof(double));
         fp = fnv(fp, &hp.cost, sizeof(hp.cost));
         fp = fnv(fp, &hp.n, sizeof(hp.n));
         fp = fnv(fp, &hp.chains, sizeof(hp.chains));
@@ -936,15 +976,15 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
     return st;
 }
 
-sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q, int32_t k,
-                         const double* x0, double step_frac, int32_t max_iter, double ftol, double xtol,
-                         double* x_out, double* f_out, int32_t* iters_out, void* stream) {
+sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
+                         const double* table, int32_t table_rows, int32_t k, const double* x0, double step_frac,
+                         int32_t max_iter, double ftol, double xtol, double* x_out, double* f_out,
+                         int32_t* iters_out, void* stream) {
     if (n < 1 || k < 1 || k > 1024 || !lo || !hi || !x0 || !x_out || !f_out || max_iter < 0 || !(ftol >= 0.0) ||
         !(xtol >= 0.0) || !(step_frac > 0.0 && step_frac <= 1.0))
         return SA_EINVAL;
-    if (cost < SA_SCHWEFEL || cost > SA_ROT_SCHWEFEL) return SA_EINVAL;
+    if (!cost_args_ok(cost, n, Q, table, table_rows) || n > nm_max_n()) return SA_EINVAL;
     const bool rot = is_rot(cost);
-    if (rot != (Q != nullptr) || n > nm_max_n()) return SA_EINVAL;
     const size_t ws = (size_t)k * nm_ws_doubles(n);
     if (ws * sizeof(double) > ((size_t)1 << 32)) return SA_EINVAL;
     for (int d = 0; d < n; ++d)
@@ -953,14 +993,12 @@ sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double
     if (rot) {
         qt.resize((size_t)n * n);
         for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) {
-                const double q = Q[(size_t)i * n + j];
-                if (!std::isfinite(q)) return SA_EINVAL;
-                qt[(size_t)j * n + i] = q;
-            }
+            for (int j = 0; j < n; ++j) qt[(size_t)j * n + i] = Q[(size_t)i * n + j];
     }
+    const size_t tn = table ? (size_t)table_rows * (size_t)(n + 1) : 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *dlo = nullptr, *dhi = nullptr, *dx0 = nullptr, *dx = nullptr, *df = nullptr, *dq = nullptr, *dws = nullptr;
+    double* dtab = nullptr;
     int* dit = nullptr;
     const size_t kn = (size_t)k * n;
     sa_status st = SA_OK;
@@ -968,20 +1006,23 @@ sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double
         cudaMallocAsync(&dlo, n * sizeof(double), s) || cudaMallocAsync(&dhi, n * sizeof(double), s) ||
         cudaMallocAsync(&dx0, kn * sizeof(double), s) || cudaMallocAsync(&dx, kn * sizeof(double), s) ||
         cudaMallocAsync(&df, k * sizeof(double), s) || cudaMallocAsync(&dit, k * sizeof(int), s) ||
-        cudaMallocAsync(&dws, ws * sizeof(double), s))
+        cudaMallocAsync(&dws, ws * sizeof(double), s) || (tn && cudaMallocAsync(&dtab, tn * sizeof(double), s)))
         st = SA_ENOMEM;
     if (st == SA_OK &&
         ((rot && cudaMemcpyAsync(dq, qt.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, s)) ||
          cudaMemcpyAsync(dlo, lo, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
          cudaMemcpyAsync(dhi, hi, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
          cudaMemcpyAsync(dx0, x0, kn * sizeof(double), cudaMemcpyHostToDevice, s) ||
-         launch_nm(cost, n, dlo, dhi, dq, k, dx0, dx, df, dit, step_frac, max_iter, ftol, xtol, dws, s) ||
+         (tn && cudaMemcpyAsync(dtab, table, tn * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+         launch_nm(cost, n, dlo, dhi, dq, dtab, table_rows, k, dx0, dx, df, dit, step_frac, max_iter, ftol, xtol, dws,
+                   s) ||
          cudaMemcpyAsync(x_out, dx, kn * sizeof(double), cudaMemcpyDeviceToHost, s) ||
          cudaMemcpyAsync(f_out, df, k * sizeof(double), cudaMemcpyDeviceToHost, s) ||
          (iters_out && cudaMemcpyAsync(iters_out, dit, k * sizeof(int), cudaMemcpyDeviceToHost, s)) ||
          cudaStreamSynchronize(s)))
         st = SA_ECUDA;
-    for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit, (void*)dq, (void*)dws})
+    for (void* p : {(void*)dlo, (void*)dhi, (void*)dx0, (void*)dx, (void*)df, (void*)dit, (void*)dq, (void*)dws,
+                    (void*)dtab})
         if (p) cudaFreeAsync(p, s);
     cudaGetLastError();
     return st;

@@ -11,7 +11,13 @@
 
 namespace sa {
 
-enum CostId : int32_t { kSchwefel = 0, kRastrigin = 1, kAckley = 2, kRosenbrock = 3, kRotRastrigin = 4, kRotSchwefel = 5 };
+enum CostId : int32_t {
+    kSchwefel = 0, kRastrigin = 1, kAckley = 2, kRosenbrock = 3, kRotRastrigin = 4, kRotSchwefel = 5,
+    // the rest of the Appendix's tests (FP64, full evaluation)
+    kBranin = 6, kCosineMixture = 7, kDekkersAarts = 8, kEasom = 9, kExponential = 10, kGoldsteinPrice = 11,
+    kGriewank = 12, kHimmelblau = 13, kLevyMontalvo = 14, kLangerman = 15, kMichalewicz = 16, kSalomon = 17,
+    kSixHumpCamel = 18, kShubert = 19, kShekel = 20, kFoxholes = 21
+};
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll

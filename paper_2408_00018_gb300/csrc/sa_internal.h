@@ -53,6 +53,9 @@ struct ProbDev {
     double* log_finc;     // [levels]
     long long* log_t;     // [levels] device clock (ns) at the end of the level
     unsigned long long* accepts;  // running count of accepted moves
+    // Tests 11, 18, 19: rows (a_i1 .. a_in, c_i) (NULL otherwise)
+    const double* table;  // [table_rows][n + 1]
+    int32_t table_rows;
     // rotated costs f(x) = F(Q x) (NULL otherwise)
     const double* q64;    // [n][n] Q row-major (FP64)
     const double* qt64;   // [n][n] Q transposed: qt64[d * n + i] = Q[i][d]
@@ -135,9 +138,9 @@ cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, cons
 // costs take QT = Q^T (row-major, i.e. Q column-major); n <= nm_max_n().
 size_t nm_ws_doubles(int n);
 int nm_max_n();
-cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, int k, const double* x0,
-                      double* x_out, double* f_out, int* it_out, double step_frac, int max_iter, double ftol,
-                      double xtol, double* ws, cudaStream_t s);
+cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, const double* table,
+                      int table_rows, int k, const double* x0, double* x_out, double* f_out, int* it_out,
+                      double step_frac, int max_iter, double ftol, double xtol, double* ws, cudaStream_t s);
 cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStream_t s);
 cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
                                  int* status, cudaStream_t s);

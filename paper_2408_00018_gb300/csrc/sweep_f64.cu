@@ -2,13 +2,15 @@
 //
 // The kernel of Listing 4 in double precision: one thread per chain, state in
 // shared memory x[d][lane], and -- as in the paper -- f(x1) recomputed in full
-// at every step, summed in index order.  This translation unit is compiled
+// at every step, summed in index order.  It serves every cost, including the
+// Appendix's Tests 2-12 and 15-19 (appendix.cuh).  This translation unit is compiled
 // with -fmad=false: every product and sum is rounded as written, so the only
 // differences from a correctly rounded evaluation are the last-ulp errors of
 // the math library's log, cos, sin and exp.
 #include <cmath>
 #include <math_constants.h>
 
+#include "appendix.cuh"
 #include "sa_device.cuh"
 #include "sa_internal.h"
 
@@ -17,10 +19,20 @@ namespace {
 
 constexpr int kMaxBlock = 256;
 
+// Coordinate i of the chain's column, with coordinate d replaced by xd (d < 0: none).
+struct ColX {
+    const double* col;
+    int B, d;
+    double xd;
+    __device__ __forceinline__ double operator()(int i) const { return i == d ? xd : col[(size_t)i * B]; }
+};
+
 // f at the chain's column, with coordinate d replaced by xd_new (d < 0: none).
 template <int COST>
-__device__ __forceinline__ double full_cost(const double* xcol, int B, int n, int d, double xd_new) {
-    if (COST == kSchwefel) {
+__device__ __forceinline__ double full_cost(const ProbDev& P, const double* xcol, int B, int n, int d, double xd_new) {
+    if (COST >= kBranin) {
+        return appendix_cost<COST>(n, ColX{xcol, B, d, xd_new}, P.table, P.table_rows);
+    } else if (COST == kSchwefel) {
         double s = 0.0;
         for (int i = 0; i < n; ++i) s = s + h64_schwefel(i == d ? xd_new : xcol[i * B]);
         return -(s / (double)n);
@@ -76,7 +88,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     uint32_t nacc = 0;
     if (active) {
-        double F = full_cost<COST>(xcol, B, n, -1, 0.0);
+        double F = full_cost<COST>(P, xcol, B, n, -1, 0.0);
         uint32_t bw = 0;
         for (int s = 0; s < A.L; ++s) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
@@ -93,7 +105,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             }
             if (xp < lo) xp = lo;
             if (xp > hi) xp = hi;
-            const double Fp = full_cost<COST>(xcol, B, n, d, xp);
+            const double Fp = full_cost<COST>(P, xcol, B, n, d, xp);
             const double dF = Fp - F;
             const bool acc = (dF <= 0.0) || (u3 < exp(-dF / T));
             if (acc) {
@@ -135,6 +147,22 @@ __global__ void __launch_bounds__(kMaxBlock) sweep_f64_kernel(SweepArgs A) {
     case kRastrigin: sweep_tile<kRastrigin>(A, P, it, level, xs, red); break;
     case kAckley: sweep_tile<kAckley>(A, P, it, level, xs, red); break;
     case kRosenbrock: sweep_tile<kRosenbrock>(A, P, it, level, xs, red); break;
+    case kBranin: sweep_tile<kBranin>(A, P, it, level, xs, red); break;
+    case kCosineMixture: sweep_tile<kCosineMixture>(A, P, it, level, xs, red); break;
+    case kDekkersAarts: sweep_tile<kDekkersAarts>(A, P, it, level, xs, red); break;
+    case kEasom: sweep_tile<kEasom>(A, P, it, level, xs, red); break;
+    case kExponential: sweep_tile<kExponential>(A, P, it, level, xs, red); break;
+    case kGoldsteinPrice: sweep_tile<kGoldsteinPrice>(A, P, it, level, xs, red); break;
+    case kGriewank: sweep_tile<kGriewank>(A, P, it, level, xs, red); break;
+    case kHimmelblau: sweep_tile<kHimmelblau>(A, P, it, level, xs, red); break;
+    case kLevyMontalvo: sweep_tile<kLevyMontalvo>(A, P, it, level, xs, red); break;
+    case kLangerman: sweep_tile<kLangerman>(A, P, it, level, xs, red); break;
+    case kMichalewicz: sweep_tile<kMichalewicz>(A, P, it, level, xs, red); break;
+    case kSalomon: sweep_tile<kSalomon>(A, P, it, level, xs, red); break;
+    case kSixHumpCamel: sweep_tile<kSixHumpCamel>(A, P, it, level, xs, red); break;
+    case kShubert: sweep_tile<kShubert>(A, P, it, level, xs, red); break;
+    case kShekel: sweep_tile<kShekel>(A, P, it, level, xs, red); break;
+    case kFoxholes: sweep_tile<kFoxholes>(A, P, it, level, xs, red); break;
     default: if (threadIdx.x == 0) A.run->status = 1; break;
     }
 }

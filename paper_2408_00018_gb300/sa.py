@@ -17,7 +17,10 @@ import numpy as np
 from . import _build
 
 SA_OK, SA_EINVAL, SA_ENOMEM, SA_ECUDA, SA_ETIMEOUT, SA_ENUMERIC, SA_ESTATE = range(7)
-COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "rot_rastrigin": 4, "rot_schwefel": 5}
+COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "rot_rastrigin": 4, "rot_schwefel": 5,
+         "branin": 6, "cosine_mixture": 7, "dekkers_aarts": 8, "easom": 9, "exponential": 10,
+         "goldstein_price": 11, "griewank": 12, "himmelblau": 13, "levy_montalvo": 14, "langerman": 15,
+         "michalewicz": 16, "salomon": 17, "six_hump_camel": 18, "shubert": 19, "shekel": 20, "foxholes": 21}
 BOUNDARY = {"reflect": 0, "clip": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_bf16": 2}
 POLISH = {"pgd": 0, "nelder_mead": 1}
@@ -30,7 +33,21 @@ class SAError(RuntimeError):
 
 
 class _Problem(ctypes.Structure):
-    _fields_ = [("cost", ctypes.c_int32), ("Q", ctypes.c_void_p)]
+    _fields_ = [("cost", ctypes.c_int32), ("Q", ctypes.c_void_p), ("table", ctypes.c_void_p),
+                ("table_rows", ctypes.c_int32)]
+
+
+def _table(table):
+    """(contiguous FP64 array, rows) of a table of rows (a_i1 .. a_in, c_i), or (None, 0)."""
+    if table is None:
+        return None, 0
+    t = np.ascontiguousarray(np.atleast_2d(np.asarray(table, np.float64)))
+    return t, t.shape[0]
+
+
+def _problem(cost, Qa, tab, rows):
+    return _Problem(COSTS[cost] if isinstance(cost, str) else int(cost), None if Qa is None else Qa.ctypes.data,
+                    None if tab is None else tab.ctypes.data, rows)
 
 
 class _Box(ctypes.Structure):
@@ -77,7 +94,7 @@ SIGNATURES = {
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
     "sa_polish": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _I32, _D, _V, _V, _V, _V]),
-    "sa_nelder_mead": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _D, _I32, _D, _D, _V, _V, _V, _V]),
+    "sa_nelder_mead": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _V, _I32, _I32, _V, _D, _I32, _D, _D, _V, _V, _V, _V]),
     "sa_gemm_bf16": (ctypes.c_int, [_V, _I32, _V, _I32, _V, _I32, _I32, _I32, _I32, _V, _V]),
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
@@ -292,14 +309,17 @@ class Handle:
             pass
 
 
-def create(cost, lo, hi, n, chains, L, schedule: Schedule | None = None, seed: int = 0, Q=None, stream=None) -> Handle:
-    """sa_create: one box-constrained problem (Eq. 1) with `chains` chains of L steps per level."""
+def create(cost, lo, hi, n, chains, L, schedule: Schedule | None = None, seed: int = 0, Q=None, stream=None,
+           table=None) -> Handle:
+    """sa_create: one box-constrained problem (Eq. 1) with `chains` chains of L steps per level.
+    Rotated costs take Q (n x n); Tests 11, 18 and 19 take table (rows of (a_i1 .. a_in, c_i))."""
     lib = load()
     schedule = schedule or Schedule()
     lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
     hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (n,)))
     Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
-    prob = _Problem(COSTS[cost] if isinstance(cost, str) else int(cost), None if Qa is None else Qa.ctypes.data)
+    tab, rows = _table(table)
+    prob = _problem(cost, Qa, tab, rows)
     box = _Box(lo.ctypes.data, hi.ctypes.data)
     sch = schedule._c()
     out = ctypes.c_void_p()
@@ -349,15 +369,16 @@ class BatchHandle(Handle):
 
 
 def create_batch(problems, L, schedule: Schedule | None = None, seed: int = 0, stream=None) -> BatchHandle:
-    """sa_create_batch: problems is a list of dicts with cost, n, chains, lo, hi (and Q for rotated costs)."""
+    """sa_create_batch: problems is a list of dicts with cost, n, chains, lo, hi (and Q for rotated costs,
+    table for Tests 11, 18, 19)."""
     lib = load()
     schedule = schedule or Schedule()
     P = len(problems)
     los = [np.ascontiguousarray(np.broadcast_to(np.asarray(p["lo"], np.float64), (p["n"],))) for p in problems]
     his = [np.ascontiguousarray(np.broadcast_to(np.asarray(p["hi"], np.float64), (p["n"],))) for p in problems]
     Qs = [None if p.get("Q") is None else np.ascontiguousarray(p["Q"], dtype=np.float64) for p in problems]
-    probs = (_Problem * P)(*[_Problem(COSTS[p["cost"]] if isinstance(p["cost"], str) else int(p["cost"]),
-                                      None if q is None else q.ctypes.data) for p, q in zip(problems, Qs)])
+    tabs = [_table(p.get("table")) for p in problems]
+    probs = (_Problem * P)(*[_problem(p["cost"], q, t, r) for p, q, (t, r) in zip(problems, Qs, tabs)])
     boxes = (_Box * P)(*[_Box(lo.ctypes.data, hi.ctypes.data) for lo, hi in zip(los, his)])
     ns = np.array([p["n"] for p in problems], np.int32)
     cs = np.array([p["chains"] for p in problems], np.int64)
@@ -389,9 +410,9 @@ def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, Q=None, s
 
 
 def nelder_mead(cost, x0, lo, hi, step_frac: float = 0.05, max_iter: int = 20000, ftol: float = 1e-12,
-                xtol: float = 1e-10, Q=None, stream=None):
+                xtol: float = 1e-10, Q=None, stream=None, table=None):
     """sa_nelder_mead: Nelder-Mead with box clipping from each row of x0 (k x n); returns (x, f, iters).
-    Rotated costs take Q (n x n)."""
+    Rotated costs take Q (n x n); Tests 11, 18 and 19 take table."""
     x0 = np.ascontiguousarray(np.atleast_2d(np.asarray(x0, np.float64)))
     k, n = x0.shape
     lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (n,)))
@@ -401,8 +422,10 @@ def nelder_mead(cost, x0, lo, hi, step_frac: float = 0.05, max_iter: int = 20000
     it = np.zeros(k, np.int32)
     s = _current_stream() if stream is None else ctypes.c_void_p(stream)
     Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    tab, rows = _table(table)
     _check(load().sa_nelder_mead(COSTS[cost] if isinstance(cost, str) else int(cost), n, lo.ctypes.data,
-                                 hi.ctypes.data, None if Qa is None else Qa.ctypes.data, k, x0.ctypes.data, step_frac,
+                                 hi.ctypes.data, None if Qa is None else Qa.ctypes.data,
+                                 None if tab is None else tab.ctypes.data, rows, k, x0.ctypes.data, step_frac,
                                  max_iter, ftol, xtol, x.ctypes.data, f.ctypes.data, it.ctypes.data, s),
            "sa_nelder_mead")
     return x, f, it
