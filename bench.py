@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling runs only)")
     ap.add_argument("--independent", action="store_true",
                     help="asynchronous chains (no exchange between levels; the paper's V1), single-problem workloads")
+    ap.add_argument("--suite", action="store_true",
+                    help="the paper's 41-problem test suite (Tables 8-9) instead: one synchronous run per problem, "
+                         "then the hybrid's Nelder-Mead polish (one JSON line per problem and a summary)")
     ap.add_argument("--hybrid", action="store_true",
                     help="the hybrid SA of Table 10 instead: annealing stopped early, then Nelder-Mead or projected "
                          "gradients from its best final states (one JSON line per function)")
@@ -494,8 +497,64 @@ def run_hybrid(args):
         print(json.dumps(out), flush=True)
 
 
+# The suite's schedule: one for every problem (the paper tunes per function and
+# prints no schedule): T0 = 10, rho = 0.9, 100 levels of L = 500 steps.  Costs
+# with an O(1) energy difference run FP32 with 65536 chains; the Appendix's other
+# tests run the FP64 full evaluation with 16384 chains (4096 above 16 coordinates,
+# where every step evaluates n transcendental terms in FP64).
+SUITE_L, SUITE_K, SUITE_T0, SUITE_RHO, SUITE_POLISH = 500, 100, 10.0, 0.9, 8
+
+
+def run_suite(args):
+    """Tables 8-9 on this GPU: per problem the steps, the device time of the run
+    (CUDA events around sa_run, after an untimed run), |f - f*| and the same after
+    the hybrid's Nelder-Mead polish of the 8 best final states."""
+    import numpy as np
+    import torch
+    from paper_2408_00018_gb300 import _build, inputs, sa
+
+    _build.build()
+    sa.load()
+    base_costs = ("schwefel", "ackley", "rastrigin", "rosenbrock")
+    rows = []
+    for p in inputs.appendix_suite():
+        fp32 = p["cost"] in base_costs
+        C = 65536 if fp32 else (16384 if p["n"] <= 16 else 4096)
+        out = {"metric": "suite: seconds and |f - f*| per problem (Tables 8-9 problems)", "problem": p["name"],
+               "cost": p["cost"], "n": p["n"], "chains": C, "L": SUITE_L, "levels": SUITE_K,
+               "precision": "fp32" if fp32 else "fp64", "steps": C * SUITE_L * SUITE_K, "f_star": p["f_star"]}
+        for polish in (0, SUITE_POLISH):
+            sch = sa.Schedule(T0=SUITE_T0, rho=SUITE_RHO, levels=SUITE_K, precision="fp32" if fp32 else "fp64",
+                              polish_k=polish, polish_method="nelder_mead")
+            with sa.create(p["cost"], p["lo"], p["hi"], p["n"], C, SUITE_L, sch, seed=0, table=p["table"]) as h:
+                h.run()  # untimed: graph capture
+                h.reset()
+                stream = torch.cuda.current_stream()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                h.run()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                _, f, _ = h.best()
+            key = "sa" if polish == 0 else "hybrid"
+            out[key] = {"s": e0.elapsed_time(e1) / 1e3, "f": f, "err": abs(f - p["f_star"])}
+        out["steps_per_s"] = out["steps"] / out["sa"]["s"]
+        rows.append(out)
+        print(json.dumps(out), flush=True)
+    tol = lambda r, k: r[k]["err"] <= 1e-4 * max(1.0, abs(r["f_star"]))  # noqa: E731
+    summary = {"metric": "suite summary", "problems": len(rows),
+               "sa_seconds": sum(r["sa"]["s"] for r in rows), "hybrid_seconds": sum(r["hybrid"]["s"] for r in rows),
+               "steps": sum(r["steps"] for r in rows),
+               "sa_within_1e-4": sum(tol(r, "sa") for r in rows), "hybrid_within_1e-4": sum(tol(r, "hybrid") for r in rows)}
+    print(json.dumps(summary), flush=True)
+
+
 def main():
     args = parse()
+    if args.suite:
+        run_suite(args)
+        return
     if args.hybrid:
         run_hybrid(args)
         return

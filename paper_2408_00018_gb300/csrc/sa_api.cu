@@ -17,7 +17,8 @@
 
 namespace sa {
 size_t sweep_f32_smem_bytes(int n, int block);
-size_t sweep_f64_smem_bytes(int n, int block);
+size_t sweep_f64_smem_bytes(int n, int block, bool keeps_terms);
+bool sweep_f64_keeps_terms(int cost);
 cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                                int64_t count, uint32_t* out, cudaStream_t s);
 int64_t argmin_num_parts(int64_t count);
@@ -84,6 +85,7 @@ bool cost_args_ok(int cost, int n, const double* Q, const double* table, int row
 struct Group {
     int kind = kSweepF32;
     int n_max = 1;
+    bool f64_terms = false;  // FP64 group: a problem keeps per-coordinate factors (twice the state)
     int block = 32;        // threads per block
     size_t smem = 0;       // dynamic shared memory per block
     std::vector<int> probs;
@@ -333,7 +335,7 @@ sa_status set_group_items(sa_handle* h, Group& g) {
 size_t group_smem(const Group& g) {
     if (g.kind == kSweepF32Warp) return sweep_f32w_smem_bytes(g.n_max);
     if (g.kind == kSweepRot) return sweep_rot_smem_bytes(g.n_max);
-    if (g.kind == kSweepF64) return sweep_f64_smem_bytes(g.n_max, g.block);
+    if (g.kind == kSweepF64) return sweep_f64_smem_bytes(g.n_max, g.block, g.f64_terms);
     return sweep_f32_smem_bytes(g.n_max, g.block);
 }
 
@@ -566,7 +568,10 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     } else if (h->precision == SA_FP64) {
         h->groups.resize(1);
         h->groups[0].kind = kSweepF64;
-        for (int p = 0; p < P; ++p) h->groups[0].probs.push_back(p);
+        for (int p = 0; p < P; ++p) {
+            h->groups[0].probs.push_back(p);
+            if (sweep_f64_keeps_terms(h->probs[p].cost)) h->groups[0].f64_terms = true;
+        }
     } else {
         // one group per (dimension bucket, class) pair: class 0 = thread
         // layout only, 1 = costs the chain-per-warp layout serves (no global

@@ -56,6 +56,38 @@ __device__ __forceinline__ double full_cost(const ProbDev& P, const double* xcol
     }
 }
 
+// Griewank's and Michalewicz's per-coordinate factors (cos(x_i / sqrt i) and
+// sin(x_i) sin(i x_i^2 / pi)^20): each chain keeps them beside its state, so a
+// step evaluates one new factor and redoes the sum and the product in index
+// order from the kept ones -- the same operations on the same values as the
+// full evaluation, at a fraction of its transcendental work.
+template <int COST>
+constexpr bool kKeepsTerms = COST == kGriewank || COST == kMichalewicz;
+
+template <int COST>
+__device__ __forceinline__ double term64(int i, double t) {
+    if (COST == kGriewank) return cos(t / sqrt((double)(i + 1)));
+    return sin(t) * pow(sin((double)(i + 1) * t * t / CUDART_PI), 20.0);
+}
+
+// f from the kept factors, with coordinate d's value and factor replaced (d < 0: none).
+template <int COST>
+__device__ __forceinline__ double kept_cost(const double* xcol, const double* tcol, int B, int n, int d, double xd,
+                                            double td) {
+    if (COST == kGriewank) {
+        double q = 0.0, p = 1.0;
+        for (int i = 0; i < n; ++i) {
+            const double v = i == d ? xd : xcol[i * B];
+            q += v * v;
+            p *= i == d ? td : tcol[i * B];
+        }
+        return 1.0 + q / 4000.0 - p;
+    }
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += i == d ? td : tcol[i * B];
+    return -s;
+}
+
 template <int COST>
 __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level, double* xs,
                            unsigned long long* red) {
@@ -87,8 +119,15 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     uint32_t nacc = 0;
+    double* tcol = xs + (size_t)n * B + t;  // kept factors (kKeepsTerms costs only)
     if (active) {
-        double F = full_cost<COST>(P, xcol, B, n, -1, 0.0);
+        double F;
+        if (kKeepsTerms<COST>) {
+            for (int k = 0; k < n; ++k) tcol[k * B] = term64<COST>(k, xcol[k * B]);
+            F = kept_cost<COST>(xcol, tcol, B, n, -1, 0.0, 0.0);
+        } else {
+            F = full_cost<COST>(P, xcol, B, n, -1, 0.0);
+        }
         uint32_t bw = 0;
         for (int s = 0; s < A.L; ++s) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
@@ -105,11 +144,18 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             }
             if (xp < lo) xp = lo;
             if (xp > hi) xp = hi;
-            const double Fp = full_cost<COST>(P, xcol, B, n, d, xp);
+            double td = 0.0, Fp;
+            if (kKeepsTerms<COST>) {
+                td = term64<COST>(d, xp);
+                Fp = kept_cost<COST>(xcol, tcol, B, n, d, xp, td);
+            } else {
+                Fp = full_cost<COST>(P, xcol, B, n, d, xp);
+            }
             const double dF = Fp - F;
             const bool acc = (dF <= 0.0) || (u3 < exp(-dF / T));
             if (acc) {
                 xcol[d * B] = xp;
+                if (kKeepsTerms<COST>) tcol[d * B] = td;
                 F = Fp;
                 ++nacc;
             }
@@ -169,9 +215,11 @@ __global__ void __launch_bounds__(kMaxBlock) sweep_f64_kernel(SweepArgs A) {
 
 }  // namespace
 
-size_t sweep_f64_smem_bytes(int n, int block) {
-    return 32 * sizeof(unsigned long long) + (size_t)n * block * sizeof(double);
+size_t sweep_f64_smem_bytes(int n, int block, bool keeps_terms) {
+    return 32 * sizeof(unsigned long long) + (size_t)n * block * sizeof(double) * (keeps_terms ? 2 : 1);
 }
+
+bool sweep_f64_keeps_terms(int cost) { return cost == kGriewank || cost == kMichalewicz; }
 
 cudaError_t sweep_f64_set_smem(size_t bytes) {
     // The limit only grows, so a later handle never invalidates an earlier handle's graphs.
