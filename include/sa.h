@@ -82,6 +82,11 @@ typedef enum {
 enum { SA_REFLECT = 0, SA_CLIP = 1 };                 /* box handling of a move */
 enum { SA_FP64 = 0, SA_FP32 = 1, SA_MIXED_BF16 = 2 }; /* arithmetic of the sweep */
 enum { SA_POLISH_PGD = 0, SA_POLISH_NELDER_MEAD = 1 };  /* local minimiser of the hybrid SA */
+/* Move of the selected coordinate (Sec. 2.1 Step 2: "a random number to modify the selected
+ * coordinate"): a Gaussian step sigma_frac (u_d - l_d) sqrt(T / T0) z (Box-Muller, cosine
+ * branch, then the box rule), or a uniform redraw x_d' = l_d + u2 (u_d - l_d) with the
+ * block's second uniform. */
+enum { SA_PROPOSAL_GAUSSIAN = 0, SA_PROPOSAL_UNIFORM = 1 };
 
 typedef struct {
     int32_t cost;        /* sa_cost */
@@ -123,6 +128,8 @@ typedef struct {
                                SA_POLISH_NELDER_MEAD: sa_nelder_mead with step_frac = sigma_frac
                                sqrt(T_last / T0) (the last level's step scale), max_iter
                                200 (n + 1), ftol 1e-12, xtol 1e-10 (n <= 4096) */
+    int32_t proposal;       /* SA_PROPOSAL_GAUSSIAN (the default) or SA_PROPOSAL_UNIFORM (not with
+                               the surrogate) */
 } sa_schedule;
 
 typedef struct {

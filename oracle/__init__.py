@@ -57,7 +57,7 @@ class Cfg(ctypes.Structure):
                 ("rho", ctypes.c_double), ("sigma_frac", ctypes.c_double),
                 ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("independent", ctypes.c_int32), ("exchange_every", ctypes.c_int32),
-                ("table", ctypes.c_void_p), ("table_rows", ctypes.c_int32)]
+                ("table", ctypes.c_void_p), ("table_rows", ctypes.c_int32), ("proposal", ctypes.c_int32)]
 
 
 class Out(ctypes.Structure):
@@ -171,7 +171,7 @@ class Problem:
 
     def __init__(self, cost, n, lo, hi, chains, L, T0=100.0, rho=0.9, sigma_frac=0.1,
                  boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0, independent=False,
-                 exchange_every=1, table=None):
+                 exchange_every=1, table=None, proposal="gaussian"):
         self.cost = COSTS[cost] if isinstance(cost, str) else int(cost)
         self.n = int(n)
         self.lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.n,)))
@@ -184,12 +184,13 @@ class Problem:
         self.independent = 1 if independent else 0
         self.exchange_every = int(exchange_every)
         self.table, self.table_rows = _table(table)
+        self.proposal = {"gaussian": 0, "uniform": 1}[proposal] if isinstance(proposal, str) else int(proposal)
 
     def cfg(self, K=0, level0=0) -> Cfg:
         return Cfg(self.cost, self.n, self.chains, self.L, K, level0, self.boundary, self.mode,
                    self.threads, self.problem, self.seed, self.T0, self.rho, self.sigma_frac,
                    _p(self.lo), _p(self.hi), _p(self.Q), self.independent, self.exchange_every,
-                   _p(self.table), self.table_rows)
+                   _p(self.table), self.table_rows, self.proposal)
 
     def init_point(self, c: int) -> np.ndarray:
         x = np.zeros(self.n)

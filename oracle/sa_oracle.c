@@ -381,6 +381,8 @@ typedef struct {
                                m-1, 2m-1, ...; chains continue their own states in between */
     const double* table; /* Tests 11, 18, 19: rows x (n + 1), row i = (a_i1 .. a_in, c_i) */
     int32_t table_rows;
+    int32_t proposal;    /* 0: Gaussian step sigma_frac (u_d - l_d) sqrt(T / T0) z (Box-Muller);
+                            1: the coordinate redrawn uniformly, x_d' = l_d + u2 (u_d - l_d) */
 } sao_cfg;
 
 typedef struct {
@@ -510,11 +512,17 @@ static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, doubl
         sao_block(cfg->seed, SAO_TAG_SWEEP, (uint32_t)s, (uint32_t)level, (uint32_t)c, cfg->problem, w);
         const int d = (int)sao_coord(w[0], n);
         const double u1 = sao_uniform(w[1]), u2 = sao_uniform(w[2]), u3 = sao_uniform(w[3]);
-        /* Step 2: Gaussian move of coordinate d (Box-Muller, cosine branch). */
-        const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
-        const double sigma = cfg->sigma_frac * (cfg->hi[d] - cfg->lo[d]) * s_l;
+        /* Step 2: move coordinate d -- a Gaussian step (Box-Muller, cosine branch), or a
+         * uniform redraw of the coordinate in [l_d, u_d] with the second uniform. */
         const double xd = x[d];
-        const double xp = apply_box(xd + sigma * z, cfg->lo[d], cfg->hi[d], cfg->boundary);
+        double xp;
+        if (cfg->proposal == 1) {
+            xp = apply_box(cfg->lo[d] + u2 * (cfg->hi[d] - cfg->lo[d]), cfg->lo[d], cfg->hi[d], cfg->boundary);
+        } else {
+            const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+            const double sigma = cfg->sigma_frac * (cfg->hi[d] - cfg->lo[d]) * s_l;
+            xp = apply_box(xd + sigma * z, cfg->lo[d], cfg->hi[d], cfg->boundary);
+        }
 
         /* Delayed acceptance, stage 1 (surrogate only). */
         double dFs = 0.0;

@@ -116,7 +116,7 @@ __global__ void da_patch_kernel(SweepArgs A, DaDev D, int s) {
     const int n = P.n;
     const double T = A.T_tab[level];
     const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
-    const RotMove mv = rot_propose(w, D.xf + (size_t)c * n, P, (float)A.s_tab[level], A.boundary,
+    const RotMove mv = rot_propose(w, D.xf + (size_t)c * n, P, (float)A.s_tab[level], A.boundary, 0,
                                    (float)(-T * 0.69314718055994531));
     D.xs[(size_t)c * D.np + mv.d] = std_bf16(mv.xp, D.mid[mv.d], D.inv_half[mv.d]);
 }
@@ -132,7 +132,7 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     float* yl = D.yl + (size_t)c * n;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
     const float neg_T_ln2 = (float)(-T * 0.69314718055994531);
-    const RotMove mv = rot_propose(w, x, P, (float)A.s_tab[level], A.boundary, neg_T_ln2);
+    const RotMove mv = rot_propose(w, x, P, (float)A.s_tab[level], A.boundary, 0, neg_T_ln2);
     // surrogate at the proposal (fixed summation order) and at the current state
     const float* q = D.part + (size_t)c * 4;
     const float ftp = D.ms[0] + D.ms[1] * (((q[0] + q[1]) + q[2]) + q[3] + D.b3[0]);

@@ -66,20 +66,26 @@ struct RotMove {
     uint32_t w3;  // the word of u3
 };
 // P: the box (uniform scalars, or per coordinate when P.uniform == 0); sl = sqrt(T / T0).
+// uprop: 1 = uniform redraw of the coordinate (x' = lo + u2 (hi - lo)), 0 = Gaussian step.
 __device__ __forceinline__ RotMove rot_propose(uint4 w, const float* x, const ProbDev& P, float sl, int boundary,
-                                               float neg_T_ln2) {
+                                               int uprop, float neg_T_ln2) {
     RotMove m;
     const int n = P.n;
     m.d = coord_of(w.x, n);
     float sig, lo, hi;
     if (P.uniform) { sig = P.sig_u * sl; lo = P.lo_u; hi = P.hi_u; }
     else { sig = P.sig32[m.d] * sl; lo = P.lo32[m.d]; hi = P.hi32[m.d]; }
-    const float r = sqrt_approx(-1.3862943611198906f * __log2f(u23f(w.y)));
-    const float z = -r * __cosf(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
     m.tau = neg_T_ln2 * __log2f(u23f(w.w));
     m.w3 = w.w;
     m.xo = x[m.d];
-    float xp = fmaf(sig, z, m.xo);
+    float xp;
+    if (uprop) {
+        xp = fmaf(hi - lo, u23f(w.z), lo);
+    } else {
+        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u23f(w.y)));
+        const float z = -r * __cosf(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
+        xp = fmaf(sig, z, m.xo);
+    }
     if (boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);
     m.xp = fminf(fmaxf(xp, lo), hi);
     // delta = xp - xo exactly, as dh + dl (TwoSum)

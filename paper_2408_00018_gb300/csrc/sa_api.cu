@@ -198,6 +198,9 @@ sa_status check_schedule(const sa_schedule* s) {
     if (s->precision != SA_FP64 && s->precision != SA_FP32) return SA_EINVAL;
     if ((s->surrogate != 0 && s->surrogate != 1) || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
     if (s->polish_method != SA_POLISH_PGD && s->polish_method != SA_POLISH_NELDER_MEAD) return SA_EINVAL;
+    if ((s->proposal != SA_PROPOSAL_GAUSSIAN && s->proposal != SA_PROPOSAL_UNIFORM) ||
+        (s->proposal == SA_PROPOSAL_UNIFORM && s->surrogate))
+        return SA_EINVAL;
     if (s->cost_repeat < 0 || s->cost_repeat > 4096) return SA_EINVAL;
     if ((s->independent != 0 && s->independent != 1) || (s->independent && s->surrogate)) return SA_EINVAL;
     if (s->exchange_every < 0 || (s->exchange_every > 1 && s->surrogate)) return SA_EINVAL;
@@ -754,6 +757,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         }
     }
     a.boundary = h->sch.boundary;
+    a.proposal = h->sch.proposal;
     a.key0 = (uint32_t)h->seed;
     a.key1 = (uint32_t)(h->seed >> 32) ^ kTagSweep;
     a.ikey0 = (uint32_t)h->seed;

@@ -104,6 +104,7 @@ struct SweepArgs {
     int32_t cost_repeat;   // rotated costs: evaluations of each energy difference (1; more only to emulate costlier f)
     int32_t independent;   // 1: asynchronous chains (no restart from the best; each continues its own state)
     int32_t exchange_every;  // > 1: restart from the best only after every exchange_every-th level
+    int32_t proposal;        // 0: Gaussian step; 1: uniform redraw of the coordinate in its interval
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
     uint32_t rk[20];       // sweep key of each Philox round r: (rk[2r], rk[2r+1]) (kernel-parameter operands)

@@ -154,6 +154,7 @@ struct Ctx {
     float lo_u, hi_u, sig_u;         // uniform box (sig_u already scaled by sqrt(T/T0))
     const float *slo, *shi, *ssig;   // per-coordinate box (ssig scaled)
     int boundary;
+    int uprop;        // 1: uniform redraw of the coordinate (z = u2), 0: Gaussian step
     float neg_T_ln2;  // -T ln 2: tau = -T ln u3 = neg_T_ln2 * log2(u3)
     float kappa;      // bound on the FP32 error of any accepted step's dF over the box (Schwefel, Rastrigin)
     uint32_t level, chain, pid, key0, key1;
@@ -164,9 +165,13 @@ __device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
     const uint4 w = philox4x32_10(make_uint4(s, C.level, C.chain, C.pid), C.key0, C.key1);
     p.d = coord_of(w.x, C.n);
     const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
-    // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
-    const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
-    p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+    if (C.uprop) {
+        p.z = u2;  // uniform redraw: x' = lo + u2 (hi - lo)
+    } else {
+        // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
+        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
+        p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+    }
     // u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3   (tau > 0, so dF <= 0 is always accepted)
     p.tau = C.neg_T_ln2 * __log2f(u3);
 }
@@ -179,7 +184,7 @@ __device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step&
     float lo, hi, sg;
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
-    float xp = fmaf(sg, p.z, xo);
+    float xp = C.uprop ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
     if (C.boundary == 0) {  // reflect once (selects, no branch)
         const float r1 = 2.0f * lo - xp, r2 = 2.0f * hi - xp;
         xp = xp < lo ? r1 : (xp > hi ? r2 : xp);
@@ -301,6 +306,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     C.shi = shi;
     C.ssig = ssig;
     C.boundary = A.boundary;
+    C.uprop = A.proposal;
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
     C.kappa = P.kappa;
     C.level = (uint32_t)level;

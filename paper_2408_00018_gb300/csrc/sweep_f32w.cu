@@ -77,6 +77,7 @@ struct WCtx {
     float lo_u, hi_u, sig_u;
     const float *slo, *shi, *ssig;
     int boundary;
+    int uprop;  // 1: uniform redraw of the coordinate (z = u2), 0: Gaussian step
     float neg_T_ln2;
     PhiloxFixed pf;
     const uint32_t* rk;  // Philox round keys (kernel parameters)
@@ -86,9 +87,13 @@ __device__ __forceinline__ void wpropose(const WCtx& C, uint32_t s, WStep& p) {
     const uint4 w = philox_step(s, C.pf, C.rk);
     p.d = coord_of(w.x, C.n);
     const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
-    // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
-    const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
-    p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+    if (C.uprop) {
+        p.z = u2;  // uniform redraw: x' = lo + u2 (hi - lo)
+    } else {
+        // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
+        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
+        p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+    }
     // u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3
     p.tau = C.neg_T_ln2 * __log2f(u3);
 }
@@ -101,7 +106,7 @@ __device__ __forceinline__ void wevaluate(const WCtx& C, WStep& p) {
     float lo, hi, sg;
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
-    float xp = fmaf(sg, p.z, xo);
+    float xp = C.uprop ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
     if (C.boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);
     xp = fminf(fmaxf(xp, lo), hi);
     p.xo = xo;
@@ -233,6 +238,7 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
     C.shi = shi;
     C.ssig = ssig;
     C.boundary = (int)opaque((uint32_t)A.boundary);
+    C.uprop = (int)opaque((uint32_t)A.proposal);
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
     // Round keys in registers for the whole level: reading them from the
     // kernel-parameter bank inside the loop would issue constant loads, which

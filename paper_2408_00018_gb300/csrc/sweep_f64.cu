@@ -133,11 +133,15 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
             const int d = coord_of(w.x, n);
             const double u1 = u23d(w.y), u2 = u23d(w.z), u3 = u23d(w.w);
-            const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
-            const double sigma = P.sig[d] * sl;
             const double xd = xcol[d * B];
             const double lo = P.lo[d], hi = P.hi[d];
-            double xp = xd + sigma * z;
+            double xp;
+            if (A.proposal == 1) {  // uniform redraw of the coordinate
+                xp = lo + u2 * (hi - lo);
+            } else {
+                const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+                xp = xd + P.sig[d] * sl * z;
+            }
             if (A.boundary == 0) {
                 if (xp < lo) xp = 2.0 * lo - xp;
                 else if (xp > hi) xp = 2.0 * hi - xp;

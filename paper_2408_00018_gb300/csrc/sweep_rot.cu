@@ -88,7 +88,7 @@ __device__ RotEnd rot_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int
     for (int s = 0; s < A.L; ++s) {
         // randomness of step s (the same block in every lane)
         const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
-        const RotMove mv = rot_propose(w, x, P, sl, A.boundary, neg_T_ln2);
+        const RotMove mv = rot_propose(w, x, P, sl, A.boundary, A.proposal, neg_T_ln2);
         const int d = mv.d;
         const float xo = mv.xo, xp = mv.xp, dh = mv.dh, dl = mv.dl, tau = mv.tau;
         // ---- FP32 energy difference and its error bound
