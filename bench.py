@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling runs only)")
     ap.add_argument("--independent", action="store_true",
                     help="asynchronous chains (no exchange between levels; the paper's V1), single-problem workloads")
+    ap.add_argument("--paper-schwefel", action="store_true",
+                    help="the paper's Schwefel accuracy and timing tables instead (T0 = 1000, rho = 0.99, 1146 levels "
+                         "of N = 100, 16384 chains, n = 8 .. 512, uniform redraw moves): V2 and V1 per n")
     ap.add_argument("--suite", action="store_true",
                     help="the paper's 41-problem test suite (Tables 8-9) instead: one synchronous run per problem, "
                          "then the hybrid's Nelder-Mead polish (one JSON line per problem and a summary)")
@@ -440,8 +443,9 @@ def run_reference(args, rank, world):
 
 
 # Table 10's functions at its sizes (F0_g Schwefel n = 512, F1_d Ackley n = 400,
-# F13_b Rastrigin n = 400) with f* from their closed forms, and the annealing
-# stopped early: (cost, n, f*, T0, rho, levels).  A move changes Ackley's f by
+# F13_b Rastrigin n = 400) with f* from their closed forms, moves by the paper's
+# reading (a uniform redraw of the chosen coordinate), and the annealing stopped
+# early: (cost, n, f*, T0, rho, levels).  A move changes Ackley's f by
 # ~1e-3 at n = 400 (the others' by ~1 to 10), hence its lower T0.
 HYBRID = [("schwefel", 512, -418.9828872724337, 100.0, 0.9, 100), ("ackley", 400, 0.0, 0.01, 0.9, 100),
           ("rastrigin", 400, 0.0, 100.0, 0.9, 100)]
@@ -474,7 +478,7 @@ def run_hybrid(args):
 
     for cost, n, fstar, T0, rho, K in HYBRID:
         lo, hi = inputs.box(cost, n)
-        base = dict(T0=T0, rho=rho, levels=K, precision="fp32")
+        base = dict(T0=T0, rho=rho, levels=K, precision="fp32", proposal="uniform")
         t_sa, x_sa, f_sa = timed(sa.Schedule(**base), cost, lo, hi, n)
         out = {"metric": "hybrid SA: seconds and |f - f*| (Table 10 functions)", "workload": f"{cost}_n{n}",
                "data": "synthetic", "n_gpus": 1,
@@ -497,8 +501,47 @@ def run_hybrid(args):
         print(json.dumps(out), flush=True)
 
 
+def run_paper_schwefel(args):
+    """The normalised Schwefel function under the paper's configuration (Sec. 4.1):
+    T0 = 1000, T_min = 0.01, rho = 0.99 (1146 levels), N = 100 steps, 16384 chains,
+    box [-512, 512]^n, the paper's reading of a move (a uniform redraw of the chosen
+    coordinate); FP32 state, FP64 argmin.  Per n and version (V2 synchronous, V1
+    asynchronous): |f - f*|, the relative error of x, the device time of the run
+    (CUDA events, after an untimed run) and steps/s."""
+    import numpy as np
+    import torch
+    from paper_2408_00018_gb300 import _build, inputs, sa
+
+    _build.build()
+    sa.load()
+    xs, fs = 420.968746, inputs.SCHWEFEL_F_STAR
+    for n in (8, 16, 32, 64, 128, 256, 512):
+        lo, hi = np.full(n, -512.0), np.full(n, 512.0)
+        out = {"metric": "paper Schwefel table: |f - f*|, relative x error, seconds", "n": n, "chains": 16384,
+               "L": 100, "levels": 1146, "proposal": "uniform", "precision": "fp32"}
+        for version, indep in (("V2", 0), ("V1", 1)):
+            sch = sa.Schedule(T0=1000.0, rho=0.99, levels=0, T_min=0.01, precision="fp32", independent=indep,
+                              proposal="uniform")
+            with sa.create("schwefel", lo, hi, n, 16384, 100, sch, seed=0) as h:
+                h.run()  # untimed: graph capture
+                h.reset()
+                stream = torch.cuda.current_stream()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                h.run()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                x, f, st = h.best()
+            dt = e0.elapsed_time(e1) / 1e3
+            out[version] = {"err": abs(f - fs), "rel_x": float(np.linalg.norm(x - xs) / np.linalg.norm(np.full(n, xs))),
+                            "s": dt, "steps": st["steps"], "steps_per_s": st["steps"] / dt}
+        print(json.dumps(out), flush=True)
+
+
 # The suite's schedule: one for every problem (the paper tunes per function and
-# prints no schedule): T0 = 10, rho = 0.9, 100 levels of L = 500 steps.  Costs
+# prints no schedule): T0 = 10, rho = 0.9, 100 levels of L = 500 steps, moves
+# by the paper's reading (a uniform redraw of the chosen coordinate).  Costs
 # with an O(1) energy difference run FP32 with 65536 chains; the Appendix's other
 # tests run the FP64 full evaluation with 16384 chains (4096 above 16 coordinates,
 # where every step evaluates n transcendental terms in FP64).
@@ -525,7 +568,7 @@ def run_suite(args):
                "precision": "fp32" if fp32 else "fp64", "steps": C * SUITE_L * SUITE_K, "f_star": p["f_star"]}
         for polish in (0, SUITE_POLISH):
             sch = sa.Schedule(T0=SUITE_T0, rho=SUITE_RHO, levels=SUITE_K, precision="fp32" if fp32 else "fp64",
-                              polish_k=polish, polish_method="nelder_mead")
+                              polish_k=polish, polish_method="nelder_mead", proposal="uniform")
             with sa.create(p["cost"], p["lo"], p["hi"], p["n"], C, SUITE_L, sch, seed=0, table=p["table"]) as h:
                 h.run()  # untimed: graph capture
                 h.reset()
@@ -552,6 +595,9 @@ def run_suite(args):
 
 def main():
     args = parse()
+    if args.paper_schwefel:
+        run_paper_schwefel(args)
+        return
     if args.suite:
         run_suite(args)
         return
