@@ -57,14 +57,15 @@ class Cfg(ctypes.Structure):
                 ("rho", ctypes.c_double), ("sigma_frac", ctypes.c_double),
                 ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("independent", ctypes.c_int32), ("exchange_every", ctypes.c_int32),
-                ("table", ctypes.c_void_p), ("table_rows", ctypes.c_int32), ("proposal", ctypes.c_int32)]
+                ("table", ctypes.c_void_p), ("table_rows", ctypes.c_int32), ("proposal", ctypes.c_int32),
+                ("crossover", ctypes.c_int32)]
 
 
 class Out(ctypes.Structure):
     _fields_ = [("x_best", ctypes.c_void_p), ("f_best", ctypes.c_void_p), ("x_inc", ctypes.c_void_p),
                 ("f_inc", ctypes.c_void_p), ("argmin", ctypes.c_void_p), ("f_level", ctypes.c_void_p),
                 ("accepts", ctypes.c_void_p), ("bits", ctypes.c_void_p), ("trace_levels", ctypes.c_int32),
-                ("F_final", ctypes.c_void_p), ("X_final", ctypes.c_void_p)]
+                ("F_final", ctypes.c_void_p), ("X_final", ctypes.c_void_p), ("xo_src", ctypes.c_void_p)]
 
 
 def lib():
@@ -104,6 +105,8 @@ def lib():
             L.sao_pgd.restype = ctypes.c_int
             L.sao_nelder_mead.argtypes = [i32, i32, vp, vp, vp, vp, i32, vp, f64, i32, f64, f64, vp, vp]
             L.sao_nelder_mead.restype = ctypes.c_int
+            L.sao_crossover_sources.argtypes = [ctypes.POINTER(Cfg), i32, vp, i64, vp]
+            L.sao_crossover_sources.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -171,7 +174,7 @@ class Problem:
 
     def __init__(self, cost, n, lo, hi, chains, L, T0=100.0, rho=0.9, sigma_frac=0.1,
                  boundary="reflect", seed=0, problem=0, Q=None, mode=0, threads=0, independent=False,
-                 exchange_every=1, table=None, proposal="gaussian"):
+                 exchange_every=1, table=None, proposal="gaussian", crossover=False):
         self.cost = COSTS[cost] if isinstance(cost, str) else int(cost)
         self.n = int(n)
         self.lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.n,)))
@@ -185,12 +188,22 @@ class Problem:
         self.exchange_every = int(exchange_every)
         self.table, self.table_rows = _table(table)
         self.proposal = {"gaussian": 0, "uniform": 1}[proposal] if isinstance(proposal, str) else int(proposal)
+        self.crossover = 1 if crossover else 0
 
     def cfg(self, K=0, level0=0) -> Cfg:
         return Cfg(self.cost, self.n, self.chains, self.L, K, level0, self.boundary, self.mode,
                    self.threads, self.problem, self.seed, self.T0, self.rho, self.sigma_frac,
                    _p(self.lo), _p(self.hi), _p(self.Q), self.independent, self.exchange_every,
-                   _p(self.table), self.table_rows, self.proposal)
+                   _p(self.table), self.table_rows, self.proposal, self.crossover)
+
+    def crossover_sources(self, level: int, F) -> np.ndarray:
+        """The stochastic crossover's draw of a source chain for every chain, given final values F."""
+        F = np.ascontiguousarray(F, np.float64)
+        src = np.zeros(F.size, np.int64)
+        cfg = self.cfg()
+        if lib().sao_crossover_sources(ctypes.byref(cfg), level, _p(F), F.size, _p(src)) != 0:
+            raise ValueError("sao_crossover_sources failed")
+        return src
 
     def init_point(self, c: int) -> np.ndarray:
         x = np.zeros(self.n)
@@ -291,14 +304,15 @@ class Problem:
         bits = np.zeros((max(tl, 1), C, words), np.uint32) if tl > 0 else None
         Ff = np.zeros(C) if want_final else None
         Xf = np.zeros((C, n)) if want_final else None
-        out = Out(_p(xb), _p(fb), _p(xi), _p(fi), _p(am), _p(fl), _p(ac), _p(bits), tl, _p(Ff), _p(Xf))
+        xs = np.zeros((max(K, 1), C), np.int64) if self.crossover else None
+        out = Out(_p(xb), _p(fb), _p(xi), _p(fi), _p(am), _p(fl), _p(ac), _p(bits), tl, _p(Ff), _p(Xf), _p(xs))
         cfg = self.cfg(K, level0)
         rc = lib().sao_run(ctypes.byref(cfg), ctypes.byref(out))
         if rc != 0:
             raise ValueError(f"sao_run failed ({rc})")
         return {"x_best": xb, "f_best": float(fb[0]), "x_inc": xi, "f_inc": float(fi[0]),
                 "argmin": am[:K], "f_level": fl[:K], "accepts": ac[:K], "bits": bits,
-                "F_final": Ff, "X_final": Xf}
+                "F_final": Ff, "X_final": Xf, "xo_src": None if xs is None else xs[:K]}
 
 
 def pgd(name_or_id, x0, lo, hi, Q=None, max_iter=1000, tol=1e-10, armijo_c=1e-4, max_halvings=30):

@@ -44,6 +44,7 @@
 #define SAO_TAG_SWEEP 0u
 #define SAO_TAG_INIT 1u
 #define SAO_TAG_DA 3u
+#define SAO_TAG_XO 5u
 
 enum { SAO_SCHWEFEL = 0, SAO_RASTRIGIN = 1, SAO_ACKLEY = 2, SAO_ROSENBROCK = 3,
        SAO_ROT_RASTRIGIN = 4, SAO_ROT_SCHWEFEL = 5,
@@ -383,6 +384,8 @@ typedef struct {
     int32_t table_rows;
     int32_t proposal;    /* 0: Gaussian step sigma_frac (u_d - l_d) sqrt(T / T0) z (Box-Muller);
                             1: the coordinate redrawn uniformly, x_d' = l_d + u2 (u_d - l_d) */
+    int32_t crossover;   /* 0: every exchange restarts all chains from the minimum; 1: stochastic
+                            crossover (Boltzmann selection, see crossover_sources) */
 } sao_cfg;
 
 typedef struct {
@@ -397,6 +400,8 @@ typedef struct {
     int32_t trace_levels;
     double* F_final;     /* [chains] F at the end of the last level, or NULL */
     double* X_final;     /* [chains * n] states at the end of the last level, or NULL */
+    int64_t* xo_src;     /* [K][chains] crossover: the chain each chain restarts from after
+                            level k (-1 where no exchange follows), or NULL */
 } sao_out;
 
 /* T_l = T0 rho^l by repeated multiplication (the host loop of Listing 3). */
@@ -646,6 +651,50 @@ static int cost_ok(const sao_cfg* cfg) {
 }
 
 /*
+ * Stochastic crossover (a reading of the SOS scheme the paper cites in Sec. 2.2:
+ * an exchange operator that is random instead of the minimum): at an exchange,
+ * chain c restarts from the final state of chain j, drawn with probability
+ * w_j / sum_k w_k, w_j = exp(-(F_j - F_min) / T) at the level's temperature T
+ * (0 for a non-finite F_j).  The draw inverts the running sum S_j = w_0 + ... + w_j
+ * at t = u_c S_{C-1}: j = min{ j : S_j > t }, u_c from word 0 of the Philox block
+ * (0, level, c, problem) of stream tag 5.  As T -> 0 every chain draws the minimum.
+ */
+static void crossover_sources(const sao_cfg* cfg, int32_t level, const double* F, int64_t C, double Fmin,
+                              int64_t* src, double* S) {
+    const double T = sao_temperature(cfg->T0, cfg->rho, level);
+    double acc = 0.0;
+    for (int64_t j = 0; j < C; ++j) {
+        acc += isfinite(F[j]) ? exp(-(F[j] - Fmin) / T) : 0.0;
+        S[j] = acc;
+    }
+    for (int64_t c = 0; c < C; ++c) {
+        uint32_t w[4];
+        sao_block(cfg->seed, SAO_TAG_XO, 0u, (uint32_t)level, (uint32_t)c, cfg->problem, w);
+        const double t = sao_uniform(w[0]) * acc;
+        int64_t a = 0, b = C - 1;
+        while (a < b) {
+            const int64_t m = a + (b - a) / 2;
+            if (S[m] > t) b = m;
+            else a = m + 1;
+        }
+        src[c] = a;
+    }
+}
+
+/* The crossover's draw for given final values (exposed for tests). */
+int sao_crossover_sources(const sao_cfg* cfg, int32_t level, const double* F, int64_t C, int64_t* src) {
+    if (!cfg || !F || !src || C < 1) return -1;
+    int64_t p = 0;
+    for (int64_t c = 1; c < C; ++c)
+        if (F[c] < F[p]) p = c;
+    double* S = (double*)malloc(sizeof(double) * (size_t)C);
+    if (!S) return -2;
+    crossover_sources(cfg, level, F, C, F[p], src, S);
+    free(S);
+    return 0;
+}
+
+/*
  * Run levels level0 .. level0+K-1 of synchronous parallel SA (Listings 3-4).
  * Returns 0 on success, -1 on a bad argument, -2 on allocation failure.
  */
@@ -655,14 +704,21 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
         return -1;
     if (!cost_ok(cfg)) return -1;
     const int periodic = cfg->exchange_every > 1;
-    if ((cfg->independent || periodic) && cfg->level0 != 0) return -1;
+    if ((cfg->independent || periodic || cfg->crossover) && cfg->level0 != 0) return -1;
+    if (cfg->crossover && cfg->independent) return -1;
     const int n = cfg->n;
     const int64_t C = cfg->chains;
     const int words = (cfg->L + 31) / 32;
     double* X = (double*)malloc(sizeof(double) * (size_t)C * (size_t)n);
     double* F = (double*)malloc(sizeof(double) * (size_t)C);
     int64_t* A = (int64_t*)malloc(sizeof(int64_t) * (size_t)C);
-    if (!X || !F || !A) { free(X); free(F); free(A); return -2; }
+    double* Xn = cfg->crossover ? (double*)malloc(sizeof(double) * (size_t)C * (size_t)n) : NULL;
+    double* S = cfg->crossover ? (double*)malloc(sizeof(double) * (size_t)C) : NULL;
+    int64_t* src = cfg->crossover ? (int64_t*)malloc(sizeof(int64_t) * (size_t)C) : NULL;
+    if (!X || !F || !A || (cfg->crossover && (!Xn || !S || !src))) {
+        free(X); free(F); free(A); free(Xn); free(S); free(src);
+        return -2;
+    }
 #ifdef _OPENMP
     int nthreads = cfg->threads > 0 ? cfg->threads : omp_get_max_threads();
 #endif
@@ -675,7 +731,8 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
 #endif
         for (int64_t c = 0; c < C; ++c) {
             double* x = X + (size_t)c * n;
-            const int own = cfg->independent || (periodic && level % cfg->exchange_every != 0);
+            /* crossover: x already holds the state the chain drew at the exchange */
+            const int own = cfg->independent || cfg->crossover || (periodic && level % cfg->exchange_every != 0);
             if (level == 0) sao_init_point(cfg, c, x);
             else if (!own) memcpy(x, out->x_best, sizeof(double) * (size_t)n);
             /* own start: x is the chain's own state after the previous level */
@@ -701,10 +758,24 @@ int sao_run(const sao_cfg* cfg, sao_out* out) {
             if (out->F_final) memcpy(out->F_final, F, sizeof(double) * (size_t)C);
             if (out->X_final) memcpy(out->X_final, X, sizeof(double) * (size_t)C * (size_t)n);
         }
+        /* Stochastic crossover before the next level when it starts with an exchange. */
+        const int32_t nxt = level + 1;
+        const int exchange_next = !(periodic && nxt % cfg->exchange_every != 0);
+        if (out->xo_src) for (int64_t c = 0; c < C; ++c) out->xo_src[(size_t)k * (size_t)C + (size_t)c] = -1;
+        if (cfg->crossover && exchange_next && k + 1 < cfg->K) {
+            crossover_sources(cfg, level, F, C, F[p], src, S);
+            for (int64_t c = 0; c < C; ++c)
+                memcpy(Xn + (size_t)c * n, X + (size_t)src[c] * n, sizeof(double) * (size_t)n);
+            double* t = X; X = Xn; Xn = t;
+            if (out->xo_src) memcpy(out->xo_src + (size_t)k * (size_t)C, src, sizeof(int64_t) * (size_t)C);
+        }
     }
     free(X);
     free(F);
     free(A);
+    free(Xn);
+    free(S);
+    free(src);
     return 0;
 }
 
