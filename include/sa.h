@@ -130,6 +130,13 @@ typedef struct {
                                200 (n + 1), ftol 1e-12, xtol 1e-10 (n <= 4096) */
     int32_t proposal;       /* SA_PROPOSAL_GAUSSIAN (the default) or SA_PROPOSAL_UNIFORM (not with
                                the surrogate) */
+    int32_t crossover;      /* 0: an exchange restarts every chain from the minimum (Sec. 2.2.2);
+                               1: stochastic crossover (a reading of the SOS scheme cited in Sec. 2.2):
+                               chain c restarts from chain j's final state, j drawn with probability
+                               exp(-(F_j - F_min) / T) / Z at the finished level's temperature
+                               (Philox stream tag 5).  Every chain's F is then exact in FP64 at
+                               every level.  Not with the surrogate, independent chains or
+                               sa_set_chain_offset */
 } sa_schedule;
 
 typedef struct {

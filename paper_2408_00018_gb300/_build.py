@@ -33,6 +33,7 @@ UNITS = {
     "rot_prep.cu": [],
     "mlp.cu": [],
     "da.cu": [],
+    "crossover.cu": ["-fmad=false"],
 }
 
 

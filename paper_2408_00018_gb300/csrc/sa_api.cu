@@ -134,6 +134,8 @@ struct sa_handle {
     double *d_px0 = nullptr, *d_px = nullptr, *d_pf = nullptr;
     int* d_pit = nullptr;
     double* d_nmws = nullptr;  // Nelder-Mead workspace (polish_method == SA_POLISH_NELDER_MEAD)
+    CrossoverWork xo{};        // stochastic crossover scratch (schedule.crossover)
+    uint32_t xkey0 = 0, xkey1 = 0;
     double nm_step = 0.0;      // its initial simplex size, as a fraction of the box
     SweepArgs args{};
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
@@ -200,6 +202,8 @@ sa_status check_schedule(const sa_schedule* s) {
     if (s->polish_method != SA_POLISH_PGD && s->polish_method != SA_POLISH_NELDER_MEAD) return SA_EINVAL;
     if ((s->proposal != SA_PROPOSAL_GAUSSIAN && s->proposal != SA_PROPOSAL_UNIFORM) ||
         (s->proposal == SA_PROPOSAL_UNIFORM && s->surrogate))
+        return SA_EINVAL;
+    if ((s->crossover != 0 && s->crossover != 1) || (s->crossover && (s->surrogate || s->independent)))
         return SA_EINVAL;
     if (s->cost_repeat < 0 || s->cost_repeat > 4096) return SA_EINVAL;
     if ((s->independent != 0 && s->independent != 1) || (s->independent && s->surrogate)) return SA_EINVAL;
@@ -302,6 +306,15 @@ cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
 // The sweep of one level: one launch per group; several groups run
 // concurrently on forked streams (also inside a captured graph).
 cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
+    // stochastic crossover: this level's start states drawn from the previous level's final
+    // states (a no-op on the device unless an exchange precedes this level); the previous
+    // level's states stay readable until here (sa_trace_states)
+    if (h->sch.crossover)
+        for (size_t p = 0; p < h->probs.size(); ++p) {
+            const cudaError_t e = launch_crossover(h->args, h->d_probs + p, h->probs[p].dev, h->precision,
+                                                   is_rot(h->probs[p].cost), h->xkey0, h->xkey1, h->xo, s);
+            if (e != cudaSuccess) return e;
+        }
     if (h->groups.size() == 1) return launch_group(h, h->groups[0], s);
     cudaError_t e = cudaEventRecord(h->fork_ev, s);
     for (Group& g : h->groups) {
@@ -758,6 +771,25 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     }
     a.boundary = h->sch.boundary;
     a.proposal = h->sch.proposal;
+    a.crossover = h->sch.crossover;
+    a.levels_total = h->levels_total;
+    if (h->sch.crossover) {
+        int64_t cmax = 1;
+        size_t xbytes = 16;
+        for (auto& hp : h->probs) {
+            cmax = std::max(cmax, hp.chains);
+            const size_t total = (size_t)hp.chains * (size_t)hp.n;
+            xbytes = std::max(xbytes, total * (is_rot(hp.cost) ? 12 : (h->precision == SA_FP64 ? 8 : 4)) + 16);
+        }
+        unsigned char* xt;
+        if ((st = dalloc(h, &h->xo.w, (size_t)cmax)) || (st = dalloc(h, &h->xo.S, (size_t)cmax)) ||
+            (st = dalloc(h, &h->xo.bsum, crossover_blocks(cmax) + 1)) || (st = dalloc(h, &h->xo.src, (size_t)cmax)) ||
+            (st = dalloc(h, &xt, xbytes)))
+            return st;
+        h->xo.xtmp = xt;
+        h->xkey0 = (uint32_t)h->seed;
+        h->xkey1 = (uint32_t)(h->seed >> 32) ^ kTagCrossover;
+    }
     a.key0 = (uint32_t)h->seed;
     a.key1 = (uint32_t)(h->seed >> 32) ^ kTagSweep;
     a.ikey0 = (uint32_t)h->seed;
@@ -1081,6 +1113,7 @@ sa_status sa_set_chain_offset(sa_handle* h, int64_t offset) {
     if (!h) return SA_EINVAL;
     if (h->failed != SA_OK) return SA_ESTATE;
     if (h->probs.size() != 1 || offset < 0 || offset + h->probs[0].chains > ((int64_t)1 << 32)) return SA_EINVAL;
+    if (h->sch.crossover) return SA_EINVAL;  // the crossover draws among one handle's chains
     if (h->levels_done != 0) return SA_ESTATE;
     h->pd[0].cid0 = (uint32_t)offset;
     h->probs[0].dev.cid0 = (uint32_t)offset;

@@ -9,6 +9,7 @@ namespace sa {
 // Philox stream tags: key = (seed_lo, seed_hi ^ tag).
 constexpr uint32_t kTagSweep = 0u;
 constexpr uint32_t kTagInit = 1u;
+constexpr uint32_t kTagCrossover = 5u;
 
 // Scalars kept per problem in device memory.
 enum ScalarSlot : int {
@@ -105,6 +106,8 @@ struct SweepArgs {
     int32_t independent;   // 1: asynchronous chains (no restart from the best; each continues its own state)
     int32_t exchange_every;  // > 1: restart from the best only after every exchange_every-th level
     int32_t proposal;        // 0: Gaussian step; 1: uniform redraw of the coordinate in its interval
+    int32_t crossover;       // 1: stochastic crossover at each exchange (every level > 0 starts from X)
+    int32_t levels_total;    // levels of the schedule (the crossover skips the last level)
     uint32_t key0, key1;   // Philox key of the sweep stream
     uint32_t ikey0, ikey1; // Philox key of the initial-point stream
     uint32_t rk[20];       // sweep key of each Philox round r: (rk[2r], rk[2r+1]) (kernel-parameter operands)
@@ -113,11 +116,20 @@ struct SweepArgs {
 // Does level `level` start each chain from its own state (rather than from the
 // best state of the previous level)?  Asynchronous chains never exchange; with a
 // period m > 1 the exchange follows levels m-1, 2m-1, ... (Sec. 2.2.1-2.2.2).
+// With the stochastic crossover every level > 0 starts from X, which the crossover
+// has refilled with the drawn states when an exchange preceded the level.
 __host__ __device__ inline bool own_start(const SweepArgs& a, int level) {
-    return level > 0 && (a.independent || (a.exchange_every > 1 && level % a.exchange_every != 0));
+    return level > 0 && (a.independent || a.crossover || (a.exchange_every > 1 && level % a.exchange_every != 0));
 }
 // Must every chain keep its state at the end of a level (for the next level's own start)?
-__host__ __device__ inline bool keep_states(const SweepArgs& a) { return a.independent || a.exchange_every > 1; }
+__host__ __device__ inline bool keep_states(const SweepArgs& a) {
+    return a.independent || a.crossover || a.exchange_every > 1;
+}
+// Is the level after `level` an exchange level (the synchronous restart or the crossover)?
+__host__ __device__ inline bool exchange_after(const SweepArgs& a, int level) {
+    const int next = level + 1;
+    return !a.independent && next < a.levels_total && !(a.exchange_every > 1 && next % a.exchange_every != 0);
+}
 
 // Launch wrappers (one per translation unit).
 cudaError_t launch_sweep_f32(const SweepArgs& a, int num_items, int block, size_t smem, cudaStream_t s);
@@ -125,6 +137,20 @@ cudaError_t launch_sweep_f64(const SweepArgs& a, int num_items, int block, size_
 cudaError_t launch_argmin_restart(const SweepArgs& a, const ProbDev* probs, int num_probs, int max_blocks,
                                   int precision, cudaStream_t s);
 cudaError_t launch_level_end(RunDev* run, cudaStream_t s);
+// Stochastic crossover of one problem before the current level (device-side no-op unless
+// an exchange follows the previous level): Boltzmann weights of the previous level's F,
+// their running sum, one draw per chain, and the drawn states gathered into the
+// problem's start states.
+struct CrossoverWork {
+    double* w;        // [max chains] weights
+    double* S;        // [max chains] running sums
+    double* bsum;     // [max blocks] block sums, then their exclusive prefix
+    int64_t* src;     // [max chains] drawn source chain
+    void* xtmp;       // gather buffer: max over problems of n * chains * 12 bytes
+};
+cudaError_t launch_crossover(const SweepArgs& a, const ProbDev* dprob, const ProbDev& hprob, int precision, bool rot,
+                             uint32_t xkey0, uint32_t xkey1, const CrossoverWork& w, cudaStream_t s);
+size_t crossover_blocks(int64_t chains);
 cudaError_t launch_reset(ProbDev* probs, int num_probs, RunDev* run, cudaStream_t s);
 cudaError_t launch_stamp_start(RunDev* run, cudaStream_t s);
 cudaError_t sweep_f32_set_smem(size_t bytes);

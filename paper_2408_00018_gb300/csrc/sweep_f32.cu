@@ -392,7 +392,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     }
     __syncthreads();
     const double M = red[64];
-    const bool is_cand = finite && (tracing || level == A.full_level || lo_c <= M);
+    const bool is_cand = finite && (tracing || level == A.full_level || A.crossover || lo_c <= M);
     if (is_cand) cand[atomicAdd(ncand, 1)] = t;
     else if (active) {
         A.F[gc] = finite ? CUDART_INF : CUDART_NAN;

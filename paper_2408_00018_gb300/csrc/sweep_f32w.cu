@@ -341,7 +341,7 @@ __device__ void warp_chain_finish(const SweepArgs& A, const ProbDev& P, int64_t 
     const int64_t gc = P.chain_base + c;
     const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
     const bool finite = isfinite(Fa);
-    if (finite && (tracing || level == A.full_level || Fa - ec <= M)) {
+    if (finite && (tracing || level == A.full_level || A.crossover || Fa - ec <= M)) {
         double p1 = 0.0;
         for (int k = lane; k < n; k += 32) partial64<COST>(xw, n, k, p1);
 #pragma unroll

@@ -144,7 +144,7 @@ __device__ void rot_finish(const SweepArgs& A, const ProbDev& P, int64_t c, int 
     const int64_t gc = P.chain_base + c;
     const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
     const bool finite = isfinite(r.Fa);
-    if (finite && (tracing || level == A.full_level || r.Fa - r.ec <= M)) {
+    if (finite && (tracing || level == A.full_level || A.crossover || r.Fa - r.ec <= M)) {
         double part = 0.0;
         for (int i = lane; i < n; i += 32) part += rot_g64<COST>((double)yh[i] + (double)yl[i]);
         part = rot_wsumd(part);

@@ -60,7 +60,8 @@ class _Schedule(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("sigma_frac", ctypes.c_double), ("boundary", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("surrogate", ctypes.c_int32), ("polish_k", ctypes.c_int32),
                 ("trace_levels", ctypes.c_int32), ("cost_repeat", ctypes.c_int32), ("independent", ctypes.c_int32),
-                ("exchange_every", ctypes.c_int32), ("polish_method", ctypes.c_int32), ("proposal", ctypes.c_int32)]
+                ("exchange_every", ctypes.c_int32), ("polish_method", ctypes.c_int32), ("proposal", ctypes.c_int32),
+                ("crossover", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -171,12 +172,13 @@ class Schedule:
     exchange_every: int = 1
     polish_method: str = "pgd"
     proposal: str = "gaussian"
+    crossover: int = 0
 
     def _c(self) -> _Schedule:
         return _Schedule(self.T0, self.rho, self.T_min, self.levels, self.sigma_frac, BOUNDARY[self.boundary],
                          PRECISION[self.precision], self.surrogate, self.polish_k, self.trace_levels,
                          self.cost_repeat, self.independent, self.exchange_every, POLISH[self.polish_method],
-                         PROPOSAL[self.proposal])
+                         PROPOSAL[self.proposal], self.crossover)
 
 
 def levels_for(T0: float, rho: float, T_min: float) -> int:
