@@ -506,8 +506,9 @@ def run_paper_schwefel(args):
     T0 = 1000, T_min = 0.01, rho = 0.99 (1146 levels), N = 100 steps, 16384 chains,
     box [-512, 512]^n, the paper's reading of a move (a uniform redraw of the chosen
     coordinate); FP32 state, FP64 argmin.  Per n and version (V2 synchronous, V1
-    asynchronous): |f - f*|, the relative error of x, the device time of the run
-    (CUDA events, after an untimed run) and steps/s."""
+    asynchronous, V2 with the stochastic crossover instead of the minimum): |f - f*|,
+    the relative error of x, the device time of the run (CUDA events, after an
+    untimed run) and steps/s."""
     import numpy as np
     import torch
     from paper_2408_00018_gb300 import _build, inputs, sa
@@ -519,9 +520,9 @@ def run_paper_schwefel(args):
         lo, hi = np.full(n, -512.0), np.full(n, 512.0)
         out = {"metric": "paper Schwefel table: |f - f*|, relative x error, seconds", "n": n, "chains": 16384,
                "L": 100, "levels": 1146, "proposal": "uniform", "precision": "fp32"}
-        for version, indep in (("V2", 0), ("V1", 1)):
+        for version, indep, xo in (("V2", 0, 0), ("V1", 1, 0), ("V2_crossover", 0, 1)):
             sch = sa.Schedule(T0=1000.0, rho=0.99, levels=0, T_min=0.01, precision="fp32", independent=indep,
-                              proposal="uniform")
+                              proposal="uniform", crossover=xo)
             with sa.create("schwefel", lo, hi, n, 16384, 100, sch, seed=0) as h:
                 h.run()  # untimed: graph capture
                 h.reset()
