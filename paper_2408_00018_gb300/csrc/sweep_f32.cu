@@ -154,18 +154,19 @@ struct Ctx {
     float lo_u, hi_u, sig_u;         // uniform box (sig_u already scaled by sqrt(T/T0))
     const float *slo, *shi, *ssig;   // per-coordinate box (ssig scaled)
     int boundary;
-    int uprop;        // 1: uniform redraw of the coordinate (z = u2), 0: Gaussian step
     float neg_T_ln2;  // -T ln 2: tau = -T ln u3 = neg_T_ln2 * log2(u3)
     float kappa;      // bound on the FP32 error of any accepted step's dF over the box (Schwefel, Rastrigin)
     uint32_t level, chain, pid, key0, key1;
 };
 
 // Randomness of step s: coordinate, Gaussian deviate, acceptance threshold.
+// UP: the move is a uniform redraw of the coordinate (z = u2) instead of a Gaussian step.
+template <bool UP>
 __device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
     const uint4 w = philox4x32_10(make_uint4(s, C.level, C.chain, C.pid), C.key0, C.key1);
     p.d = coord_of(w.x, C.n);
     const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
-    if (C.uprop) {
+    if (UP) {
         p.z = u2;  // uniform redraw: x' = lo + u2 (hi - lo)
     } else {
         // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
@@ -177,14 +178,14 @@ __device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
 }
 
 // Move and energy difference of a proposed step from the chain's current state.
-template <int COST, bool UB>
+template <int COST, bool UB, bool UP>
 __device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step& p) {
     const int d = p.d;
     const float xo = C.xcol[d * C.B];
     float lo, hi, sg;
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
-    float xp = C.uprop ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
+    float xp = UP ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
     if (C.boundary == 0) {  // reflect once (selects, no branch)
         const float r1 = 2.0f * lo - xp, r2 = 2.0f * hi - xp;
         xp = xp < lo ? r1 : (xp > hi ? r2 : xp);
@@ -242,7 +243,7 @@ __device__ __forceinline__ bool conflicts(int dk, int dj) {
     return dk == dj;
 }
 
-template <int COST, bool UB, int U>
+template <int COST, bool UB, int U, bool UP>
 __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
                            float* xs, float* slo, float* shi, float* ssig, double* red, int* cand, int* ncand) {
     const int t = threadIdx.x, B = blockDim.x, n = P.n;
@@ -306,7 +307,6 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     C.shi = shi;
     C.ssig = ssig;
     C.boundary = A.boundary;
-    C.uprop = A.proposal;
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
     C.kappa = P.kappa;
     C.level = (uint32_t)level;
@@ -350,24 +350,24 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             for (; s + U <= L; s += U) {
                 Step p[U];
 #pragma unroll
-                for (int j = 0; j < U; ++j) propose(C, (uint32_t)(s + j), p[j]);
+                for (int j = 0; j < U; ++j) propose<UP>(C, (uint32_t)(s + j), p[j]);
 #pragma unroll
-                for (int j = 0; j < U; ++j) evaluate<COST, UB>(C, st, p[j]);
+                for (int j = 0; j < U; ++j) evaluate<COST, UB, UP>(C, st, p[j]);
                 bool acc[U];
 #pragma unroll
                 for (int j = 0; j < U; ++j) {
                     bool dirty = false;
 #pragma unroll
                     for (int k = 0; k < j; ++k) dirty |= acc[k] && conflicts<COST>(p[k].d, p[j].d);
-                    if (dirty) evaluate<COST, UB>(C, st, p[j]);
+                    if (dirty) evaluate<COST, UB, UP>(C, st, p[j]);
                     acc[j] = commit(p[j], s + j);
                 }
             }
         }
         for (; s < L; ++s) {
             Step p;
-            propose(C, (uint32_t)s, p);
-            evaluate<COST, UB>(C, st, p);
+            propose<UP>(C, (uint32_t)s, p);
+            evaluate<COST, UB, UP>(C, st, p);
             commit(p, s);
         }
     }
@@ -436,14 +436,17 @@ __device__ __forceinline__ void dispatch_u(const SweepArgs& A, const ProbDev& P,
                                            int* ncand) {
     const bool ub = P.uniform != 0;
     const int u = (COST == kAckley) ? 1 : P.unroll;
-    if (ub) {
-        if (u >= 4) sweep_tile<COST, true, 4>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else if (u == 2) sweep_tile<COST, true, 2>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else sweep_tile<COST, true, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+    if (A.proposal == 1) {  // uniform redraws: one step at a time
+        if (ub) sweep_tile<COST, true, 1, true>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else sweep_tile<COST, false, 1, true>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+    } else if (ub) {
+        if (u >= 4) sweep_tile<COST, true, 4, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else if (u == 2) sweep_tile<COST, true, 2, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else sweep_tile<COST, true, 1, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
     } else {
-        if (u >= 4) sweep_tile<COST, false, 4>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else if (u == 2) sweep_tile<COST, false, 2>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else sweep_tile<COST, false, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        if (u >= 4) sweep_tile<COST, false, 4, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else if (u == 2) sweep_tile<COST, false, 2, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        else sweep_tile<COST, false, 1, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
     }
 }
 

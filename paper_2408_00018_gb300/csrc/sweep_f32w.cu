@@ -77,17 +77,18 @@ struct WCtx {
     float lo_u, hi_u, sig_u;
     const float *slo, *shi, *ssig;
     int boundary;
-    int uprop;  // 1: uniform redraw of the coordinate (z = u2), 0: Gaussian step
     float neg_T_ln2;
     PhiloxFixed pf;
     const uint32_t* rk;  // Philox round keys (kernel parameters)
 };
 
+// UP: the move is a uniform redraw of the coordinate (z = u2) instead of a Gaussian step.
+template <bool UP>
 __device__ __forceinline__ void wpropose(const WCtx& C, uint32_t s, WStep& p) {
     const uint4 w = philox_step(s, C.pf, C.rk);
     p.d = coord_of(w.x, C.n);
     const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
-    if (C.uprop) {
+    if (UP) {
         p.z = u2;  // uniform redraw: x' = lo + u2 (hi - lo)
     } else {
         // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
@@ -99,14 +100,14 @@ __device__ __forceinline__ void wpropose(const WCtx& C, uint32_t s, WStep& p) {
 }
 
 // Move and energy difference from the chain's current state.
-template <int COST, bool UB>
+template <int COST, bool UB, bool UP>
 __device__ __forceinline__ void wevaluate(const WCtx& C, WStep& p) {
     const int d = p.d;
     const float xo = C.xw[d];
     float lo, hi, sg;
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
-    float xp = C.uprop ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
+    float xp = UP ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
     if (C.boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);
     xp = fminf(fmaxf(xp, lo), hi);
     p.xo = xo;
@@ -148,7 +149,7 @@ struct ChainEnd {
     unsigned nacc;   // accepted moves
 };
 
-template <int COST, bool UB>
+template <int COST, bool UB, bool UP>
 __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int level, float* xw, float* hw,
                                const float* slo, const float* shi, const float* ssig, double* block_hi) {
     const int lane = threadIdx.x & 31;
@@ -238,7 +239,6 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
     C.shi = shi;
     C.ssig = ssig;
     C.boundary = (int)opaque((uint32_t)A.boundary);
-    C.uprop = (int)opaque((uint32_t)A.proposal);
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
     // Round keys in registers for the whole level: reading them from the
     // kernel-parameter bank inside the loop would issue constant loads, which
@@ -262,8 +262,8 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
         const int s = s0 + lane;
         const bool live = s < L;
         WStep p;
-        wpropose(C, (uint32_t)s, p);
-        wevaluate<COST, UB>(C, p);
+        wpropose<UP>(C, (uint32_t)s, p);
+        wevaluate<COST, UB, UP>(C, p);
         // earlier lanes of the group whose step can change what this lane's evaluation read
         unsigned earlier;
         const int key = live ? p.d : -1 - lane;
@@ -292,7 +292,7 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
             __syncwarp();
             const bool go = ((undecided >> lane) & 1u) && (earlier & undecided) == 0u;
             WStep q = p;
-            wevaluate<COST, UB>(C, q);
+            wevaluate<COST, UB, UP>(C, q);
             const bool a2 = q.dF < q.tau;
             if (go) p = q;
             acc = go ? a2 : acc;
@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(kBlock, SA_F32W_MIN_BLOCKS) sweep_f32w_kernel(
     float* shi = slo + n;
     float* ssig = shi + n;
     const bool ub = P.uniform != 0;
+    const bool up = A.proposal == 1;
     if (threadIdx.x == 0) block_acc = 0u;
     if (threadIdx.x < kWarps) block_hi[threadIdx.x] = CUDART_INF;
     if (!ub) {
@@ -392,16 +393,22 @@ __global__ void __launch_bounds__(kBlock, SA_F32W_MIN_BLOCKS) sweep_f32w_kernel(
     if (mine) {
         switch (P.cost) {
         case kSchwefel:
-            end = ub ? warp_chain<kSchwefel, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                     : warp_chain<kSchwefel, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi);
+            end = up ? (ub ? warp_chain<kSchwefel, true, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
+                           : warp_chain<kSchwefel, false, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi))
+                     : (ub ? warp_chain<kSchwefel, true, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
+                           : warp_chain<kSchwefel, false, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi));
             break;
         case kRastrigin:
-            end = ub ? warp_chain<kRastrigin, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                     : warp_chain<kRastrigin, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi);
+            end = up ? (ub ? warp_chain<kRastrigin, true, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
+                           : warp_chain<kRastrigin, false, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi))
+                     : (ub ? warp_chain<kRastrigin, true, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
+                           : warp_chain<kRastrigin, false, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi));
             break;
         case kRosenbrock:
-            end = ub ? warp_chain<kRosenbrock, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                     : warp_chain<kRosenbrock, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi);
+            end = up ? (ub ? warp_chain<kRosenbrock, true, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
+                           : warp_chain<kRosenbrock, false, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi))
+                     : (ub ? warp_chain<kRosenbrock, true, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
+                           : warp_chain<kRosenbrock, false, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi));
             break;
         default:
             if ((threadIdx.x & 31) == 0) A.run->status = 1;
