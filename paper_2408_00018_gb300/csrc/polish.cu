@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cooperative_groups.h>
 #include <math_constants.h>
 
 #include "appendix.cuh"
@@ -488,6 +489,241 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
     }
 }
 
+// ---- Nelder-Mead on a thread-block cluster (separable costs, many coordinates) ----
+//
+// The same method and order of operations as nm_kernel (above), for costs that
+// are sums or products of one-coordinate terms.  One start runs on a cluster of
+// G CTAs (G <= 8, one SM each, so G times the FP64 rate of one SM): CTA r owns the
+// coordinates [r c, (r + 1) c), c = ceil(n / G), of every vertex and of the
+// centroid, reflected and trial points, and keeps its own replica of the vertex
+// values F.  An evaluation of f forms each CTA's partial sum (or product) over its
+// coordinates, writes it into slot r of every CTA's exchange buffer through
+// distributed shared memory, and crosses one cluster barrier; every CTA then
+// combines the G partials in rank order, so all of them hold the same f bit for
+// bit and take the same decisions.  The exchange buffer alternates between two
+// halves, so a CTA that is one evaluation ahead never overwrites a partial a
+// slower CTA has still to read (it cannot pass the next barrier before them).
+namespace cg = cooperative_groups;
+
+constexpr int kNmClusterMax = 8;
+
+__device__ __forceinline__ bool nm_separable(int cost) {
+    return cost == kSchwefel || cost == kRastrigin || cost == kAckley || cost == kCosineMixture ||
+           cost == kExponential || cost == kMichalewicz || cost == kSalomon || cost == kGriewank || cost == kShubert;
+}
+__device__ __forceinline__ bool nm_second_is_product(int cost) { return cost == kGriewank || cost == kShubert; }
+
+// One coordinate's contribution to the cost's two running quantities (a: a sum;
+// b: a second sum, or a product for Griewank and Shubert).
+__device__ __forceinline__ void nm_term(int cost, int i, double x, double& a, double& b) {
+    constexpr double pi = CUDART_PI;
+    switch (cost) {
+    case kSchwefel: a += h64_schwefel(x); break;
+    case kRastrigin: a += g64_rastrigin(x); break;
+    case kAckley: a += x * x; b += cos(6.283185307179586 * x); break;
+    case kCosineMixture: a += x * x; b += cos(5.0 * pi * x); break;
+    case kExponential: case kSalomon: a += x * x; break;
+    case kMichalewicz: a += sin(x) * pow(sin((double)(i + 1) * x * x / pi), 20.0); break;
+    case kGriewank: a += x * x; b *= cos(x / sqrt((double)(i + 1))); break;
+    default: {  // kShubert
+        double s = 0.0;
+        for (int j = 1; j <= 5; ++j) s += (double)j * cos((double)(j + 1) * x + (double)j);
+        b *= s;
+    }
+    }
+}
+
+__device__ __forceinline__ double nm_finish(int cost, int n, double a, double b) {
+    constexpr double pi = CUDART_PI;
+    switch (cost) {
+    case kSchwefel: return -(a / (double)n);
+    case kRastrigin: return 10.0 * (double)n + a;
+    case kAckley: return ackley64(n, a, b);
+    case kCosineMixture: return a - 0.1 * b;
+    case kExponential: return -exp(-0.5 * a);
+    case kMichalewicz: return -a;
+    case kSalomon: { const double r = sqrt(a); return 1.0 - cos(2.0 * pi * r) + 0.1 * r; }
+    case kGriewank: return 1.0 + a / 4000.0 - b;
+    default: return b;  // kShubert
+    }
+}
+
+// The cluster-wide pair (sum of a, sum or product of b) of every CTA's (a, b);
+// pbuf: 2 halves x kNmClusterMax slots x 2 doubles of shared memory; half: the
+// half this exchange uses (alternates).
+__device__ void nm_cluster_reduce(cg::cluster_group& cl, int G, bool prod, double a, double b, double* pbuf,
+                                  int& half, double& A, double& Bv) {
+    double* mine = pbuf + half * 2 * kNmClusterMax;
+    if (threadIdx.x == 0) {
+        const int r = (int)cl.block_rank();
+        for (int q = 0; q < G; ++q) {
+            double* dst = cl.map_shared_rank(mine, q);
+            dst[2 * r] = a;
+            dst[2 * r + 1] = b;
+        }
+    }
+    cl.sync();
+    A = 0.0;
+    Bv = prod ? 1.0 : 0.0;
+    for (int q = 0; q < G; ++q) {
+        A += mine[2 * q];
+        Bv = prod ? Bv * mine[2 * q + 1] : Bv + mine[2 * q + 1];
+    }
+    half ^= 1;
+}
+
+// f at the point whose slice [i0, i0 + cnt) this CTA holds in xs (shared memory).
+__device__ double nm_cluster_cost(cg::cluster_group& cl, int G, int cost, int n, const double* xs, int i0, int cnt,
+                                  double* red, double* pbuf, int& half) {
+    const bool prod = nm_second_is_product(cost);
+    double a = 0.0, b = prod ? 1.0 : 0.0;
+    for (int li = threadIdx.x; li < cnt; li += blockDim.x) nm_term(cost, i0 + li, xs[li], a, b);
+    a = block_sum(a, red);
+    b = prod ? block_prod(b, red) : block_sum(b, red);
+    double A, Bv;
+    nm_cluster_reduce(cl, G, prod, a, b, pbuf, half, A, Bv);
+    return nm_finish(cost, n, A, Bv);
+}
+
+__global__ void __launch_bounds__(256, 1) nm_cluster_kernel(int cost, int n, const double* __restrict__ lo,
+                                                         const double* __restrict__ hi, const double* __restrict__ x0,
+                                                         double* __restrict__ x_out, double* __restrict__ f_out,
+                                                         int* __restrict__ it_out, double step_frac, int max_iter,
+                                                         double ftol, double xtol, double* __restrict__ ws, int G) {
+    extern __shared__ __align__(16) double csm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int w = blockIdx.x / G;  // the start this cluster runs
+    const int t = threadIdx.x, B = blockDim.x, m = n + 1;
+    const int chunk = (n + G - 1) / G;
+    const int i0 = rank * chunk;
+    const int cnt = max(0, min(n, i0 + chunk) - i0);
+    double* F = csm;
+    double* S = F + m;
+    double* xc = S + chunk;
+    double* xr = xc + chunk;
+    double* xt = xr + chunk;
+    double* pbuf = xt + chunk;                 // 2 x kNmClusterMax x 2
+    double* red = pbuf + 4 * kNmClusterMax;   // 32 doubles
+    int* jred = reinterpret_cast<int*>(red + 32);
+    double* V = ws + (size_t)w * (size_t)m * (size_t)n;
+    int half = 0;
+
+    for (int li = t; li < cnt; li += B) {
+        const int i = i0 + li;
+        const double v0 = clipd(x0[(size_t)w * n + i], lo[i], hi[i]);
+        for (int j = 0; j < m; ++j) {
+            double v = v0;
+            if (i == j - 1) {
+                const double d = step_frac * (hi[i] - lo[i]);
+                v = clipd(v + d <= hi[i] ? v + d : v - d, lo[i], hi[i]);
+            }
+            V[(size_t)j * n + i] = v;
+        }
+    }
+    for (int j = 0; j < m; ++j) {
+        for (int li = t; li < cnt; li += B) xt[li] = V[(size_t)j * n + i0 + li];
+        __syncthreads();
+        const double f = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
+        if (t == 0) F[j] = f;
+    }
+    auto resum = [&]() {
+        for (int li = t; li < cnt; li += B) {
+            double a = 0.0;
+            for (int j = 0; j < m; ++j) a += V[(size_t)j * n + i0 + li];
+            S[li] = a;
+        }
+    };
+    resum();
+    __syncthreads();
+
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        double fl, fh, fs;
+        const int l = nm_pick(F, m, true, -1, red, jred, &fl);
+        const int h = nm_pick(F, m, false, -1, red, jred, &fh);
+        const int sw = nm_pick(F, m, false, h, red, jred, &fs);
+        if (l >= m || h < 0 || sw < 0) break;  // only if f is NaN at every vertex
+        if (fh - fl <= ftol * fmax(1.0, fabs(fl))) {
+            double big = 0.0;
+            for (int j = 0; j < m; ++j)
+                for (int li = t; li < cnt; li += B) {
+                    const int i = i0 + li;
+                    if (fabs(V[(size_t)j * n + i] - V[(size_t)l * n + i]) > xtol * (hi[i] - lo[i])) big = 1.0;
+                }
+            big = block_sum(big, red);
+            double A, Bv;
+            nm_cluster_reduce(cl, G, false, big, 0.0, pbuf, half, A, Bv);
+            if (A == 0.0) break;
+        }
+        const double* vh = V + (size_t)h * n + i0;
+        for (int li = t; li < cnt; li += B) {
+            xc[li] = (S[li] - vh[li]) / (double)n;
+            const int i = i0 + li;
+            xr[li] = clipd(xc[li] + (xc[li] - vh[li]), lo[i], hi[i]);
+        }
+        __syncthreads();
+        const double fr = nm_cluster_cost(cl, G, cost, n, xr, i0, cnt, red, pbuf, half);
+        bool accept = false, trial = false;
+        double fa = fr;
+        if (fr < fl) {  // expansion
+            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] + 2.0 * (xr[li] - xc[li]), lo[i0 + li], hi[i0 + li]);
+            __syncthreads();
+            const double fe = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
+            accept = true;
+            if (fe < fr) { fa = fe; trial = true; }
+        } else if (fr < fs) {
+            accept = true;
+        } else if (fr < fh) {  // outside contraction
+            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] + 0.5 * (xr[li] - xc[li]), lo[i0 + li], hi[i0 + li]);
+            __syncthreads();
+            const double fo = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
+            if (fo <= fr) { accept = true; fa = fo; trial = true; }
+        } else {  // inside contraction
+            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] - 0.5 * (xc[li] - vh[li]), lo[i0 + li], hi[i0 + li]);
+            __syncthreads();
+            const double fi = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
+            if (fi < fh) { accept = true; fa = fi; trial = true; }
+        }
+        if (accept) {
+            double* dst = V + (size_t)h * n + i0;
+            for (int li = t; li < cnt; li += B) {
+                const double a = trial ? xt[li] : xr[li];
+                S[li] += a - dst[li];
+                dst[li] = a;
+            }
+            if (t == 0) F[h] = fa;
+            __syncthreads();
+            if ((it + 1) % m == 0) resum();
+        } else {  // shrink towards the best vertex
+            const double* vl = V + (size_t)l * n + i0;
+            for (int j = 0; j < m; ++j) {
+                if (j == l) continue;
+                double* v = V + (size_t)j * n + i0;
+                for (int li = t; li < cnt; li += B) {
+                    const double a = clipd(vl[li] + 0.5 * (v[li] - vl[li]), lo[i0 + li], hi[i0 + li]);
+                    v[li] = a;
+                    xt[li] = a;
+                }
+                __syncthreads();
+                const double f = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
+                if (t == 0) F[j] = f;
+            }
+            resum();
+        }
+        __syncthreads();
+    }
+    double fl;
+    int l = nm_pick(F, m, true, -1, red, jred, &fl);
+    if (l >= m) l = 0;
+    for (int li = t; li < cnt; li += B) x_out[(size_t)w * n + i0 + li] = V[(size_t)l * n + i0 + li];
+    if (rank == 0 && t == 0) {
+        f_out[w] = fl;
+        if (it_out) it_out[w] = it;
+    }
+    cl.sync();  // no CTA leaves while a peer may still address its shared memory
+}
+
 // Top-k of the level's FP64 values (lowest value, then lowest index), one block;
 // destroys the copy it works on by marking winners with +inf.
 __global__ void topk_kernel(double* F, int64_t count, int k, int64_t* idx_out) {
@@ -565,10 +801,50 @@ size_t nm_ws_doubles(int n) { return (size_t)(n + 1) * (size_t)n; }
 
 int nm_max_n() { return kNmMaxN; }
 
+// Costs of one-coordinate terms with at least 128 coordinates run on a cluster of
+// G = min(8, n / 64) CTAs (rounded down to a power of two).
+static int nm_cluster_size(int cost, int n) {
+    const bool sep = cost == kSchwefel || cost == kRastrigin || cost == kAckley || cost == kCosineMixture ||
+                     cost == kExponential || cost == kMichalewicz || cost == kSalomon || cost == kGriewank ||
+                     cost == kShubert;
+    if (!sep || n < 128) return 1;
+    int G = 2;
+    while (G * 2 <= kNmClusterMax && G * 2 * 64 <= n) G *= 2;
+    return G;
+}
+
 cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, const double* table,
                       int table_rows, int k, const double* x0, double* x_out, double* f_out, int* it_out,
                       double step_frac, int max_iter, double ftol, double xtol, double* ws, cudaStream_t s) {
     if (n < 1 || n > kNmMaxN) return cudaErrorInvalidValue;
+    const int G = nm_cluster_size(cost, n);
+    if (G > 1) {
+        const int chunk = (n + G - 1) / G;
+        const int block = std::min(256, std::max(32, (chunk + 31) / 32 * 32));
+        const size_t smem = ((size_t)(n + 1) + 4 * (size_t)chunk + 4 * kNmClusterMax + 32) * sizeof(double) +
+                            32 * sizeof(int);
+        static size_t current_c = 0;  // the limit only grows
+        if (smem > current_c) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(nm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            current_c = smem;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(k * G));
+        cfg.blockDim = dim3((unsigned)block);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)G;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, nm_cluster_kernel, cost, n, lo, hi, x0, x_out, f_out, it_out, step_frac,
+                                  max_iter, ftol, xtol, ws, G);
+    }
     const int block = std::min(1024, std::max(32, (n + 31) / 32 * 32));
     const size_t smem = ((size_t)(n + 1) + 4 * (size_t)n + 32) * sizeof(double) + 32 * sizeof(int);
     static size_t current = 0;  // the limit only grows
