@@ -42,12 +42,14 @@ MUFU_PER_CLK_SM = 16
 SFU_PER_STEP = {"schwefel": 6, "rastrigin": 5, "ackley": 8, "rosenbrock": 4}
 
 
-def sfu_per_step(cost, n):
+def sfu_per_step(cost, n, proposal="gaussian"):
+    # a uniform redraw of the coordinate needs none of the Gaussian step's lg2, sqrt and cos
+    less = 3 if proposal == "uniform" else 0
     if cost == "rot_rastrigin":
-        return n + 4
+        return n + 4 - less
     if cost == "rot_schwefel":
-        return 2 * n + 4
-    return SFU_PER_STEP[cost]
+        return 2 * n + 4 - less
+    return SFU_PER_STEP[cost] - less
 
 
 SWEEP_SOURCES = ["sweep_f32.cu", "sweep_f32w.cu", "sweep_rot.cu", "sa_device.cuh", "sa_internal.h"]
@@ -65,6 +67,12 @@ def parse():
     ap.add_argument("--workload", choices=WORKLOADS, default="schwefel_n256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling runs only)")
+    ap.add_argument("--polish-k", type=int, default=0,
+                    help="the hybrid SA: polish the k best final states by projected gradients after the last "
+                         "level (its time counts in the run; time-to-target may then be reached at the run's end)")
+    ap.add_argument("--proposal", choices=["gaussian", "uniform"], default="gaussian",
+                    help="the move: the workloads' Gaussian step, or the paper's reading (a uniform redraw of the "
+                         "chosen coordinate)")
     ap.add_argument("--independent", action="store_true",
                     help="asynchronous chains (no exchange between levels; the paper's V1), single-problem workloads")
     ap.add_argument("--paper-schwefel", action="store_true",
@@ -83,10 +91,12 @@ def parse():
 class Workload:
     """One workload: how to build its handle and what one run amounts to."""
 
-    def __init__(self, name, levels_override=0, independent=False):
+    def __init__(self, name, levels_override=0, independent=False, proposal="gaussian", polish_k=0):
         from paper_2408_00018_gb300 import inputs
         self.name = name
         self.independent = bool(independent)
+        self.proposal = proposal
+        self.polish_k = int(polish_k)
         if name in ("schwefel_n256", "schwefel_n2") or name in ROT_WORKLOADS:
             if name in ROT_WORKLOADS:
                 cfg = dict(getattr(inputs, ROT_WORKLOADS[name]))
@@ -109,13 +119,15 @@ class Workload:
             self.batch = True
             self.tag = f"batched512_L500_K{self.K}_fp32_autotuned"
         self.steps_per_run = sum(p["chains"] for p in self.problems) * self.L * self.K
-        self.sfu_per_level = sum(p["chains"] * self.L * sfu_per_step(p["cost"], p["n"]) for p in self.problems)
+        self.sfu_per_level = sum(p["chains"] * self.L * sfu_per_step(p["cost"], p["n"], proposal)
+                                 for p in self.problems)
         self.f_star = [inputs.F_STAR.get(p["cost"]) for p in self.problems]
         self.rotated = [p["cost"].startswith("rot_") for p in self.problems]
 
     def schedule(self, sa):
         return sa.Schedule(T0=self.T0, rho=self.rho, levels=self.K, sigma_frac=self.sigma_frac,
-                           precision=self.precision, independent=1 if self.independent else 0)
+                           precision=self.precision, independent=1 if self.independent else 0,
+                           proposal=self.proposal, polish_k=self.polish_k)
 
     def create(self, sa, tune=True):
         if self.batch:
@@ -135,7 +147,9 @@ class Workload:
         return 1 + 2 * rot + self.K * (groups + 2 + rot)
 
     def config(self):
-        c = {"workload": self.tag + ("_async" if self.independent else ""), "L": self.L, "levels": self.K,
+        c = {"workload": self.tag + ("_async" if self.independent else "") +
+                         ("_uniform_moves" if self.proposal == "uniform" else "") +
+                         (f"_polish{self.polish_k}" if self.polish_k else ""), "L": self.L, "levels": self.K,
              "T0": self.T0, "rho": self.rho, "seed": self.seed, "steps_per_run": self.steps_per_run, "argmin": "f64",
              "exchange": "none (asynchronous chains)" if self.independent else "restart from the level's best"}
         if self.batch:
@@ -241,26 +255,34 @@ def traffic_from_profile(workload):
     return d.get("dram_bytes_per_launch")
 
 
-def time_to_target(logs, t_start_ns, f_stars):
-    """Per problem: first level whose incumbent is within 1e-6 max(1, |f*|) of f*."""
+def time_to_target(logs, t_start_ns, f_stars, final_f=None, run_s=None):
+    """Per problem: first level whose incumbent is within 1e-6 max(1, |f*|) of f*; with the
+    hybrid's polish, a problem whose polished incumbent (final_f) is within it counts as
+    reached at the end of the run (run_s, the run's device time)."""
     if any(fs is None for fs in f_stars):
         return {"reached": None, "note": "no closed-form minimum for this cost (rotated Schwefel in a box)"}
-    reached, last_t, gaps = 0, 0.0, []
-    for log, fs in zip(logs, f_stars):
+    reached, last_t, gaps, by_polish = 0, 0.0, [], 0
+    for p, (log, fs) in enumerate(zip(logs, f_stars)):
         tol = 1e-6 * max(1.0, abs(fs))
         hit = [l for l, f in enumerate(log["f_inc"]) if abs(f - fs) <= tol]
         if hit:
             reached += 1
             last_t = max(last_t, (int(log["t_ns"][hit[0]]) - int(t_start_ns)) * 1e-9)
+        elif final_f is not None and abs(final_f[p] - fs) <= tol:
+            reached += 1
+            by_polish += 1
+            last_t = max(last_t, run_s)
         else:
             f_last = float(log["f_inc"][-1])
             gaps.append(abs(f_last - fs) / max(1.0, abs(fs)))
     out = {"reached": reached == len(f_stars), "problems_reached": reached, "problems": len(f_stars),
            "seconds": last_t if reached == len(f_stars) else None}
+    if by_polish:
+        out["reached_by_polish"] = by_polish
     if gaps:
         out["worst_final_rel_gap"] = max(gaps)
         out["median_final_rel_gap"] = statistics.median(gaps)
-    if len(f_stars) == 1 and not gaps:
+    if len(f_stars) == 1 and not gaps and not by_polish:
         out["level"] = next(l for l, f in enumerate(logs[0]["f_inc"])
                             if abs(f - f_stars[0]) <= 1e-6 * max(1.0, abs(f_stars[0])))
     return out
@@ -281,7 +303,7 @@ def oracle_sample(w, budget_steps, threads):
             steps = chains * w.L * levels
         op = oracle.Problem(p["cost"], p["n"], p["lo"], p["hi"], chains=chains, L=w.L, T0=w.T0, rho=w.rho,
                             sigma_frac=w.sigma_frac, seed=w.seed, problem=p_idx, mode=mode, threads=threads,
-                            Q=p.get("Q"), independent=w.independent)
+                            Q=p.get("Q"), independent=w.independent, proposal=w.proposal)
         op.run(levels)
         done += steps
         descr.append(p_idx)
@@ -309,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     sa.load()
-    w = Workload(args.workload, args.levels, args.independent)
+    w = Workload(args.workload, args.levels, args.independent, args.proposal, args.polish_k)
     h = w.create(sa)
     groups = h.describe()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
@@ -347,7 +369,8 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     bests = [h.best(p) for p in range(len(w.problems))]
     logs = [h.level_log(p) for p in range(len(w.problems))]
-    ttt = time_to_target(logs, bests[0][2]["t_start_ns"], w.f_star)
+    ttt = time_to_target(logs, bests[0][2]["t_start_ns"], w.f_star,
+                         final_f=[b[1] for b in bests] if w.polish_k else None, run_s=ms * 1e-3 / args.steps)
 
     t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -367,7 +390,7 @@ def run_ours(args, rank, world, local_rank):
     peak = MUFU_PER_CLK_SM * sms * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "TSFU-op/s (algorithmic SFU ops per Metropolis step: " +
-                        ", ".join(f"{k} {v}" for k, v in SFU_PER_STEP.items()) + ")",
+                        ", ".join(f"{k} {sfu_per_step(k, 1, w.proposal)}" for k in SFU_PER_STEP) + ")",
                 "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(args.workload),
                 "kernel": "sweep (" + ", ".join(g["kind"] for g in groups) + ")",
                 "launch_ms": round(sweep_avg, 4),
@@ -421,7 +444,7 @@ def run_ours(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = Workload(args.workload, args.levels, args.independent)
+    w = Workload(args.workload, args.levels, args.independent, args.proposal, args.polish_k)
     threads = os.cpu_count() or 1
     budget = 6.5e7 / (w.problems[0]["n"] / 4 if any(w.rotated) else 1)
     for _ in range(args.warmup):
