@@ -103,7 +103,7 @@ def lib():
             L.sao_level_chains.restype = ctypes.c_int
             L.sao_pgd.argtypes = [i32, i32, vp, vp, vp, vp, i32, f64, f64, i32, vp, vp]
             L.sao_pgd.restype = ctypes.c_int
-            L.sao_nelder_mead.argtypes = [i32, i32, vp, vp, vp, vp, i32, vp, f64, i32, f64, f64, vp, vp]
+            L.sao_nelder_mead.argtypes = [i32, i32, vp, vp, vp, vp, i32, vp, f64, i32, f64, f64, i32, vp, vp]
             L.sao_nelder_mead.restype = ctypes.c_int
             L.sao_crossover_sources.argtypes = [ctypes.POINTER(Cfg), i32, vp, i64, vp]
             L.sao_crossover_sources.restype = ctypes.c_int
@@ -332,8 +332,8 @@ def pgd(name_or_id, x0, lo, hi, Q=None, max_iter=1000, tol=1e-10, armijo_c=1e-4,
 
 
 def nelder_mead(name_or_id, x0, lo, hi, Q=None, step_frac=0.05, max_iter=20000, ftol=1e-12, xtol=1e-10,
-                table=None):
-    """Nelder-Mead with box clipping from x0; returns (x, f, iterations)."""
+                table=None, adaptive=False):
+    """Nelder-Mead with box clipping from x0 (adaptive: Gao & Han's coefficients); returns (x, f, iterations)."""
     cid = COSTS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
     x = np.array(x0, np.float64)
     n = x.size
@@ -344,7 +344,7 @@ def nelder_mead(name_or_id, x0, lo, hi, Q=None, step_frac=0.05, max_iter=20000, 
     it = np.zeros(1, np.int32)
     t, rows = _table(table)
     rc = lib().sao_nelder_mead(cid, n, _p(lo), _p(hi), _p(Qa), _p(t), rows, _p(x), step_frac, max_iter, ftol, xtol,
-                               _p(f), _p(it))
+                               1 if adaptive else 0, _p(f), _p(it))
     if rc != 0:
         raise ValueError("sao_nelder_mead failed")
     return x, float(f[0]), int(it[0])

@@ -864,7 +864,12 @@ int sao_pgd(int32_t cost, int32_t n, const double* lo, const double* hi, const d
 /* ------------------------------------------------------------------------ */
 /* Nelder-Mead (the paper's local minimiser of the hybrid SA, Sec. 4.2 and    */
 /* Table 10), in the standard form of Lagarias, Reeds, Wright & Wright (SIAM  */
-/* J. Optim. 1998): reflection 1, expansion 2, contraction 1/2, shrink 1/2.  */
+/* J. Optim. 1998): reflection rho = 1, expansion chi = 2, contraction        */
+/* psi = 1/2, shrink sigma = 1/2; every trial point is formed from the        */
+/* centroid c and the worst vertex v_h (c + rho (c - v_h), c + rho chi        */
+/* (c - v_h), c + psi rho (c - v_h), c - psi (c - v_h)).  adaptive: the       */
+/* dimension-dependent coefficients of Gao & Han (Comput. Optim. Appl. 2012),  */
+/* chi = 1 + 2/n, psi = 3/4 - 1/(2n), sigma = 1 - 1/n.                         */
 /* Box constraints: every trial point is clipped into the box.  Vertices are */
 /* ordered by (f, slot); the initial simplex is x0 and x0 + delta_k e_k,     */
 /* delta_k = step_frac (u_k - l_k) (or minus, if that leaves the box).       */
@@ -878,8 +883,12 @@ static void nm_clip(int n, const double* lo, const double* hi, double* x) {
 
 int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
                     const double* table, int32_t rows, double* x, double step_frac, int32_t max_iter, double ftol,
-                    double xtol, double* f_out, int32_t* iters_out) {
+                    double xtol, int32_t adaptive, double* f_out, int32_t* iters_out) {
     const int m = n + 1;
+    const double rho = 1.0;
+    const double chi = adaptive ? 1.0 + 2.0 / (double)n : 2.0;
+    const double psi = adaptive ? 0.75 - 1.0 / (2.0 * (double)n) : 0.5;
+    const double sig = adaptive ? 1.0 - 1.0 / (double)n : 0.5;
     double* V = (double*)malloc(sizeof(double) * (size_t)m * n);
     double* F = (double*)malloc(sizeof(double) * (size_t)m);
     double* xc = (double*)malloc(sizeof(double) * (size_t)n);
@@ -928,14 +937,14 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
             xc[i] = a / (double)n;
         }
         const double* vh = V + (size_t)h * n;
-        for (int i = 0; i < n; ++i) xr[i] = xc[i] + (xc[i] - vh[i]);
+        for (int i = 0; i < n; ++i) xr[i] = xc[i] + rho * (xc[i] - vh[i]);
         nm_clip(n, lo, hi, xr);
         const double fr = sao_cost_tab(cost, n, xr, Q, table, rows, yw);
         int accept = 0;
         double fa = fr;
         const double* xa = xr;
         if (fr < F[l]) {
-            for (int i = 0; i < n; ++i) xt[i] = xc[i] + 2.0 * (xr[i] - xc[i]);
+            for (int i = 0; i < n; ++i) xt[i] = xc[i] + rho * chi * (xc[i] - vh[i]);
             nm_clip(n, lo, hi, xt);
             const double fe = sao_cost_tab(cost, n, xt, Q, table, rows, yw);
             accept = 1;
@@ -943,12 +952,12 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
         } else if (fr < F[sw]) {
             accept = 1;
         } else if (fr < F[h]) {
-            for (int i = 0; i < n; ++i) xt[i] = xc[i] + 0.5 * (xr[i] - xc[i]);
+            for (int i = 0; i < n; ++i) xt[i] = xc[i] + psi * rho * (xc[i] - vh[i]);
             nm_clip(n, lo, hi, xt);
             const double fo = sao_cost_tab(cost, n, xt, Q, table, rows, yw);
             if (fo <= fr) { accept = 1; fa = fo; xa = xt; }
         } else {
-            for (int i = 0; i < n; ++i) xt[i] = xc[i] - 0.5 * (xc[i] - vh[i]);
+            for (int i = 0; i < n; ++i) xt[i] = xc[i] - psi * (xc[i] - vh[i]);
             nm_clip(n, lo, hi, xt);
             const double fi = sao_cost_tab(cost, n, xt, Q, table, rows, yw);
             if (fi < F[h]) { accept = 1; fa = fi; xa = xt; }
@@ -961,7 +970,7 @@ int sao_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi,
             for (int j = 0; j < m; ++j) {
                 if (j == l) continue;
                 double* v = V + (size_t)j * n;
-                for (int i = 0; i < n; ++i) v[i] = vl[i] + 0.5 * (v[i] - vl[i]);
+                for (int i = 0; i < n; ++i) v[i] = vl[i] + sig * (v[i] - vl[i]);
                 nm_clip(n, lo, hi, v);
                 F[j] = sao_cost_tab(cost, n, v, Q, table, rows, yw);
             }

@@ -29,7 +29,9 @@ def _simplex(x0, lo, hi, step_frac):
     ("rastrigin", 3, 0.6, 5.0, [0.7, 0.9, 1.3], 50),  # clipping at the face x = 0.6 is active
     ("ackley", 5, -32.768, 32.768, [0.5, -0.3, 0.2, 0.1, -0.4], 80),
 ])
-def test_matches_scipy_nelder_mead_iteration_for_iteration(cost, n, lo, hi, x0, iters):
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_matches_scipy_nelder_mead_iteration_for_iteration(cost, n, lo, hi, x0, iters, adaptive):
+    """Standard coefficients, and Gao & Han's adaptive ones (scipy's adaptive=True)."""
     scipy_opt = pytest.importorskip("scipy.optimize")
     lo_v, hi_v = np.full(n, lo), np.full(n, hi)
     x0 = np.array(x0, np.float64)
@@ -38,10 +40,11 @@ def test_matches_scipy_nelder_mead_iteration_for_iteration(cost, n, lo, hi, x0, 
     ref = scipy_opt.minimize(f, x0, method="Nelder-Mead", bounds=list(zip(lo_v, hi_v)),
                              # scipy's iteration counter starts at 1: maxiter = iters + 1 runs `iters` iterations
                              options=dict(initial_simplex=_simplex(x0, lo_v, hi_v, step), maxiter=iters + 1,
-                                          xatol=0.0, fatol=0.0, adaptive=False))
-    x, fx, it = oracle.nelder_mead(cost, x0, lo_v, hi_v, step_frac=step, max_iter=iters, ftol=-1.0)
+                                          xatol=0.0, fatol=0.0, adaptive=adaptive))
+    x, fx, it = oracle.nelder_mead(cost, x0, lo_v, hi_v, step_frac=step, max_iter=iters, ftol=-1.0, adaptive=adaptive)
     assert it == iters
-    # the two differ only in the order the centroid is summed in (sorted vs slot order)
+    # the two differ only in rounding: the centroid's summation order (sorted vs slot order)
+    # and the trial points' form ((1 + a) c - a v_h there, c + a (c - v_h) here)
     assert np.allclose(x, ref.x, rtol=1e-9, atol=1e-9 * (hi - lo)), (x, ref.x)
     assert abs(fx - ref.fun) <= 1e-9 * max(1.0, abs(ref.fun))
 
