@@ -507,7 +507,7 @@ def run_hybrid(args):
                "data": "synthetic", "n_gpus": 1,
                "sa": {"chains": HYBRID_CHAINS, "L": HYBRID_L, "levels": K, "T0": T0, "rho": rho,
                       "steps": HYBRID_CHAINS * HYBRID_L * K, "s": t_sa, "err": abs(f_sa - fstar)}}
-        for method in ("pgd", "nelder_mead"):
+        for method in ("pgd", "nelder_mead", "nelder_mead_adaptive"):
             t, x, f = timed(sa.Schedule(**base, polish_k=HYBRID_K, polish_method=method), cost, lo, hi, n)
             out[method] = {"starts": HYBRID_K, "s": t, "polish_s": t - t_sa, "err": abs(f - fstar)}
         T = T0
@@ -521,6 +521,11 @@ def run_hybrid(args):
         dt = time.perf_counter() - t
         out["nelder_mead_from_best"] = {"s": dt, "iters": int(it1[0]), "us_per_iter": 1e6 * dt / max(1, int(it1[0])),
                                         "err": abs(float(f1[0]) - fstar)}
+        t = time.perf_counter()
+        _, f2, it2 = sa.nelder_mead(cost, x_sa[None], lo, hi, step_frac=step, max_iter=200 * (n + 1),
+                                    ftol=1e-12, xtol=1e-10, adaptive=True)
+        dt = time.perf_counter() - t
+        out["nelder_mead_adaptive_from_best"] = {"s": dt, "iters": int(it2[0]), "err": abs(float(f2[0]) - fstar)}
         print(json.dumps(out), flush=True)
 
 

@@ -81,7 +81,8 @@ typedef enum {
 
 enum { SA_REFLECT = 0, SA_CLIP = 1 };                 /* box handling of a move */
 enum { SA_FP64 = 0, SA_FP32 = 1, SA_MIXED_BF16 = 2 }; /* arithmetic of the sweep */
-enum { SA_POLISH_PGD = 0, SA_POLISH_NELDER_MEAD = 1 };  /* local minimiser of the hybrid SA */
+/* local minimiser of the hybrid SA (the adaptive Nelder-Mead: Gao & Han's coefficients) */
+enum { SA_POLISH_PGD = 0, SA_POLISH_NELDER_MEAD = 1, SA_POLISH_NELDER_MEAD_ADAPTIVE = 2 };
 /* Move of the selected coordinate (Sec. 2.1 Step 2: "a random number to modify the selected
  * coordinate"): a Gaussian step sigma_frac (u_d - l_d) sqrt(T / T0) z (Box-Muller, cosine
  * branch, then the box rule), or a uniform redraw x_d' = l_d + u2 (u_d - l_d) with the
@@ -125,7 +126,7 @@ typedef struct {
     int32_t exchange_every; /* m > 1: synchronous exchange only after levels m-1, 2m-1, ...; the
                                chains continue their own states in between (0 or 1: every level) */
     int32_t polish_method;  /* SA_POLISH_PGD: sa_polish (max_iter 1000, tol 1e-10);
-                               SA_POLISH_NELDER_MEAD: sa_nelder_mead with step_frac = sigma_frac
+                               SA_POLISH_NELDER_MEAD(_ADAPTIVE): sa_nelder_mead with step_frac = sigma_frac
                                sqrt(T_last / T0) (the last level's step scale), max_iter
                                200 (n + 1), ftol 1e-12, xtol 1e-10 (n <= 4096) */
     int32_t proposal;       /* SA_PROPOSAL_GAUSSIAN (the default) or SA_PROPOSAL_UNIFORM (not with
@@ -370,8 +371,10 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
  * Nelder-Mead, the local minimiser of the paper's hybrid SA (Sec. 4.2, Table
  * 10), in the standard form (Lagarias, Reeds, Wright & Wright, SIAM J. Optim.
  * 1998): reflection 1, expansion 2, outside and inside contraction 1/2,
- * shrink 1/2 towards the best vertex; every trial point is clipped into the
- * box.  From each of k start points x0[j*n .. j*n+n) (host) the simplex is
+ * shrink 1/2 towards the best vertex -- or, with adaptive = 1, Gao & Han's
+ * dimension-dependent coefficients (expansion 1 + 2/n, contractions
+ * 3/4 - 1/(2n), shrink 1 - 1/n).  Every trial point is c + a (c - v_h) for the
+ * centroid c and the worst vertex v_h, clipped into the box.  From each of k start points x0[j*n .. j*n+n) (host) the simplex is
  * x0 and x0 + delta_i e_i, delta_i = step_frac (u_i - l_i) (minus that if plus
  * leaves the box); vertices rank by (f, slot) -- best = lowest f, then lowest
  * slot; worst and second worst = highest f, then highest slot.  Stops when
@@ -388,14 +391,14 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
  * implementation by rounding there as well as in f.
  * Errors: SA_EINVAL on n < 1 or n > 4096, k not in [1, 1024], a bad box,
  * step_frac not in (0, 1], max_iter < 0, ftol or xtol negative or NaN, a NULL
- * array, Q or the table missing where the cost needs it (or given where it
+ * array, adaptive not 0 or 1, Q or the table missing where the cost needs it (or given where it
  * does not), a non-finite Q or table entry, n != 2 for a two-variable test, or
  * a workspace above 4 GiB; SA_ENOMEM; SA_ECUDA.
  */
 sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
                          const double* table, int32_t table_rows, int32_t k, const double* x0, double step_frac,
-                         int32_t max_iter, double ftol, double xtol, double* x_out, double* f_out,
-                         int32_t* iters_out, void* stream);
+                         int32_t max_iter, double ftol, double xtol, int32_t adaptive, double* x_out,
+                         double* f_out, int32_t* iters_out, void* stream);
 
 /*
  * Kernel-level entry point: tensor-core GEMM D = A . B^T with A [M x K] and

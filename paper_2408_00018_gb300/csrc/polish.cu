@@ -206,6 +206,14 @@ __global__ void pgd_kernel(int cost, int n, const double* __restrict__ lo, const
 constexpr int kNmMaxN = 4096;
 constexpr int kNmExactN = 64;
 
+// Trial-point coefficients: reflection c + r (c - v_h), expansion c + e (c - v_h),
+// outside contraction c + o (c - v_h), inside contraction c - i (c - v_h), shrink
+// v_l + s (v - v_l).  Standard: r = 1, e = 2, o = i = s = 1/2; adaptive (Gao & Han):
+// e = 1 + 2/n, o = i = 3/4 - 1/(2n), s = 1 - 1/n.
+struct NmCoef {
+    double r, e, o, i, s;
+};
+
 __device__ __forceinline__ double clipd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
 
 // (f, slot) order: true when (fa, a) ranks below (fb, b)
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
                                                   const double* __restrict__ x0, double* __restrict__ x_out,
                                                   double* __restrict__ f_out, int* __restrict__ it_out,
                                                   double step_frac, int max_iter, double ftol, double xtol,
-                                                  double* __restrict__ ws) {
+                                                  double* __restrict__ ws, NmCoef K) {
     extern __shared__ __align__(16) double nsm[];
     const int t = threadIdx.x, B = blockDim.x, w = blockIdx.x, m = n + 1;
     double* F = nsm;
@@ -426,14 +434,14 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
                 a = S[i] - vh[i];
             }
             xc[i] = a / (double)n;
-            xr[i] = clipd(xc[i] + (xc[i] - vh[i]), lo[i], hi[i]);
+            xr[i] = clipd(xc[i] + K.r * (xc[i] - vh[i]), lo[i], hi[i]);
         }
         __syncthreads();
         const double fr = bcost(cost, n, xr, QT, table, rows, red);
         bool accept = false, trial = false;
         double fa = fr;
         if (fr < fl) {  // expansion
-            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + 2.0 * (xr[i] - xc[i]), lo[i], hi[i]);
+            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + K.e * (xc[i] - vh[i]), lo[i], hi[i]);
             __syncthreads();
             const double fe = bcost(cost, n, xt, QT, table, rows, red);
             accept = true;
@@ -441,12 +449,12 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
         } else if (fr < fs) {
             accept = true;
         } else if (fr < fh) {  // outside contraction
-            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + 0.5 * (xr[i] - xc[i]), lo[i], hi[i]);
+            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] + K.o * (xc[i] - vh[i]), lo[i], hi[i]);
             __syncthreads();
             const double fo = bcost(cost, n, xt, QT, table, rows, red);
             if (fo <= fr) { accept = true; fa = fo; trial = true; }
         } else {  // inside contraction
-            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] - 0.5 * (xc[i] - vh[i]), lo[i], hi[i]);
+            for (int i = t; i < n; i += B) xt[i] = clipd(xc[i] - K.i * (xc[i] - vh[i]), lo[i], hi[i]);
             __syncthreads();
             const double fi = bcost(cost, n, xt, QT, table, rows, red);
             if (fi < fh) { accept = true; fa = fi; trial = true; }
@@ -467,7 +475,7 @@ __global__ void __launch_bounds__(1024) nm_kernel(int cost, int n, const double*
                 if (j == l) continue;
                 double* v = V + (size_t)j * n;
                 for (int i = t; i < n; i += B) {
-                    const double a = clipd(vl[i] + 0.5 * (v[i] - vl[i]), lo[i], hi[i]);
+                    const double a = clipd(vl[i] + K.s * (v[i] - vl[i]), lo[i], hi[i]);
                     v[i] = a;
                     xt[i] = a;
                 }
@@ -589,7 +597,8 @@ __global__ void __launch_bounds__(256, 1) nm_cluster_kernel(int cost, int n, con
                                                          const double* __restrict__ hi, const double* __restrict__ x0,
                                                          double* __restrict__ x_out, double* __restrict__ f_out,
                                                          int* __restrict__ it_out, double step_frac, int max_iter,
-                                                         double ftol, double xtol, double* __restrict__ ws, int G) {
+                                                         double ftol, double xtol, double* __restrict__ ws, int G,
+                                                         NmCoef K) {
     extern __shared__ __align__(16) double csm[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -660,14 +669,14 @@ __global__ void __launch_bounds__(256, 1) nm_cluster_kernel(int cost, int n, con
         for (int li = t; li < cnt; li += B) {
             xc[li] = (S[li] - vh[li]) / (double)n;
             const int i = i0 + li;
-            xr[li] = clipd(xc[li] + (xc[li] - vh[li]), lo[i], hi[i]);
+            xr[li] = clipd(xc[li] + K.r * (xc[li] - vh[li]), lo[i], hi[i]);
         }
         __syncthreads();
         const double fr = nm_cluster_cost(cl, G, cost, n, xr, i0, cnt, red, pbuf, half);
         bool accept = false, trial = false;
         double fa = fr;
         if (fr < fl) {  // expansion
-            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] + 2.0 * (xr[li] - xc[li]), lo[i0 + li], hi[i0 + li]);
+            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] + K.e * (xc[li] - vh[li]), lo[i0 + li], hi[i0 + li]);
             __syncthreads();
             const double fe = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
             accept = true;
@@ -675,12 +684,12 @@ __global__ void __launch_bounds__(256, 1) nm_cluster_kernel(int cost, int n, con
         } else if (fr < fs) {
             accept = true;
         } else if (fr < fh) {  // outside contraction
-            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] + 0.5 * (xr[li] - xc[li]), lo[i0 + li], hi[i0 + li]);
+            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] + K.o * (xc[li] - vh[li]), lo[i0 + li], hi[i0 + li]);
             __syncthreads();
             const double fo = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
             if (fo <= fr) { accept = true; fa = fo; trial = true; }
         } else {  // inside contraction
-            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] - 0.5 * (xc[li] - vh[li]), lo[i0 + li], hi[i0 + li]);
+            for (int li = t; li < cnt; li += B) xt[li] = clipd(xc[li] - K.i * (xc[li] - vh[li]), lo[i0 + li], hi[i0 + li]);
             __syncthreads();
             const double fi = nm_cluster_cost(cl, G, cost, n, xt, i0, cnt, red, pbuf, half);
             if (fi < fh) { accept = true; fa = fi; trial = true; }
@@ -701,7 +710,7 @@ __global__ void __launch_bounds__(256, 1) nm_cluster_kernel(int cost, int n, con
                 if (j == l) continue;
                 double* v = V + (size_t)j * n + i0;
                 for (int li = t; li < cnt; li += B) {
-                    const double a = clipd(vl[li] + 0.5 * (v[li] - vl[li]), lo[i0 + li], hi[i0 + li]);
+                    const double a = clipd(vl[li] + K.s * (v[li] - vl[li]), lo[i0 + li], hi[i0 + li]);
                     v[li] = a;
                     xt[li] = a;
                 }
@@ -815,8 +824,16 @@ static int nm_cluster_size(int cost, int n) {
 
 cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, const double* table,
                       int table_rows, int k, const double* x0, double* x_out, double* f_out, int* it_out,
-                      double step_frac, int max_iter, double ftol, double xtol, double* ws, cudaStream_t s) {
+                      double step_frac, int max_iter, double ftol, double xtol, bool adaptive, double* ws,
+                      cudaStream_t s) {
     if (n < 1 || n > kNmMaxN) return cudaErrorInvalidValue;
+    NmCoef K;
+    const double dn = (double)n;
+    K.r = 1.0;
+    K.e = adaptive ? 1.0 + 2.0 / dn : 2.0;
+    K.o = adaptive ? 0.75 - 1.0 / (2.0 * dn) : 0.5;
+    K.i = K.o;
+    K.s = adaptive ? 1.0 - 1.0 / dn : 0.5;
     const int G = nm_cluster_size(cost, n);
     if (G > 1) {
         const int chunk = (n + G - 1) / G;
@@ -843,7 +860,7 @@ cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, nm_cluster_kernel, cost, n, lo, hi, x0, x_out, f_out, it_out, step_frac,
-                                  max_iter, ftol, xtol, ws, G);
+                                  max_iter, ftol, xtol, ws, G, K);
     }
     const int block = std::min(1024, std::max(32, (n + 31) / 32 * 32));
     const size_t smem = ((size_t)(n + 1) + 4 * (size_t)n + 32) * sizeof(double) + 32 * sizeof(int);
@@ -854,7 +871,7 @@ cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const
         current = smem;
     }
     nm_kernel<<<k, block, smem, s>>>(cost, n, lo, hi, QT, table, table_rows, x0, x_out, f_out, it_out, step_frac,
-                                     max_iter, ftol, xtol, ws);
+                                     max_iter, ftol, xtol, ws, K);
     return cudaGetLastError();
 }
 

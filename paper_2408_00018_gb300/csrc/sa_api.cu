@@ -199,7 +199,9 @@ sa_status check_schedule(const sa_schedule* s) {
     if (s->boundary != SA_REFLECT && s->boundary != SA_CLIP) return SA_EINVAL;
     if (s->precision != SA_FP64 && s->precision != SA_FP32) return SA_EINVAL;
     if ((s->surrogate != 0 && s->surrogate != 1) || s->polish_k < 0 || s->polish_k > 1024) return SA_EINVAL;
-    if (s->polish_method != SA_POLISH_PGD && s->polish_method != SA_POLISH_NELDER_MEAD) return SA_EINVAL;
+    if (s->polish_method != SA_POLISH_PGD && s->polish_method != SA_POLISH_NELDER_MEAD &&
+        s->polish_method != SA_POLISH_NELDER_MEAD_ADAPTIVE)
+        return SA_EINVAL;
     if ((s->proposal != SA_PROPOSAL_GAUSSIAN && s->proposal != SA_PROPOSAL_UNIFORM) ||
         (s->proposal == SA_PROPOSAL_UNIFORM && s->surrogate))
         return SA_EINVAL;
@@ -222,7 +224,7 @@ sa_status check_problem(const sa_problem& pr, const sa_box& box, int32_t n, int6
     if (is_appendix(pr.cost) && sch.precision != SA_FP64) return SA_EINVAL;
     // no gradient is written for the Appendix's other tests: they polish with Nelder-Mead
     if (is_appendix(pr.cost) && sch.polish_k > 0 && sch.polish_method == SA_POLISH_PGD) return SA_EINVAL;
-    if (sch.polish_k > 0 && sch.polish_method == SA_POLISH_NELDER_MEAD && n > nm_max_n()) return SA_EINVAL;
+    if (sch.polish_k > 0 && sch.polish_method != SA_POLISH_PGD && n > nm_max_n()) return SA_EINVAL;
     for (int k = 0; k < n; ++k)
         if (!std::isfinite(box.lo[k]) || !std::isfinite(box.hi[k]) || box.lo[k] > box.hi[k]) return SA_EINVAL;
     return SA_OK;
@@ -423,10 +425,10 @@ sa_status run_polish(sa_handle* h) {
             launch_topk(h->d_Fcopy, hp.chains, k, h->d_topk, h->stream) != cudaSuccess ||
             launch_gather(h->d_X32, h->d_X64, hp.x_base, hp.chains, hp.n, h->d_topk, k, h->d_px0, h->stream) !=
                 cudaSuccess ||
-            (h->sch.polish_method == SA_POLISH_NELDER_MEAD
+            (h->sch.polish_method != SA_POLISH_PGD
                  ? launch_nm(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.qt64, hp.dev.table, hp.dev.table_rows, k,
-                             h->d_px0, h->d_px, h->d_pf, h->d_pit,
-                             h->nm_step, 200 * (hp.n + 1), 1e-12, 1e-10, h->d_nmws, h->stream)
+                             h->d_px0, h->d_px, h->d_pf, h->d_pit, h->nm_step, 200 * (hp.n + 1), 1e-12, 1e-10,
+                             h->sch.polish_method == SA_POLISH_NELDER_MEAD_ADAPTIVE, h->d_nmws, h->stream)
                  : launch_pgd(hp.cost, hp.n, hp.dev.lo, hp.dev.hi, hp.dev.q64, k, h->d_px0, h->d_px, h->d_pf,
                               h->d_pit, 1000, 1e-10, h->stream)) != cudaSuccess ||
             launch_polish_update(h->d_probs, (int)p, h->d_px, h->d_pf, k, h->stream) != cudaSuccess)
@@ -763,7 +765,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
             (st = dalloc(h, &h->d_px0, k * n_max)) || (st = dalloc(h, &h->d_px, k * n_max)) ||
             (st = dalloc(h, &h->d_pf, k)) || (st = dalloc(h, &h->d_pit, k)))
             return st;
-        if (h->sch.polish_method == SA_POLISH_NELDER_MEAD) {
+        if (h->sch.polish_method != SA_POLISH_PGD) {
             if (n_max > nm_max_n() || k * nm_ws_doubles(n_max) * sizeof(double) > ((size_t)1 << 32)) return SA_EINVAL;
             if ((st = dalloc(h, &h->d_nmws, k * nm_ws_doubles(n_max)))) return st;
             h->nm_step = std::min(1.0, h->sch.sigma_frac * s.back());  // s[l] = sqrt(T_l / T0)
@@ -1019,8 +1021,9 @@ sa_status sa_polish(int32_t cost, int32_t n, const double* lo, const double* hi,
 
 sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double* hi, const double* Q,
                          const double* table, int32_t table_rows, int32_t k, const double* x0, double step_frac,
-                         int32_t max_iter, double ftol, double xtol, double* x_out, double* f_out,
-                         int32_t* iters_out, void* stream) {
+                         int32_t max_iter, double ftol, double xtol, int32_t adaptive, double* x_out,
+                         double* f_out, int32_t* iters_out, void* stream) {
+    if (adaptive != 0 && adaptive != 1) return SA_EINVAL;
     if (n < 1 || k < 1 || k > 1024 || !lo || !hi || !x0 || !x_out || !f_out || max_iter < 0 || !(ftol >= 0.0) ||
         !(xtol >= 0.0) || !(step_frac > 0.0 && step_frac <= 1.0))
         return SA_EINVAL;
@@ -1055,8 +1058,8 @@ sa_status sa_nelder_mead(int32_t cost, int32_t n, const double* lo, const double
          cudaMemcpyAsync(dhi, hi, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
          cudaMemcpyAsync(dx0, x0, kn * sizeof(double), cudaMemcpyHostToDevice, s) ||
          (tn && cudaMemcpyAsync(dtab, table, tn * sizeof(double), cudaMemcpyHostToDevice, s)) ||
-         launch_nm(cost, n, dlo, dhi, dq, dtab, table_rows, k, dx0, dx, df, dit, step_frac, max_iter, ftol, xtol, dws,
-                   s) ||
+         launch_nm(cost, n, dlo, dhi, dq, dtab, table_rows, k, dx0, dx, df, dit, step_frac, max_iter, ftol, xtol,
+                   adaptive != 0, dws, s) ||
          cudaMemcpyAsync(x_out, dx, kn * sizeof(double), cudaMemcpyDeviceToHost, s) ||
          cudaMemcpyAsync(f_out, df, k * sizeof(double), cudaMemcpyDeviceToHost, s) ||
          (iters_out && cudaMemcpyAsync(iters_out, dit, k * sizeof(int), cudaMemcpyDeviceToHost, s)) ||

@@ -167,7 +167,8 @@ size_t nm_ws_doubles(int n);
 int nm_max_n();
 cudaError_t launch_nm(int cost, int n, const double* lo, const double* hi, const double* QT, const double* table,
                       int table_rows, int k, const double* x0, double* x_out, double* f_out, int* it_out,
-                      double step_frac, int max_iter, double ftol, double xtol, double* ws, cudaStream_t s);
+                      double step_frac, int max_iter, double ftol, double xtol, bool adaptive, double* ws,
+                      cudaStream_t s);
 cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStream_t s);
 cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
                                  int* status, cudaStream_t s);

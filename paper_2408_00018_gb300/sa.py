@@ -23,7 +23,7 @@ COSTS = {"schwefel": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "rot_rastr
          "michalewicz": 16, "salomon": 17, "six_hump_camel": 18, "shubert": 19, "shekel": 20, "foxholes": 21}
 BOUNDARY = {"reflect": 0, "clip": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_bf16": 2}
-POLISH = {"pgd": 0, "nelder_mead": 1}
+POLISH = {"pgd": 0, "nelder_mead": 1, "nelder_mead_adaptive": 2}
 PROPOSAL = {"gaussian": 0, "uniform": 1}
 
 
@@ -96,7 +96,8 @@ SIGNATURES = {
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_philox_fill": (ctypes.c_int, [_U32, _U32, _U32, _U32, _U32, _U32, _I64, _V, _V]),
     "sa_polish": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _I32, _V, _I32, _D, _V, _V, _V, _V]),
-    "sa_nelder_mead": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _V, _I32, _I32, _V, _D, _I32, _D, _D, _V, _V, _V, _V]),
+    "sa_nelder_mead": (ctypes.c_int, [_I32, _I32, _V, _V, _V, _V, _I32, _I32, _V, _D, _I32, _D, _D, _I32, _V, _V, _V,
+                                      _V]),
     "sa_gemm_bf16": (ctypes.c_int, [_V, _I32, _V, _I32, _V, _I32, _I32, _I32, _I32, _V, _V]),
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
@@ -415,7 +416,7 @@ def polish(cost, x0, lo, hi, max_iter: int = 1000, tol: float = 1e-10, Q=None, s
 
 
 def nelder_mead(cost, x0, lo, hi, step_frac: float = 0.05, max_iter: int = 20000, ftol: float = 1e-12,
-                xtol: float = 1e-10, Q=None, stream=None, table=None):
+                xtol: float = 1e-10, Q=None, stream=None, table=None, adaptive: bool = False):
     """sa_nelder_mead: Nelder-Mead with box clipping from each row of x0 (k x n); returns (x, f, iters).
     Rotated costs take Q (n x n); Tests 11, 18 and 19 take table."""
     x0 = np.ascontiguousarray(np.atleast_2d(np.asarray(x0, np.float64)))
@@ -431,7 +432,8 @@ def nelder_mead(cost, x0, lo, hi, step_frac: float = 0.05, max_iter: int = 20000
     _check(load().sa_nelder_mead(COSTS[cost] if isinstance(cost, str) else int(cost), n, lo.ctypes.data,
                                  hi.ctypes.data, None if Qa is None else Qa.ctypes.data,
                                  None if tab is None else tab.ctypes.data, rows, k, x0.ctypes.data, step_frac,
-                                 max_iter, ftol, xtol, x.ctypes.data, f.ctypes.data, it.ctypes.data, s),
+                                 max_iter, ftol, xtol, 1 if adaptive else 0, x.ctypes.data, f.ctypes.data,
+                                 it.ctypes.data, s),
            "sa_nelder_mead")
     return x, f, it
 
