@@ -75,6 +75,9 @@ def parse():
                          "chosen coordinate)")
     ap.add_argument("--independent", action="store_true",
                     help="asynchronous chains (no exchange between levels; the paper's V1), single-problem workloads")
+    ap.add_argument("--gemm-route", action="store_true",
+                    help="time the rotated costs' GEMM route at the rotated Rastrigin n = 1024 workload's shape "
+                         "(every step's candidates Y' = X' Q^T on the tensor cores) against the rank-1 sweep")
     ap.add_argument("--paper-schwefel", action="store_true",
                     help="the paper's Schwefel accuracy and timing tables instead (T0 = 1000, rho = 0.99, 1146 levels "
                          "of N = 100, 16384 chains, n = 8 .. 512, uniform redraw moves): V2 and V1 per n")
@@ -529,6 +532,70 @@ def run_hybrid(args):
         print(json.dumps(out), flush=True)
 
 
+def run_gemm_route(args):
+    """The GEMM route for rotated costs at the rotated Rastrigin n = 1024 workload's shape
+    (65536 chains, L = 500): every step forms all chains' candidates X' (C x n) and
+    Y' = X' Q^T (2 C n^2 flops) on the tensor cores, which this times with the library's
+    tcgen05 BF16 GEMM and with torch.matmul (cuBLAS), CUDA events, after warm-up.  The
+    rank-1 route's level (the rotated sweep) is timed live on the same workload."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_2408_00018_gb300 import _build, inputs, sa
+
+    _build.build()
+    lib = sa.load()
+    cfg = inputs.ROT_RASTRIGIN_N1024
+    C, n, L = cfg["chains"], cfg["n"], cfg["L"]
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = (torch.rand(C, n, generator=g) * 10.24 - 5.12).to(torch.bfloat16).cuda()
+    Q = torch.as_tensor(inputs.rotation(n, cfg["q_seed"]), dtype=torch.float32).to(torch.bfloat16).cuda()
+    D = torch.empty(C, n, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    s_ptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def ours():
+        lib.sa_gemm_bf16(ctypes.c_void_p(X.data_ptr()), n, ctypes.c_void_p(Q.data_ptr()), n,
+                         ctypes.c_void_p(D.data_ptr()), n, C, n, n, ctypes.c_void_p(status.data_ptr()), s_ptr)
+
+    def cublas():
+        torch.mm(X, Q.t())
+
+    flops = 2.0 * C * n * n
+    res = {}
+    for name, fn in (("tcgen05", ours), ("cublas", cublas)):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_step": ms, "tflops": flops / (ms * 1e-3) / 1e12, "ms_per_level": ms * L}
+    assert int(status.item()) == 0
+    # the rank-1 route: the rotated sweep's live level time on the same workload
+    lo, hi = inputs.box(cfg["cost"], n)
+    sch = sa.Schedule(T0=cfg["T0"], rho=cfg["rho"], levels=3, sigma_frac=cfg["sigma_frac"], precision="fp32")
+    with sa.create(cfg["cost"], lo, hi, n, C, L, sch, seed=cfg["seed"], Q=inputs.rotation(n, cfg["q_seed"])) as h:
+        h.run()
+        h.reset()
+        sweep_ms, _ = h.profile()
+    rank1 = float(np.mean(sweep_ms[1:]))  # levels >= 1 (level 0 also reads X0, Y0)
+    peak = 1736.1
+    print(json.dumps({"metric": "rotated costs: GEMM route vs rank-1 route (rotated Rastrigin n = 1024)",
+                      "shape": {"C": C, "n": n, "L": L}, "flops_per_step": flops, "gemm": res,
+                      "bf16_peak_tflops_sustained": peak,
+                      "rank1_sweep_ms_per_level": rank1,
+                      "note": "the GEMM route's time is the BF16 product alone: BF16 inputs carry 8 "
+                              "significant bits, so nearly every decision would go to the FP64 re-check; an "
+                              "error-free split needs at least 3 products"}), flush=True)
+
+
 def run_paper_schwefel(args):
     """The normalised Schwefel function under the paper's configuration (Sec. 4.1):
     T0 = 1000, T_min = 0.01, rho = 0.99 (1146 levels), N = 100 steps, 16384 chains,
@@ -624,6 +691,9 @@ def run_suite(args):
 
 def main():
     args = parse()
+    if args.gemm_route:
+        run_gemm_route(args)
+        return
     if args.paper_schwefel:
         run_paper_schwefel(args)
         return
