@@ -3,7 +3,8 @@
 //
 // Both operands are K-major (rows of K contiguous elements).  Tiles of
 // 128 x 64 (A) and BN x 64 (B) elements are moved by TMA into 128-byte
-// swizzled shared memory through a 4-stage mbarrier pipeline; one thread
+// swizzled shared memory through a 3-stage mbarrier pipeline (two CTAs fit on an SM,
+// so one CTA's epilogue overlaps the other's main loop); one thread
 // issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator of 128 lanes x
 // BN columns in TMEM); after the last K tile the four warps of the CTA read
 // the accumulator with tcgen05.ld (warp w owns rows 32w .. 32w + 31) and apply
@@ -24,7 +25,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kThreads = 128;
 constexpr uint32_t kSpin = 1u << 20;  // bounded waits (each try_wait itself blocks for a while)
 
