@@ -3,8 +3,9 @@
 //
 // Both operands are K-major (rows of K contiguous elements).  Tiles of
 // 128 x 64 (A) and BN x 64 (B) elements are moved by TMA into 128-byte
-// swizzled shared memory through a 3-stage mbarrier pipeline (two CTAs fit on an SM,
-// so one CTA's epilogue overlaps the other's main loop); one thread
+// swizzled shared memory through a 3-stage (BN = 128) or 2-stage (BN = 256) mbarrier
+// pipeline (two CTAs fit on an SM, so one CTA's epilogue overlaps the other's main
+// loop); one thread
 // issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator of 128 lanes x
 // BN columns in TMEM); after the last K tile the four warps of the CTA read
 // the accumulator with tcgen05.ld (warp w owns rows 32w .. 32w + 31) and apply
@@ -25,7 +26,10 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kStages = 3;
+// Pipeline depth per tile width: 3 stages of a 128 x 128 pair (96 KB) or 2 of a
+// 128 x 256 pair (96 KB), so that two CTAs share an SM.
+template <int BN>
+__host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : 3; }
 constexpr int kThreads = 128;
 constexpr uint32_t kSpin = 1u << 20;  // bounded waits (each try_wait itself blocks for a while)
 
@@ -113,6 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kATile = kBM * kBK * 2;
     constexpr int kBTile = BN * kBK * 2;
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns (power of two >= 32)
+    constexpr int kStages = stages_for<BN>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
@@ -299,6 +304,7 @@ bool make_tmap(CUtensorMap* m, const void* ptr, int rows, int K, int ld, int box
 
 template <int BN>
 size_t gemm_smem() {
+    constexpr int kStages = stages_for<BN>();
     return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
 }
 
@@ -325,6 +331,7 @@ __device__ int g_gemm_status;  // status word of the kernel-level entry point
 cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
                                  int* status, cudaStream_t s) {
     EpiStoreF32 epi{D, ldd};
+    if (N % 256 == 0) return launch_gemm<256>(A, lda, B, ldb, M, N, K, epi, status, s);
     if (N % 128 == 0) return launch_gemm<128>(A, lda, B, ldb, M, N, K, epi, status, s);
     return launch_gemm<64>(A, lda, B, ldb, M, N, K, epi, status, s);
 }
