@@ -1,0 +1,46 @@
+"""Host-side logic of bench.py: the time-to-target rule (with and without the
+hybrid's polish) and the algorithmic SFU counts behind the roofline."""
+import numpy as np
+
+import bench
+
+
+def _log(f_inc, t_ns):
+    return {"f_inc": np.array(f_inc, float), "t_ns": np.array(t_ns, np.int64)}
+
+
+def test_time_to_target_first_level_within_tolerance():
+    fs = -418.9828872724337
+    logs = [_log([-300.0, fs + 1e-3, fs + 1e-5, fs], [1_000_000, 2_000_000, 3_000_000, 4_000_000])]
+    out = bench.time_to_target(logs, 0, [fs])
+    # |f - f*| <= 1e-6 |f*| = 4.19e-4: level 2 (1e-5 away) is the first
+    assert out["reached"] and out["level"] == 2 and abs(out["seconds"] - 3e-3) < 1e-12
+
+
+def test_time_to_target_not_reached_reports_the_gap():
+    logs = [_log([5.0, 1.0], [10, 20]), _log([0.0, 0.0], [10, 20])]
+    out = bench.time_to_target(logs, 0, [0.0, 0.0])
+    assert not out["reached"] and out["problems_reached"] == 1 and out["seconds"] is None
+    assert out["worst_final_rel_gap"] == 1.0
+
+
+def test_time_to_target_counts_the_polished_incumbent_at_the_run_end():
+    fs = -418.9828872724337
+    logs = [_log([-300.0, -400.0], [1_000, 2_000])]
+    out = bench.time_to_target(logs, 0, [fs], final_f=[fs + 1e-9], run_s=0.39)
+    assert out["reached"] and out["reached_by_polish"] == 1 and out["seconds"] == 0.39 and "level" not in out
+    out = bench.time_to_target(logs, 0, [fs], final_f=[-400.0], run_s=0.39)
+    assert not out["reached"]
+
+
+def test_time_to_target_without_closed_form():
+    out = bench.time_to_target([_log([1.0], [1])], 0, [None])
+    assert out["reached"] is None
+
+
+def test_sfu_counts():
+    # Gaussian step: lg2, sqrt, cos; the acceptance test: lg2; Schwefel's new term: sqrt, sin
+    assert bench.sfu_per_step("schwefel", 256) == 6
+    assert bench.sfu_per_step("schwefel", 256, "uniform") == 3
+    assert bench.sfu_per_step("rot_rastrigin", 1024) == 1028
+    assert bench.sfu_per_step("rot_schwefel", 128, "uniform") == 2 * 128 + 1
