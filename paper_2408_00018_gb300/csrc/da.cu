@@ -95,13 +95,21 @@ __global__ void __launch_bounds__(32 * kWarpsDA) da_start_kernel(SweepArgs A, Da
     else start_chain<kRotSchwefel>(A, P, D, c, level);
 }
 
+// f~ from the output head's four partial sums q and the output bias: the sum in a
+// fixed order, then mu + sigma * sum as one FMA, all by explicit round-to-nearest
+// intrinsics so that every kernel that forms f~ rounds it the same way.
+__device__ __forceinline__ float surrogate_of(const DaDev& D, const float* q, float b3) {
+    const float t = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(q[0], q[1]), q[2]), q[3]), b3);
+    return __fmaf_rn(D.ms[1], t, D.ms[0]);
+}
+
 // f~ of every chain's start state (from the head's partial sums).
 __global__ void da_ft_kernel(SweepArgs A, DaDev D, const float* __restrict__ b3) {
     const ProbDev& P = A.probs[D.problem];
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= P.chains) return;
     const float* q = D.part + (size_t)c * 4;
-    const float v = D.ms[0] + D.ms[1] * (((q[0] + q[1]) + q[2]) + q[3] + *b3);
+    const float v = surrogate_of(D, q, *b3);
     D.fts[c] = v;
     const int level = A.run->level;
     if (D.trace_ft0 && level < A.trace_levels) D.trace_ft0[(size_t)level * P.chains + c] = v;
@@ -121,21 +129,41 @@ __global__ void da_patch_kernel(SweepArgs A, DaDev D, int s) {
     D.xs[(size_t)c * D.np + mv.d] = std_bf16(mv.xp, D.mid[mv.d], D.inv_half[mv.d]);
 }
 
+// One 4-byte asynchronous copy from global into shared memory (completed by cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// One lockstep step of chain c.  sy: the warp's 2n floats of shared memory.  The
+// chain's pair state is copied into it asynchronously before the step's draws
+// (the copies do not depend on them), the step reads and updates it there, and
+// an accepted move writes it back.  Every lane touches only its own coordinates
+// k = lane + 32 j, so the copies need no exchange between lanes.
 template <int COST>
-__device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D, int64_t c, int level, int s,
+__device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D, int64_t c, int level, int s, float* sy,
                            unsigned& nacc, unsigned& nev, unsigned& nre) {
     const int lane = threadIdx.x & 31;
     const int n = P.n;
     const double T = A.T_tab[level];
     float* x = D.xf + (size_t)c * n;
-    float* yh = D.yh + (size_t)c * n;
-    float* yl = D.yl + (size_t)c * n;
+    float* yhg = D.yh + (size_t)c * n;
+    float* ylg = D.yl + (size_t)c * n;
+    float* yh = sy;
+    float* yl = sy + n;
+    for (int k = lane; k < n; k += 32) {
+        cp_async4(yh + k, yhg + k);
+        cp_async4(yl + k, ylg + k);
+    }
+    // the running value and its error bound (lane 0 updates them on acceptance)
+    const double Fa0 = D.Fa[c], Ea0 = D.Ea[c];
     const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
     const float neg_T_ln2 = (float)(-T * 0.69314718055994531);
     const RotMove mv = rot_propose(w, x, P, (float)A.s_tab[level], A.boundary, 0, neg_T_ln2);
     // surrogate at the proposal (fixed summation order) and at the current state
     const float* q = D.part + (size_t)c * 4;
-    const float ftp = D.ms[0] + D.ms[1] * (((q[0] + q[1]) + q[2]) + q[3] + D.b3[0]);
+    const float ftp = surrogate_of(D, q, D.b3[0]);
     const float ftc = D.fts[c];
     const bool tracing = level < A.trace_levels;
     if (tracing && D.trace_ftp && lane == 0) D.trace_ftp[((size_t)level * A.L + s) * P.chains + c] = ftp;
@@ -155,6 +183,8 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
         else pass1 = u23d(wd.x) < exp(-dFs / T);
     }
     bool acc = false;
+    cp_async_wait_all();
+    __syncwarp();
     if (pass1) {
         ++nev;
         // ---- stage 2: accept iff dF - dFs <= 0 or u3 < exp(-(dF - dFs)/T), i.e. dF < dFs + tau
@@ -182,10 +212,14 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
         if (acc) {
             float edrift = 0.0f;
             rot_update<COST>(P, yh, yl, mv.d, mv.dh, mv.dl, n, lane, edrift);
+            for (int k = lane; k < n; k += 32) {
+                yhg[k] = yh[k];
+                ylg[k] = yl[k];
+            }
             if (lane == 0) {
                 x[mv.d] = mv.xp;
-                D.Fa[c] += dF_used;
-                D.Ea[c] += e_step + (double)edrift;
+                D.Fa[c] = Fa0 + dF_used;
+                D.Ea[c] = Ea0 + (e_step + (double)edrift);
                 D.fts[c] = ftp;
             }
             ++nacc;
@@ -200,22 +234,27 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(32 * kWarpsDA) da_step_kernel(SweepArgs A, DaDev D, int s) {
+// A grid sized to the resident blocks; each warp takes chains blockIdx * kWarpsDA +
+// warp + j * (gridDim * kWarpsDA), so that the counters take one global atomic per block.
+__global__ void __launch_bounds__(32 * kWarpsDA, 6) da_step_kernel(SweepArgs A, DaDev D, int s) {
+    extern __shared__ __align__(16) float smem_da[];
     __shared__ unsigned sacc, sev, sre;
     const ProbDev& P = A.probs[D.problem];
     if (threadIdx.x == 0) sacc = sev = sre = 0u;
     __syncthreads();
-    const int64_t c = (int64_t)blockIdx.x * kWarpsDA + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    float* sy = smem_da + (size_t)warp * 2 * P.n;
+    const int level = A.run->level;
     unsigned nacc = 0, nev = 0, nre = 0;
-    if (c < P.chains) {
-        const int level = A.run->level;
-        if (P.cost == kRotRastrigin) step_chain<kRotRastrigin>(A, P, D, c, level, s, nacc, nev, nre);
-        else step_chain<kRotSchwefel>(A, P, D, c, level, s, nacc, nev, nre);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&sacc, nacc);
-            atomicAdd(&sev, nev);
-            atomicAdd(&sre, nre);
-        }
+    const int64_t stride = (int64_t)gridDim.x * kWarpsDA;
+    for (int64_t c = (int64_t)blockIdx.x * kWarpsDA + warp; c < P.chains; c += stride) {
+        if (P.cost == kRotRastrigin) step_chain<kRotRastrigin>(A, P, D, c, level, s, sy, nacc, nev, nre);
+        else step_chain<kRotSchwefel>(A, P, D, c, level, s, sy, nacc, nev, nre);
+    }
+    if ((threadIdx.x & 31) == 0 && (nacc | nev | nre)) {
+        atomicAdd(&sacc, nacc);
+        atomicAdd(&sev, nev);
+        atomicAdd(&sre, nre);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -405,7 +444,29 @@ int grid_for(int64_t work, int block) {
     return (int)(g < 1 ? 1 : (g > 152 * 64 ? 152 * 64 : g));
 }
 
+size_t da_step_smem(int n) { return (size_t)kWarpsDA * 2 * (size_t)n * sizeof(float); }
+
 }  // namespace
+
+// The step kernel's shared memory (above the default 48 KB from n = 1537 on) and grid:
+// the blocks that fit on the device at once, at most one per 4 chains.
+cudaError_t da_prepare(DaDev& D, int64_t chains) {
+    const size_t smem = da_step_smem(D.mlp.n);
+    static size_t current = 0;  // only ever raised: a smaller handle must not lower a larger one's limit
+    cudaError_t e = cudaSuccess;
+    if (smem > current) {
+        e = cudaFuncSetAttribute(da_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) current = smem;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, da_step_kernel, 32 * kWarpsDA, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (chains + kWarpsDA - 1) / kWarpsDA;
+    D.step_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(1, per_sm) * sms));
+    return cudaSuccess;
+}
 
 // Before level 0 of a run: fresh network (seeded), zero moments and counters.
 cudaError_t da_run_start(const DaDev& D, uint64_t seed, cudaStream_t s) {
@@ -459,7 +520,7 @@ cudaError_t launch_da_level(const SweepArgs& A, const DaDev& Dc, int64_t chains,
             e = launch_gemm_bias_gelu_dot(w.A1, kMlpHidden, D.mlp.W2b, kMlpHidden, D.Cp, kMlpHidden, kMlpHidden,
                                           D.mlp.p + o.b2, D.mlp.p + o.w3, D.part, nullptr, 0, status, s);
         if (e == cudaSuccess) {
-            da_step_kernel<<<cblocks, 32 * kWarpsDA, 0, s>>>(A, D, st);
+            da_step_kernel<<<D.step_blocks, 32 * kWarpsDA, da_step_smem(D.mlp.n), s>>>(A, D, st);
             // states along the level (and at its end) feed the training buffer
             for (int j = 0; j < kDaInserts; ++j)  // exactly kDaInserts insertions per level
                 if (std::max(1, (j + 1) * L / kDaInserts) - 1 == st)

@@ -527,6 +527,7 @@ sa_status setup_da(sa_handle* h) {
     D.mlp.n = n;
     D.mlp.np = D.np;
     D.b3 = D.mlp.p + mlp_offsets(n).b3;
+    if (da_prepare(D, C) != cudaSuccess) return SA_ECUDA;
     D.dkey0 = (uint32_t)h->seed;
     D.dkey1 = (uint32_t)(h->seed >> 32) ^ kTagDa;
     D.tkey0 = (uint32_t)h->seed;

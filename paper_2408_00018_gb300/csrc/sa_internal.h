@@ -257,6 +257,7 @@ void mlp_work_carve(void* base, int Bp, int np, MlpWork& w);
 struct DaDev {
     int problem;             // index of the (rotated) problem in the handle
     int np, Cp;              // padded input width and chain count (multiples of 64 / 128)
+    int step_blocks;         // grid of the step kernel (set by da_prepare)
     int64_t cap;             // ring buffer rows (a multiple of the chain count)
     int batch;               // training batch rows
     float* xf;               // [C][n] current states
@@ -289,6 +290,7 @@ struct DaDev {
     MlpWork work;            // training workspace (batch rows)
 };
 
+cudaError_t da_prepare(DaDev& D, int64_t chains);
 cudaError_t da_run_start(const DaDev& D, uint64_t seed, cudaStream_t s);
 cudaError_t launch_da_level(const SweepArgs& A, const DaDev& D, int64_t chains, int L, int train_steps, float lr,
                             int* status, cudaStream_t s);
