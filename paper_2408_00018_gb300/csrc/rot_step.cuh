@@ -222,7 +222,9 @@ __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* y
         #pragma unroll 4
         for (int i = lane; i < n; i += 32) {
         const float qh = qcol[i], ql = qlcol[i];
-        const float ph = dh * qh;
+        // the rounded product by an intrinsic that is never merged into an FMA: the
+        // TwoSum below (a + ph and ph - t2) is error-free only for this very ph
+        const float ph = __fmul_rn(dh, qh);
         const float pl = fmaf(dh, qh, -ph);
         const float corr = fmaf(dh, ql, dl * qh);
         const float a = yh[i];
