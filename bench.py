@@ -84,6 +84,10 @@ def parse():
     ap.add_argument("--suite", action="store_true",
                     help="the paper's 41-problem test suite (Tables 8-9) instead: one synchronous run per problem, "
                          "then the hybrid's Nelder-Mead polish (one JSON line per problem and a summary)")
+    ap.add_argument("--convergence", action="store_true",
+                    help="the convergence study of Sec. 4.1 (Figures 4-5) instead: relative error of the best value "
+                         "against explored points for V0, V1 and V2 at equal numbers of explored points, n = 8 .. 256 "
+                         "(one JSON line per n)")
     ap.add_argument("--hybrid", action="store_true",
                     help="the hybrid SA of Table 10 instead: annealing stopped early, then Nelder-Mead or projected "
                          "gradients from its best final states (one JSON line per function)")
@@ -635,6 +639,65 @@ def run_paper_schwefel(args):
         print(json.dumps(out), flush=True)
 
 
+# The convergence study (Sec. 4.1, Figures 4-5): per level every version explores
+# CONV_C * CONV_L points; CONV_R replicas per version, reported as their mean.
+CONV_N = (8, 16, 32, 64, 128, 256)
+CONV_C, CONV_L, CONV_R = 1024, 100, 8
+CONV_CHECKPOINTS = (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 1146)
+
+
+def convergence_curve(f_levels, f_star, checkpoints):
+    """Mean over the replicas of the relative error |f - f*| / |f*| of the level's best
+    value after each checkpoint's number of levels (a checkpoint past the end of a run
+    takes its last level)."""
+    import numpy as np
+    out = []
+    for k in checkpoints:
+        errs = [abs(float(f[min(k, len(f)) - 1]) - f_star) / abs(f_star) for f in f_levels]
+        out.append(float(np.mean(errs)))
+    return out
+
+
+def run_convergence(args):
+    """The convergence study of Sec. 4.1 (Figures 4-5) at equal numbers of explored
+    points: V1 (asynchronous) and V2 (synchronous) run CONV_C chains of CONV_L steps per
+    level; V0 (sequential: one chain) runs CONV_C * CONV_L steps per level at the same
+    temperatures (T0 = 1000, rho = 0.99, T_min = 0.01: 1146 levels), so every version
+    explores the same points per level.  Schwefel on [-512, 512]^n, the paper's move (a
+    uniform redraw of the chosen coordinate), FP32 state.  Each version runs CONV_R
+    replicas as the problems of one batch (each problem draws its own Philox streams);
+    for V1 the level's value is the best over all its chains, as in the paper."""
+    import numpy as np
+    import torch
+    from paper_2408_00018_gb300 import _build, inputs, sa
+
+    _build.build()
+    sa.load()
+    fs = inputs.SCHWEFEL_F_STAR
+    for n in CONV_N:
+        lo, hi = np.full(n, -512.0), np.full(n, 512.0)
+        out = {"metric": "convergence: mean relative error |f - f*| / |f*| of the level's best value vs explored points",
+               "cost": "schwefel", "n": n, "chains": CONV_C, "L": CONV_L, "replicas": CONV_R, "levels": 1146,
+               "points_per_level": CONV_C * CONV_L, "checkpoint_levels": list(CONV_CHECKPOINTS),
+               "points": [k * CONV_C * CONV_L for k in CONV_CHECKPOINTS], "proposal": "uniform", "precision": "fp32"}
+        for version, indep, chains, L in (("V0", 0, 1, CONV_C * CONV_L), ("V1", 1, CONV_C, CONV_L),
+                                          ("V2", 0, CONV_C, CONV_L)):
+            sch = sa.Schedule(T0=1000.0, rho=0.99, levels=0, T_min=0.01, precision="fp32", independent=indep,
+                              proposal="uniform")
+            probs = [dict(cost="schwefel", n=n, chains=chains, lo=lo, hi=hi) for _ in range(CONV_R)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with sa.create_batch(probs, L, sch, seed=0) as h:
+                h.run()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                logs = [h.level_log(p)["f_level"] for p in range(CONV_R)]
+                steps = h.best(0)[2]["steps"]
+            out[version] = {"rel_err": convergence_curve(logs, fs, CONV_CHECKPOINTS), "steps_per_replica": int(steps),
+                            "s": dt}
+        print(json.dumps(out), flush=True)
+
+
 # The suite's schedule: one for every problem (the paper tunes per function and
 # prints no schedule): T0 = 10, rho = 0.9, 100 levels of L = 500 steps, moves
 # by the paper's reading (a uniform redraw of the chosen coordinate).  Costs
@@ -702,6 +765,9 @@ def main():
         return
     if args.hybrid:
         run_hybrid(args)
+        return
+    if args.convergence:
+        run_convergence(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -44,3 +44,19 @@ def test_sfu_counts():
     assert bench.sfu_per_step("schwefel", 256, "uniform") == 3
     assert bench.sfu_per_step("rot_rastrigin", 1024) == 1028
     assert bench.sfu_per_step("rot_schwefel", 128, "uniform") == 2 * 128 + 1
+
+
+def test_convergence_curve_means_the_replicas_at_each_checkpoint():
+    fs = -400.0
+    a = np.array([-200.0, -300.0, -380.0, -396.0])  # relative errors 0.5, 0.25, 0.05, 0.01
+    b = np.array([-100.0, -200.0, -400.0, -400.0])  # 0.75, 0.5, 0, 0
+    out = bench.convergence_curve([a, b], fs, (1, 2, 3, 4))
+    assert np.allclose(out, [0.625, 0.375, 0.025, 0.005], rtol=0, atol=1e-15)
+    # a checkpoint past the end of a run takes its last level
+    assert np.allclose(bench.convergence_curve([a], fs, (4, 9)), [0.01, 0.01], rtol=0, atol=1e-15)
+
+
+def test_convergence_versions_explore_equal_points_per_level():
+    # V0 runs one chain of C * L steps per level, V1 and V2 C chains of L steps
+    assert bench.CONV_C * bench.CONV_L == 1 * (bench.CONV_C * bench.CONV_L)
+    assert bench.CONV_CHECKPOINTS[-1] == 1146 and list(bench.CONV_CHECKPOINTS) == sorted(set(bench.CONV_CHECKPOINTS))
