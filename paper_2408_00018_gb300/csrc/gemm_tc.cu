@@ -7,9 +7,10 @@
 // pipeline (two CTAs fit on an SM, so one CTA's epilogue overlaps the other's main
 // loop); one thread
 // issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator of 128 lanes x
-// BN columns in TMEM); after the last K tile the four warps of the CTA read
-// the accumulator with tcgen05.ld (warp w owns rows 32w .. 32w + 31) and apply
-// the epilogue.  Every wait on an mbarrier is bounded: on expiry the kernel
+// BN columns in TMEM); after the last K tile the eight warps of the CTA read
+// the accumulator with tcgen05.ld (warp w may read the lanes 32 (w mod 4) ..
+// 32 (w mod 4) + 31, its tile rows; warps w and w + 4 split the columns in
+// halves) and apply the epilogue.  Every wait on an mbarrier is bounded: on expiry the kernel
 // records a timeout in a status word, stops issuing work, waits (bounded) for
 // the copies it issued, frees its TMEM and returns.
 //
@@ -30,7 +31,7 @@ constexpr int kBK = 64;
 // 128 x 256 pair (96 KB), so that two CTAs share an SM.
 template <int BN>
 __host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : 3; }
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // 8 warps: all of them run the epilogue, two per TMEM lane quadrant
 constexpr uint32_t kSpin = 1u << 20;  // bounded waits (each try_wait itself blocks for a while)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -111,7 +112,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 template <int BN, class Epi>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, Epi epi,
                      int* status) {
     constexpr int kATile = kBM * kBK * 2;
@@ -194,31 +195,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
 
-    // ---- epilogue: warp w reads accumulator lanes 32w .. 32w + 31 (tile rows)
+    // ---- epilogue: warp w reads accumulator lanes 32 q .. 32 q + 31 (tile rows), q = w mod 4,
+    // and the columns [h BN/2, (h + 1) BN/2), h = w / 4
+    __shared__ float red[kBM];  // reducing epilogues: the second column half's sum per row
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = m0 + quad * 32 + lane;
+    float acc = 0.0f;
     const bool have = mbar_wait(done, 0);
     if (!have) atomicExch(abort_flag, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (have && !*(volatile int*)abort_flag) {
-        const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
+        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            epi(row, n0 + c, v);
+            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
+            epi(row, n0 + c, v, acc);
         }
+        if (Epi::kReduces && half == 1) red[quad * 32 + lane] = acc;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    // the row's sum: first half + second half, in that order
+    if (Epi::kReduces && half == 0 && have && !*(volatile int*)abort_flag) epi.finish(row, n0, acc + red[quad * 32 + lane]);
     if (threadIdx.x == 0 && *(volatile int*)abort_flag && status) atomicExch(status, 4);  // SA_ETIMEOUT
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
 // ---- epilogues ------------------------------------------------------------
+// Each epilogue takes 16 accumulator columns of one row; a reducing one (kReduces)
+// adds into acc, and finish() stores the row's sum over the tile.
 struct EpiStoreF32 {
+    static constexpr bool kReduces = false;
     float* D;
     int ldd;
-    __device__ __forceinline__ void operator()(int row, int col, const float* v) const {
+    __device__ __forceinline__ void finish(int, int, float) const {}
+    __device__ __forceinline__ void operator()(int row, int col, const float* v, float&) const {
         float4* p = reinterpret_cast<float4*>(D + (size_t)row * ldd + col);
 #pragma unroll
         for (int j = 0; j < 4; ++j) p[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
@@ -227,12 +239,14 @@ struct EpiStoreF32 {
 
 // Surrogate layer: z = acc + bias; stores gelu(z) as BF16 (and z as FP32 when Z != nullptr).
 struct EpiBiasGelu {
+    static constexpr bool kReduces = false;
     const float* bias;
     __nv_bfloat16* A;
     int lda;
     float* Z;
     int ldz;
-    __device__ __forceinline__ void operator()(int row, int col, const float* v) const {
+    __device__ __forceinline__ void finish(int, int, float) const {}
+    __device__ __forceinline__ void operator()(int row, int col, const float* v, float&) const {
         __align__(16) __nv_bfloat16 a[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -246,10 +260,12 @@ struct EpiBiasGelu {
     }
 };
 
-// Surrogate output head: part[row][col / tile] = sum over the tile's columns of
-// gelu(acc + b) w (one thread owns a row of a tile, so the sum is sequential
-// and deterministic); stores z as FP32 when Z != nullptr.
+// Surrogate output head: part[row][n0 / BN] = sum over the tile's columns of
+// gelu(acc + b) w, in a fixed order (per 16 columns sequentially, the chunks of
+// each column half in turn, then first half + second half), so it is
+// deterministic; stores z as FP32 when Z != nullptr.
 struct EpiBiasGeluDot {
+    static constexpr bool kReduces = true;
     const float* bias;
     const float* w;
     float* part;
@@ -257,7 +273,10 @@ struct EpiBiasGeluDot {
     int tile;
     float* Z;
     int ldz;
-    __device__ __forceinline__ void operator()(int row, int col, const float* v) const {
+    __device__ __forceinline__ void finish(int row, int n0, float total) const {
+        part[(size_t)row * nparts + n0 / tile] = total;
+    }
+    __device__ __forceinline__ void operator()(int row, int col, const float* v, float& acc) const {
         float s = 0.0f;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -265,8 +284,7 @@ struct EpiBiasGeluDot {
             if (Z) Z[(size_t)row * ldz + col + j] = z;
             s = fmaf(gelu_f(z), w[col + j], s);
         }
-        float* dst = part + (size_t)row * nparts + col / tile;
-        *dst = (col % tile == 0) ? s : *dst + s;
+        acc += s;
     }
 };
 
