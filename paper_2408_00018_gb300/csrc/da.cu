@@ -136,17 +136,22 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// The level's constants of a step, formed once per thread and launch.
+struct StepConst {
+    double T;                 // temperature
+    float Tf, neg_T_ln2, sl;  // T and -T ln 2 in FP32; sl = sqrt(T / T0)
+};
+
 // One lockstep step of chain c.  sy: the warp's 2n floats of shared memory.  The
 // chain's pair state is copied into it asynchronously before the step's draws
 // (the copies do not depend on them), the step reads and updates it there, and
 // an accepted move writes it back.  Every lane touches only its own coordinates
 // k = lane + 32 j, so the copies need no exchange between lanes.
 template <int COST>
-__device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D, int64_t c, int level, int s, float* sy,
-                           unsigned& nacc, unsigned& nev, unsigned& nre) {
+__device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D, int64_t c, int level, int s,
+                           const StepConst& K, float* sy, unsigned& nacc, unsigned& nev, unsigned& nre) {
     const int lane = threadIdx.x & 31;
     const int n = P.n;
-    const double T = A.T_tab[level];
     float* x = D.xf + (size_t)c * n;
     float* yhg = D.yh + (size_t)c * n;
     float* ylg = D.yl + (size_t)c * n;
@@ -159,28 +164,38 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     // the running value and its error bound (lane 0 updates them on acceptance)
     const double Fa0 = D.Fa[c], Ea0 = D.Ea[c];
     const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), A.key0, A.key1);
-    const float neg_T_ln2 = (float)(-T * 0.69314718055994531);
-    const RotMove mv = rot_propose(w, x, P, (float)A.s_tab[level], A.boundary, 0, neg_T_ln2);
+    const RotMove mv = rot_propose(w, x, P, K.sl, A.boundary, 0, K.neg_T_ln2);
     // surrogate at the proposal (fixed summation order) and at the current state
     const float* q = D.part + (size_t)c * 4;
     const float ftp = surrogate_of(D, q, D.b3[0]);
     const float ftc = D.fts[c];
     const bool tracing = level < A.trace_levels;
     if (tracing && D.trace_ftp && lane == 0) D.trace_ftp[((size_t)level * A.L + s) * P.chains + c] = ftp;
-    // ---- stage 1 (surrogate only): u < exp(-dFs/T), i.e. dFs < tau1 = -T ln u, taken in
-    // FP32 with a margin for the error of tau1 and in FP64 inside the margin (the
-    // same decision as the FP64 test, without an FP64 exp per lane and step)
-    const double dFs = (double)ftp - (double)ftc;
+    // ---- stage 1 (surrogate only): pass iff u < exp(-dFs/T), dFs = f~(x') - f~(x), i.e.
+    // dFs < tau1 = -T ln u.  FP32 decides outside a margin that covers the error of
+    // tau1 (1e-6 tau1 + 4e-7 T), the roundings of the FP32 difference, of the margin
+    // and of the comparison; inside it the FP64 tests decide, so the decision is the
+    // FP64 one everywhere (this GPU's FP64 rate is a small fraction of its FP32 rate).
     const uint4 wd = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)level, (uint32_t)c + P.cid0, P.pid), D.dkey0, D.dkey1);
+    const float d32 = ftp - ftc;
     bool pass1;
-    if (dFs <= 0.0) {
+    if (ftp <= ftc) {  // dFs <= 0 exactly
         pass1 = true;
     } else {
-        const double tau1 = (double)(neg_T_ln2 * __log2f(u23f(wd.x)));
-        const double m1 = 1.0e-6 * tau1 + 4.0e-7 * T;
-        if (dFs < tau1 - m1) pass1 = true;
-        else if (dFs > tau1 + m1) pass1 = false;
-        else pass1 = u23d(wd.x) < exp(-dFs / T);
+        const float t1 = K.neg_T_ln2 * __log2f(u23f(wd.x));
+        const float M1 = fmaf(1.1e-6f, t1, fmaf(4.4e-7f, K.Tf, 2.4e-7f * d32));
+        if (d32 < t1 - M1) {
+            pass1 = true;
+        } else if (d32 > t1 + M1) {
+            pass1 = false;
+        } else {
+            const double dFs = (double)ftp - (double)ftc;
+            const double tau1 = (double)t1;
+            const double m1 = 1.0e-6 * tau1 + 4.0e-7 * K.T;
+            if (dFs < tau1 - m1) pass1 = true;
+            else if (dFs > tau1 + m1) pass1 = false;
+            else pass1 = u23d(wd.x) < exp(-dFs / K.T);
+        }
     }
     bool acc = false;
     cp_async_wait_all();
@@ -195,19 +210,33 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
             rot_eval32<COST>(P, yh, yl, mv.d, mv.dh + opaque_zero(), n, lane, dF2, B2);
             asm volatile("" ::"f"(dF2), "f"(B2));
         }
-        const double thr = dFs + (double)mv.tau;
-        const double Bt = (double)B + 1.0e-6 * fabs((double)mv.tau) + 4.0e-7 * T + 1e-12 * fabs(dFs);
-        double dF_used = (double)dF, e_step = (double)B;
-        if ((double)dF < thr - Bt) {
+        // FP32 decides outside B widened by the error of tau and the roundings of the
+        // FP32 threshold and comparison; inside it the FP64 tests below decide (the
+        // FP64 decision everywhere, as in stage 1)
+        const float thr32 = d32 + mv.tau;
+        const float Bt32 = fmaf(1.00001f, B, fmaf(1.2e-6f, fabsf(mv.tau),
+                                                  fmaf(4.8e-7f, K.Tf, 4.0e-7f * (fabsf(d32) + fabsf(thr32)))));
+        bool rechecked = false;
+        double dF64 = 0.0, e64 = 0.0;
+        if (dF < thr32 - Bt32) {
             acc = true;
-        } else if ((double)dF > thr + Bt) {
+        } else if (dF > thr32 + Bt32) {
             acc = false;
         } else {
-            const double dF64 = rot_eval64<COST>(P, yh, yl, mv.d, mv.xp, mv.xo, n, lane, e_step);
-            const double r = dF64 - dFs;
-            acc = (r <= 0.0) || (u23d(mv.w3) < exp(-r / T));
-            dF_used = dF64;
-            ++nre;
+            const double dFs = (double)ftp - (double)ftc;
+            const double thr = dFs + (double)mv.tau;
+            const double Bt = (double)B + 1.0e-6 * fabs((double)mv.tau) + 4.0e-7 * K.T + 1e-12 * fabs(dFs);
+            if ((double)dF < thr - Bt) {
+                acc = true;
+            } else if ((double)dF > thr + Bt) {
+                acc = false;
+            } else {
+                dF64 = rot_eval64<COST>(P, yh, yl, mv.d, mv.xp, mv.xo, n, lane, e64);
+                const double r = dF64 - dFs;
+                acc = (r <= 0.0) || (u23d(mv.w3) < exp(-r / K.T));
+                rechecked = true;
+                ++nre;
+            }
         }
         if (acc) {
             float edrift = 0.0f;
@@ -217,6 +246,8 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
                 ylg[k] = yl[k];
             }
             if (lane == 0) {
+                const double dF_used = rechecked ? dF64 : (double)dF;
+                const double e_step = rechecked ? e64 : (double)B;
                 x[mv.d] = mv.xp;
                 D.Fa[c] = Fa0 + dF_used;
                 D.Ea[c] = Ea0 + (e_step + (double)edrift);
@@ -245,11 +276,16 @@ __global__ void __launch_bounds__(32 * kWarpsDA, 6) da_step_kernel(SweepArgs A, 
     const int warp = threadIdx.x >> 5;
     float* sy = smem_da + (size_t)warp * 2 * P.n;
     const int level = A.run->level;
+    StepConst K;
+    K.T = A.T_tab[level];
+    K.Tf = (float)K.T;
+    K.neg_T_ln2 = (float)(-K.T * 0.69314718055994531);
+    K.sl = (float)A.s_tab[level];
     unsigned nacc = 0, nev = 0, nre = 0;
     const int64_t stride = (int64_t)gridDim.x * kWarpsDA;
     for (int64_t c = (int64_t)blockIdx.x * kWarpsDA + warp; c < P.chains; c += stride) {
-        if (P.cost == kRotRastrigin) step_chain<kRotRastrigin>(A, P, D, c, level, s, sy, nacc, nev, nre);
-        else step_chain<kRotSchwefel>(A, P, D, c, level, s, sy, nacc, nev, nre);
+        if (P.cost == kRotRastrigin) step_chain<kRotRastrigin>(A, P, D, c, level, s, K, sy, nacc, nev, nre);
+        else step_chain<kRotSchwefel>(A, P, D, c, level, s, K, sy, nacc, nev, nre);
     }
     if ((threadIdx.x & 31) == 0 && (nacc | nev | nre)) {
         atomicAdd(&sacc, nacc);
