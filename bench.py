@@ -56,6 +56,9 @@ SWEEP_SOURCES = ["sweep_f32.cu", "sweep_f32w.cu", "sweep_rot.cu", "sa_device.cuh
 WARMUP_MIN_S = 4.0
 WORKLOADS = ("schwefel_n256", "schwefel_n2", "batched", "rot_rastrigin_n1024", "rot_schwefel_n128")
 ROT_WORKLOADS = {"rot_rastrigin_n1024": "ROT_RASTRIGIN_N1024", "rot_schwefel_n128": "ROT_SCHWEFEL_N128"}
+# The delayed-acceptance level's launch count: training steps per level and kernels per
+# training step (batch draw, weights' cast, forward, loss, backward, Adam), buffer insertions.
+DA_TRAIN_STEPS, DA_LAUNCHES_PER_TRAIN_STEP, DA_INSERTS = 128, 22, 4
 
 
 def parse():
@@ -73,6 +76,9 @@ def parse():
     ap.add_argument("--proposal", choices=["gaussian", "uniform"], default="gaussian",
                     help="the move: the workloads' Gaussian step, or the paper's reading (a uniform redraw of the "
                          "chosen coordinate)")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="rotated workloads: the delayed-acceptance sweep with the learned surrogate (two-stage "
+                         "acceptance, the network trained between levels) instead of the plain rotated sweep")
     ap.add_argument("--independent", action="store_true",
                     help="asynchronous chains (no exchange between levels; the paper's V1), single-problem workloads")
     ap.add_argument("--gemm-route", action="store_true",
@@ -98,9 +104,12 @@ def parse():
 class Workload:
     """One workload: how to build its handle and what one run amounts to."""
 
-    def __init__(self, name, levels_override=0, independent=False, proposal="gaussian", polish_k=0):
+    def __init__(self, name, levels_override=0, independent=False, proposal="gaussian", polish_k=0, surrogate=False):
         from paper_2408_00018_gb300 import inputs
         self.name = name
+        self.surrogate = bool(surrogate)
+        if self.surrogate and name not in ROT_WORKLOADS:
+            raise SystemExit("--surrogate: rotated workloads only")
         self.independent = bool(independent)
         self.proposal = proposal
         self.polish_k = int(polish_k)
@@ -134,7 +143,7 @@ class Workload:
     def schedule(self, sa):
         return sa.Schedule(T0=self.T0, rho=self.rho, levels=self.K, sigma_frac=self.sigma_frac,
                            precision=self.precision, independent=1 if self.independent else 0,
-                           proposal=self.proposal, polish_k=self.polish_k)
+                           proposal=self.proposal, polish_k=self.polish_k, surrogate=1 if self.surrogate else 0)
 
     def create(self, sa, tune=True):
         if self.batch:
@@ -149,12 +158,21 @@ class Workload:
     def launches_per_run(self, h):
         groups = len(h.describe())
         rot = sum(self.rotated)
+        if self.surrogate:
+            # per level: the statistics, DA_TRAIN_STEPS training steps of DA_LAUNCHES_PER_TRAIN_STEP
+            # kernels, the weights' cast, bits cleared, start states, their f~ (2 GEMMs and the head
+            # sum), L steps of (patch, 2 GEMMs, step), the buffer insertions, the level's end; then
+            # the argmin/restart, the restart transform and the level advance
+            per_level = (1 + DA_TRAIN_STEPS * DA_LAUNCHES_PER_TRAIN_STEP + 1 + 1 + 1 + 3 + 4 * self.L
+                         + DA_INSERTS + 1)
+            return 1 + 2 * rot + 2 + self.K * (per_level + 2 + rot)  # (+ 2: the network's init and reset)
         # start stamp (+ initial points and Y0 = X0 Q^T per rotated problem), then per level the
         # group sweeps, the argmin/restart, the restart transform per rotated problem, the level advance
         return 1 + 2 * rot + self.K * (groups + 2 + rot)
 
     def config(self):
         c = {"workload": self.tag + ("_async" if self.independent else "") +
+                         ("_surrogate" if self.surrogate else "") +
                          ("_uniform_moves" if self.proposal == "uniform" else "") +
                          (f"_polish{self.polish_k}" if self.polish_k else ""), "L": self.L, "levels": self.K,
              "T0": self.T0, "rho": self.rho, "seed": self.seed, "steps_per_run": self.steps_per_run, "argmin": "f64",
@@ -338,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     sa.load()
-    w = Workload(args.workload, args.levels, args.independent, args.proposal, args.polish_k)
+    w = Workload(args.workload, args.levels, args.independent, args.proposal, args.polish_k, args.surrogate)
     h = w.create(sa)
     groups = h.describe()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
@@ -403,6 +421,11 @@ def run_ours(args, rank, world, local_rank):
                 "launch_ms": round(sweep_avg, 4),
                 "sweep_share_of_level": round(float(np.sum(sweep_ms) / np.sum(level_ms)), 4),
                 "peak_basis": f"16 SFU ops/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (median sampled SM clock)"}
+    if w.surrogate:  # the timed "sweep" is the whole delayed-acceptance level: training, GEMMs, steps
+        roofline.update({"traffic": None, "kernel": "delayed-acceptance level (training, 2 surrogate GEMMs and "
+                                                    "the step kernel per step)",
+                         "note": "SFU ops of the true evaluations only; the level is bound by its lockstep "
+                                 "kernels' latency, not by the SFU"})
 
     # ---- end to end through the public API with host buffers, every step
     e2e_times = []
@@ -427,7 +450,11 @@ def run_ours(args, rank, world, local_rank):
                    + ("; default launch shapes (no autotune)" if w.batch else "")}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.surrogate:
+        cpu = {"value": None, "unit": UNIT, "kind": "oracle",
+               "sample": "none: the oracle replays the delayed-acceptance decisions from recorded surrogate values "
+                         "(tests) and does not run the sweep itself"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         budget = 3e8 if w.batch else 5.3e8 / (w.problems[0]["n"] / 4 if any(w.rotated) else 1)
         v, dt, what = oracle_sample(w, budget, threads)
@@ -450,6 +477,10 @@ def run_ours(args, rank, world, local_rank):
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     if rank != 0:
+        return
+    if args.surrogate:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no delayed-acceptance sweep of its own "
+                                                               "(it replays the GPU's decisions in the tests)"}))
         return
     w = Workload(args.workload, args.levels, args.independent, args.proposal, args.polish_k)
     threads = os.cpu_count() or 1
