@@ -466,7 +466,9 @@ def run_ours(args, rank, world, local_rank):
                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f32",
                "data": "synthetic",
                "config": dict(w.config(), parallelism=f"replicas{world}", l2="flushed between runs (256 MiB write)",
-                              launch_groups=groups, warmup_runs=warm_runs, warmup_min_s=WARMUP_MIN_S),
+                              launch_groups=[{"kind": "delayed_acceptance", "problems": 1,
+                                              "n_max": w.problems[0]["n"]}] if w.surrogate else groups,
+                              warmup_runs=warm_runs, warmup_min_s=WARMUP_MIN_S),
                "time_to_target": ttt, "best_f": bests[0][1] if len(bests) == 1 else None,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "fp64_rechecks_per_step": (bests[0][2]["rechecks"] / bests[0][2]["steps"]) if any(w.rotated) else None,
