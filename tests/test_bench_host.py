@@ -60,3 +60,23 @@ def test_convergence_versions_explore_equal_points_per_level():
     # V0 runs one chain of C * L steps per level, V1 and V2 C chains of L steps
     assert bench.CONV_C * bench.CONV_L == 1 * (bench.CONV_C * bench.CONV_L)
     assert bench.CONV_CHECKPOINTS[-1] == 1146 and list(bench.CONV_CHECKPOINTS) == sorted(set(bench.CONV_CHECKPOINTS))
+
+
+def test_surrogate_mode_is_for_rotated_workloads_only():
+    import pytest
+    w = bench.Workload("rot_schwefel_n128", 0, False, "gaussian", 0, True)
+    assert w.surrogate and w.config()["workload"].endswith("_surrogate")
+    with pytest.raises(SystemExit):
+        bench.Workload("schwefel_n256", 0, False, "gaussian", 0, True)
+
+
+def test_launch_counts_per_run():
+    class H:
+        def describe(self):
+            return [{"kind": "fp32_thread"}]
+    # the plain sweep: start stamp, then per level the sweep, the argmin/restart and the advance
+    assert bench.Workload("schwefel_n256").launches_per_run(H()) == 1 + 200 * 3
+    # delayed acceptance adds, per level, the training steps and 4 launches per Metropolis step
+    w = bench.Workload("rot_schwefel_n128", 2, False, "gaussian", 0, True)
+    per_level = 1 + bench.DA_TRAIN_STEPS * bench.DA_LAUNCHES_PER_TRAIN_STEP + 6 + 4 * w.L + bench.DA_INSERTS + 1
+    assert w.launches_per_run(H()) == 1 + 2 + 2 + 2 * (per_level + 3)
