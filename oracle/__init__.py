@@ -95,6 +95,9 @@ def lib():
             L.sao_da_chain_level.restype = f64
             L.sao_da_chain_level_steps.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp, vp]
             L.sao_da_chain_level_steps.restype = f64
+            L.sao_proposal.argtypes = [ctypes.POINTER(Cfg), i32, i64, i32, vp, vp, vp]
+            L.sao_da_chain_level_trace.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp, vp, vp, i32]
+            L.sao_da_chain_level_trace.restype = f64
             L.sao_da_chain_level_fn.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, f64, vp, vp, vp]
             L.sao_da_chain_level_fn.restype = f64
             L.sao_run.argtypes = [ctypes.POINTER(Cfg), ctypes.POINTER(Out)]
@@ -260,6 +263,33 @@ class Problem:
         F = lib().sao_da_chain_level_steps(ctypes.byref(cfg), level, c, _p(x), float(ft0), _p(ftp), _p(bits), _p(acc),
                                            _p(ev), _p(dF))
         return F, x, bits, int(acc[0]), int(ev[0]), dF
+
+    def propose_step(self, level, c, s, x):
+        """The move (d, x'_d) that chain c at state x proposes at step s of a level."""
+        cfg = self.cfg()
+        xa = np.ascontiguousarray(x, np.float64)
+        d = np.zeros(1, np.int32)
+        xp = np.zeros(1)
+        lib().sao_proposal(ctypes.byref(cfg), level, c, s, _p(xa), _p(d), _p(xp))
+        return int(d[0]), float(xp[0])
+
+    def da_chain_level_trace(self, level, c, ft0, ft_prop, x_start=None, plant=0):
+        """As da_chain_level_steps, also returning tau [L]: each step's stage-2 threshold
+        -T ln u3 (NaN where stage 1 rejected the move).  plant=1 flips the sign of the
+        surrogate difference in stage 2: a planted mistake, for the tests that show the
+        parity checks catch it.  Returns (F_end, x_end, bits, accepts, evaluations, dF, tau)."""
+        cfg = self.cfg()
+        x = self.init_point(c) if x_start is None else np.array(x_start, np.float64)
+        ftp = np.ascontiguousarray(ft_prop, np.float64)
+        assert ftp.size == self.L
+        bits = np.zeros((self.L + 31) // 32, np.uint32)
+        acc = np.zeros(1, np.int64)
+        ev = np.zeros(1, np.int64)
+        dF = np.zeros(self.L)
+        tau = np.zeros(self.L)
+        F = lib().sao_da_chain_level_trace(ctypes.byref(cfg), level, c, _p(x), float(ft0), _p(ftp), _p(bits), _p(acc),
+                                           _p(ev), _p(dF), _p(tau), int(plant))
+        return F, x, bits, int(acc[0]), int(ev[0]), dF, tau
 
     def da_chain_level_fn(self, level, c, a, b, x_start=None):
         """Delayed acceptance with the analytic surrogate a f(x) + b sum_i sin(x_i);

@@ -472,6 +472,8 @@ typedef struct {
     double ft0;
     const double* ft_prop;
     double a, b;
+    int plant;             /* 0; tests of the parity checks only: 1 = stage 2 with the sign of
+                              the surrogate difference flipped (a planted mistake) */
 } sao_da;
 
 static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
@@ -488,6 +490,40 @@ static double da_fn(const sao_cfg* cfg, const sao_da* da, const double* x, doubl
     double s = 0.0;
     for (int i = 0; i < cfg->n; ++i) s += sin(x[i]);
     return da->a * sao_cost_ws(cfg->cost, cfg->n, x, cfg->Q, ywork) + da->b * s;
+}
+
+/* Step 2 of Sec. 2.1 for chain c at step s of a level: the Philox block of
+ * (s, level, c, problem) picks the coordinate d (word 0) and moves it -- a Gaussian
+ * step (Box-Muller, cosine branch, words 1 and 2) scaled by sqrt(T / T0), or a
+ * uniform redraw of the coordinate (word 2) -- reflected/clipped into the box.
+ * Returns x'_d; *d_out = d, u3_out (may be NULL) = the uniform of word 3. */
+static double propose(const sao_cfg* cfg, int32_t level, int64_t c, int s, double s_l, const double* x, int* d_out,
+                      double* u3_out) {
+    uint32_t w[4];
+    sao_block(cfg->seed, SAO_TAG_SWEEP, (uint32_t)s, (uint32_t)level, (uint32_t)c, cfg->problem, w);
+    const int d = (int)sao_coord(w[0], cfg->n);
+    const double u1 = sao_uniform(w[1]), u2 = sao_uniform(w[2]);
+    const double xd = x[d];
+    double xp;
+    if (cfg->proposal == 1) {
+        xp = apply_box(cfg->lo[d] + u2 * (cfg->hi[d] - cfg->lo[d]), cfg->lo[d], cfg->hi[d], cfg->boundary);
+    } else {
+        const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+        const double sigma = cfg->sigma_frac * (cfg->hi[d] - cfg->lo[d]) * s_l;
+        xp = apply_box(xd + sigma * z, cfg->lo[d], cfg->hi[d], cfg->boundary);
+    }
+    *d_out = d;
+    if (u3_out) *u3_out = sao_uniform(w[3]);
+    return xp;
+}
+
+/* The proposal (d, x'_d) that chain c at state x makes at step s of a level. */
+void sao_proposal(const sao_cfg* cfg, int32_t level, int64_t c, int32_t s, const double* x, int32_t* d_out,
+                  double* xp_out) {
+    const double T = sao_temperature(cfg->T0, cfg->rho, level);
+    int d = 0;
+    *xp_out = propose(cfg, level, c, s, sqrt(T / cfg->T0), x, &d, NULL);
+    *d_out = d;
 }
 
 static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, double* x,
@@ -513,21 +549,12 @@ static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, doubl
     if (bits) memset(bits, 0, sizeof(uint32_t) * (size_t)words);
 
     for (int s = 0; s < cfg->L; ++s) {
-        uint32_t w[4];
-        sao_block(cfg->seed, SAO_TAG_SWEEP, (uint32_t)s, (uint32_t)level, (uint32_t)c, cfg->problem, w);
-        const int d = (int)sao_coord(w[0], n);
-        const double u1 = sao_uniform(w[1]), u2 = sao_uniform(w[2]), u3 = sao_uniform(w[3]);
         /* Step 2: move coordinate d -- a Gaussian step (Box-Muller, cosine branch), or a
          * uniform redraw of the coordinate in [l_d, u_d] with the second uniform. */
+        int d = 0;
+        double u3 = 0.0;
+        const double xp = propose(cfg, level, c, s, s_l, x, &d, &u3);
         const double xd = x[d];
-        double xp;
-        if (cfg->proposal == 1) {
-            xp = apply_box(cfg->lo[d] + u2 * (cfg->hi[d] - cfg->lo[d]), cfg->lo[d], cfg->hi[d], cfg->boundary);
-        } else {
-            const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
-            const double sigma = cfg->sigma_frac * (cfg->hi[d] - cfg->lo[d]) * s_l;
-            xp = apply_box(xd + sigma * z, cfg->lo[d], cfg->hi[d], cfg->boundary);
-        }
 
         /* Delayed acceptance, stage 1 (surrogate only). */
         double dFs = 0.0;
@@ -579,7 +606,7 @@ static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, doubl
 
         /* Metropolis criterion, Eq. "proba" with k_b = 1 (stage 2 of delayed
          * acceptance: the same test on dF - dFs). */
-        const double dFa = dF - dFs;
+        const double dFa = (use_da && da->plant == 1) ? dF + dFs : dF - dFs;
         const int accept = (dFa <= 0.0) || (u3 < exp(-dFa / T));
         if (dF_out) dF_out[s] = dF;
         if (tau_out) tau_out[s] = -T * log(u3); /* the same test written as dF < tau */
@@ -609,7 +636,7 @@ static double chain_level_da(const sao_cfg* cfg, int32_t level, int64_t c, doubl
 /* One chain, one level of delayed acceptance with the surrogate values given. */
 double sao_da_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double ft0,
                           const double* ft_prop, uint32_t* bits, int64_t* n_accept, int64_t* n_true) {
-    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0};
+    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0, 0};
     return chain_level_da(cfg, level, c, x, bits, n_accept, NULL, NULL, &da, n_true);
 }
 
@@ -618,14 +645,24 @@ double sao_da_chain_level(const sao_cfg* cfg, int32_t level, int64_t c, double* 
 double sao_da_chain_level_steps(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double ft0,
                                 const double* ft_prop, uint32_t* bits, int64_t* n_accept, int64_t* n_true,
                                 double* dF_out) {
-    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0};
+    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0, 0};
     return chain_level_da(cfg, level, c, x, bits, n_accept, dF_out, NULL, &da, n_true);
+}
+
+/* The same, also returning each step's threshold tau_out[s] = -T ln u3 (NaN where
+ * stage 1 rejected the move); plant != 0 only in the tests that show a parity
+ * check catches a planted mistake (see sao_da). */
+double sao_da_chain_level_trace(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double ft0,
+                                const double* ft_prop, uint32_t* bits, int64_t* n_accept, int64_t* n_true,
+                                double* dF_out, double* tau_out, int32_t plant) {
+    const sao_da da = {1, ft0, ft_prop, 0.0, 0.0, plant};
+    return chain_level_da(cfg, level, c, x, bits, n_accept, dF_out, tau_out, &da, n_true);
 }
 
 /* The same with the analytic test surrogate a f(x) + b sum_i sin(x_i). */
 double sao_da_chain_level_fn(const sao_cfg* cfg, int32_t level, int64_t c, double* x, double a, double b,
                              uint32_t* bits, int64_t* n_accept, int64_t* n_true) {
-    const sao_da da = {2, 0.0, NULL, a, b};
+    const sao_da da = {2, 0.0, NULL, a, b, 0};
     return chain_level_da(cfg, level, c, x, bits, n_accept, NULL, NULL, &da, n_true);
 }
 

@@ -119,3 +119,49 @@ def test_da_with_wrong_surrogate_still_samples_boltzmann():
     chi2 = float(((obs - exp_) ** 2 / exp_).sum())
     assert chi2 < 80.0, chi2
     assert ev_total < C * L
+
+
+def test_propose_step_is_the_chains_own_move():
+    """propose_step gives the move (d, x'_d) the chain itself makes at step s: applying
+    it wherever the traced chain accepted reproduces the chain's final state exactly
+    (the temperature scaling of the step and the counters are the chain's)."""
+    from paper_2408_00018_gb300 import inputs
+    n, L = 5, 300
+    lo, hi = inputs.box("schwefel", n)
+    p = oracle.Problem("schwefel", n, lo, hi, chains=4, L=L, T0=50.0, rho=0.7, seed=9, mode=1)
+    for level, c in ((0, 1), (3, 2)):
+        x0 = p.init_point(c)
+        _, x_end, _, bits = p.chain_level(level, c, x0, trace=True)
+        acc = np.unpackbits(bits.view(np.uint8), bitorder="little")[:L].astype(bool)
+        x = x0.copy()
+        for s in range(L):
+            d, xp = p.propose_step(level, c, s, x)
+            if acc[s]:
+                x[d] = xp
+        assert np.array_equal(x, x_end)
+
+
+def test_da_trace_equals_steps_and_plant_changes_decisions():
+    """The traced delayed-acceptance replay returns the same bits and differences as
+    the untraced one, tau = -T ln u3 where stage 1 passed (NaN elsewhere), and the
+    planted stage-2 sign error (a hook for the GPU parity tests' own tests) changes
+    the decisions of a chain with a non-constant surrogate."""
+    from paper_2408_00018_gb300 import inputs
+    n, L = 6, 200
+    lo, hi = inputs.box("rot_schwefel", n)
+    Q = inputs.rotation(n, 1)
+    p = oracle.Problem("rot_schwefel", n, lo, hi, chains=3, L=L, T0=5.0, rho=0.8, seed=2, Q=Q, mode=1)
+    rng = np.random.default_rng(0)
+    ftp = rng.standard_normal(L) * 3.0
+    x0 = p.init_point(0)
+    F1, x1, b1, a1, e1, dF1 = p.da_chain_level_steps(0, 0, 0.5, ftp, x0)
+    F2, x2, b2, a2, e2, dF2, tau = p.da_chain_level_trace(0, 0, 0.5, ftp, x0)
+    assert F1 == F2 and np.array_equal(x1, x2) and np.array_equal(b1, b2) and (a1, e1) == (a2, e2)
+    assert np.array_equal(np.isnan(dF1), np.isnan(dF2)) and np.array_equal(dF1[~np.isnan(dF1)], dF2[~np.isnan(dF2)])
+    assert np.array_equal(np.isnan(tau), np.isnan(dF2))
+    key = oracle.stream_key(2, 0)
+    for s in np.nonzero(~np.isnan(tau))[0][:20]:
+        w = oracle.philox([s, 0, 0, 0], key)
+        assert abs(tau[s] + 5.0 * np.log(oracle.uniform(w[3]))) <= 1e-14 * abs(tau[s])
+    _, _, b3, _, _, _, _ = p.da_chain_level_trace(0, 0, 0.5, ftp, x0, plant=1)
+    assert not np.array_equal(b3, b2)
