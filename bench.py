@@ -52,6 +52,61 @@ def sfu_per_step(cost, n, proposal="gaussian"):
     return SFU_PER_STEP[cost] - less
 
 
+def step_ops(cost, n, proposal="gaussian"):
+    """Algorithmic operations of one Metropolis step per measured pipe: the SFU
+    functions by kind (their sum is sfu_per_step), and one Philox4x32-10 block
+    (the step's four random words: coordinate, the two uniforms of the move, the
+    acceptance uniform), whose 32x32 -> 64-bit products run on the integer
+    multiply pipe."""
+    ops = {"lg2": 1, "sqrt": 0, "sin": 0, "cos": 0, "ex2": 0, "philox": 1}  # lg2: tau = -T ln u3
+    if proposal != "uniform":
+        ops["lg2"] += 1   # Box-Muller radius sqrt(-2 ln u1) ...
+        ops["sqrt"] += 1
+        ops["cos"] += 1   # ... and angle cos(2 pi u2)
+    if cost == "schwefel":
+        ops["sqrt"] += 1
+        ops["sin"] += 1
+    elif cost == "rastrigin":
+        ops["cos"] += 1
+    elif cost == "ackley":
+        ops["cos"] += 1
+        ops["sqrt"] += 1
+        ops["ex2"] += 2
+    elif cost == "rot_rastrigin":
+        ops["sin"] += n
+    elif cost == "rot_schwefel":
+        ops["sqrt"] += n
+        ops["sin"] += n
+    assert sum(v for k, v in ops.items() if k != "philox") == sfu_per_step(cost, n, proposal)
+    return ops
+
+
+PIPE_OPS_MEASURED = ("lg2", "sqrt", "sin", "cos", "ex2", "philox", "imad_wide", "imad_hi", "imad_lo", "lop3", "ffma")
+
+
+def measure_pipes(sa):
+    """Operations per clock per SM of each pipe the step uses, measured on this GPU (sa_pipe_rate)."""
+    return {op: sa.pipe_rate(op, 4096)[0] for op in PIPE_OPS_MEASURED}
+
+
+def pipe_roofline(w, pipes, sms, sm_mhz, sweep_ms):
+    """Roofline of the sweep: steps/s that each pipe allows (its measured rate over the
+    algorithmic operations of a level's steps), the binding (lowest) one, and the sweep's
+    achieved steps/s against it."""
+    per_level = {k: 0.0 for k in ("lg2", "sqrt", "sin", "cos", "ex2", "philox")}
+    for p in w.problems:
+        for k, v in step_ops(p["cost"], p["n"], w.proposal).items():
+            per_level[k] += v * p["chains"] * w.L
+    steps_level = sum(p["chains"] for p in w.problems) * w.L
+    clk = sm_mhz * 1e6 * sms
+    t_sfu = sum(per_level[k] / (pipes[k] * clk) for k in ("lg2", "sqrt", "sin", "cos", "ex2"))
+    t_philox = per_level["philox"] / (pipes["philox"] * clk)
+    roofs = {"sfu": steps_level / t_sfu, "philox_imad": steps_level / t_philox}
+    binding = min(roofs, key=roofs.get)
+    achieved = steps_level / (sweep_ms * 1e-3)
+    return achieved, roofs, binding
+
+
 SWEEP_SOURCES = ["sweep_f32.cu", "sweep_f32w.cu", "sweep_rot.cu", "sa_device.cuh", "sa_internal.h"]
 WARMUP_MIN_S = 4.0
 WORKLOADS = ("schwefel_n256", "schwefel_n2", "batched", "rot_rastrigin_n1024", "rot_schwefel_n128")
@@ -359,6 +414,7 @@ def run_ours(args, rank, world, local_rank):
     w = Workload(args.workload, args.levels, args.independent, args.proposal, args.polish_k, args.surrogate)
     h = w.create(sa)
     groups = h.describe()
+    pipes = measure_pipes(sa)  # the roofline's pipe rates, measured on this GPU before the timed region
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     flush.fill_(1)  # the first use of torch's fill kernel may JIT-compile it: not inside the timed region
     sampler = ClockSampler(gpu_id_for(local_rank))
@@ -411,16 +467,24 @@ def run_ours(args, rank, world, local_rank):
     sweep_avg = float(np.mean(sweep_ms))
     sm_mhz = clocks["sm_mhz"] or 2070.0
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    achieved = w.sfu_per_level / (sweep_avg * 1e-3) / 1e12
-    peak = MUFU_PER_CLK_SM * sms * sm_mhz * 1e6 / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "TSFU-op/s (algorithmic SFU ops per Metropolis step: " +
-                        ", ".join(f"{k} {sfu_per_step(k, 1, w.proposal)}" for k in SFU_PER_STEP) + ")",
-                "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(args.workload),
+    achieved, roofs, binding = pipe_roofline(w, pipes, sms, sm_mhz, sweep_avg)
+    sfu_achieved = w.sfu_per_level / (sweep_avg * 1e-3) / 1e12
+    sfu_peak = MUFU_PER_CLK_SM * sms * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(roofs[binding], 1),
+                "unit": "Metropolis steps/s", "frac": round(achieved / roofs[binding], 4),
+                "binding_pipe": binding,
+                "pipes_steps_per_s": {k: round(v, 1) for k, v in roofs.items()},
+                "frac_sfu": round(sfu_achieved / sfu_peak, 4),
+                "traffic": traffic_from_profile(args.workload),
                 "kernel": "sweep (" + ", ".join(g["kind"] for g in groups) + ")",
                 "launch_ms": round(sweep_avg, 4),
                 "sweep_share_of_level": round(float(np.sum(sweep_ms) / np.sum(level_ms)), 4),
-                "peak_basis": f"16 SFU ops/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (median sampled SM clock)"}
+                "algorithmic_ops_per_step": {p["cost"]: step_ops(p["cost"], p["n"], w.proposal)
+                                             for p in w.problems[:1]} if not w.batch else "per problem (step_ops)",
+                "pipe_rates_per_clk_per_sm": {k: round(v, 3) for k, v in pipes.items()},
+                "peak_basis": f"measured pipe rates (sa_pipe_rate, ops/clk/SM) x {sms} SMs x {sm_mhz:.0f} MHz "
+                              "(median sampled SM clock); per pipe, steps/s = rate / algorithmic ops per step; "
+                              "peak = the lowest (binding) pipe"}
     if w.surrogate:  # the timed "sweep" is the whole delayed-acceptance level: training, GEMMs, steps
         roofline.update({"traffic": None, "kernel": "delayed-acceptance level (training, 2 surrogate GEMMs and "
                                                     "the step kernel per step)",

@@ -303,6 +303,19 @@ sa_status sa_trace_states(sa_handle* h, int32_t level, double* X_out, double* F_
 sa_status sa_da_trace(sa_handle* h, int32_t level, float* ft0_out, float* ftp_out);
 
 /*
+ * The surrogate network of the last completed level of a delayed-acceptance
+ * handle (the one that level used: training for the next level runs at its
+ * start), so a test can recompute f~ = mu + sigma MLP(bf16((x - mid) / half))
+ * on its own.  All outputs are host buffers and may be NULL:
+ *   params_out    [sa_mlp_param_count(n)] FP32 parameters (layout of sa_mlp_*)
+ *   ms_out        [2] mu and sigma, the standardisation of the targets
+ *   mid_out       [n] mid-points of the box, inv_half_out [n] 1 / half-widths
+ * Errors: SA_EINVAL if h is not a surrogate handle or no level has run;
+ * SA_ESTATE after an earlier error; SA_ECUDA.
+ */
+sa_status sa_da_network(sa_handle* h, float* params_out, float* ms_out, float* mid_out, float* inv_half_out);
+
+/*
  * Chains sharded over several solvers (e.g. one per GPU), with the exchange of
  * Sec. 2.2.2 done by the caller between levels:
  *   sa_set_chain_offset  before the first level: this handle's chains are the
@@ -481,6 +494,34 @@ sa_status sa_argmin_f64(const double* d_F, int64_t count, int64_t* d_index, doub
  * SA_ECUDA if the address lookup or a launch fails.
  */
 #define SA_ARGMIN_STATIC_MAX_COUNT ((int64_t)1 << 27)
+
+/*
+ * Measurement entry point (the paper has no counterpart): the throughput of
+ * one arithmetic pipe of the current GPU, for the roofline of the sweep
+ * (the minimum over pipes of rate / algorithmic operations per step).  One
+ * kernel per operation runs a full wave of blocks of 256 threads, each
+ * thread eight independent chains of `op` for iters x 4 rounds, timed with
+ * CUDA events; the SM clock it ran at is read from one block (SM cycles over
+ * global-timer nanoseconds).
+ *   op                    one of sa_pipe_op: the SFU approximations the sweep
+ *                         uses, 32x32->64-bit products (IMAD_WIDE), their high
+ *                         and low halves, 3-input logic, FP32 and FP64
+ *                         fused multiply-adds, and whole Philox4x32-10 blocks
+ *   iters                 1 .. 2^20 (a few thousand give stable rates)
+ *   *ops_per_clock_per_sm operations (Philox: blocks) per SM clock cycle, per SM
+ *   *ops_per_second       the same per second of the whole GPU, from CUDA
+ *                         events around the launch (may be NULL)
+ * Synchronous: returns after the measurement; allocates a small stream-ordered
+ * scratch.  Errors: SA_EINVAL on a bad op or iters or a NULL output;
+ * SA_ENOMEM; SA_ECUDA.
+ */
+typedef enum {
+    SA_PIPE_SIN = 0, SA_PIPE_COS = 1, SA_PIPE_LG2 = 2, SA_PIPE_EX2 = 3, SA_PIPE_SQRT = 4, SA_PIPE_RSQRT = 5,
+    SA_PIPE_IMAD_WIDE = 6, SA_PIPE_IMAD_HI = 7, SA_PIPE_IMAD_LO = 8, SA_PIPE_LOP3 = 9, SA_PIPE_FFMA = 10,
+    SA_PIPE_DFMA = 11, SA_PIPE_PHILOX = 12, SA_PIPE_COUNT = 13
+} sa_pipe_op;
+sa_status sa_pipe_rate(int32_t op, int32_t iters, void* stream, double* ops_per_clock_per_sm,
+                       double* ops_per_second);
 sa_status sa_argmin_f64_static(const double* d_F, int64_t count, int64_t* d_index, double* d_value,
                                void* stream);
 

@@ -34,6 +34,7 @@ UNITS = {
     "mlp.cu": [],
     "da.cu": [],
     "crossover.cu": ["-fmad=false"],
+    "pipes.cu": [],
 }
 
 

@@ -12,14 +12,20 @@
 // 32 (w mod 4) + 31, its tile rows; warps w and w + 4 split the columns in
 // halves) and apply the epilogue.  Every wait on an mbarrier is bounded: on expiry the kernel
 // records a timeout in a status word, stops issuing work, waits (bounded) for
-// the copies it issued, frees its TMEM and returns.
+// the copies it issued, frees its TMEM and returns.  The abort path is exact
+// only when those second waits complete: if the wait for the issued matrix
+// operations (or for the issued copies) also runs out, the kernel still frees
+// its TMEM and exits, and what it leaves behind (tensor memory or shared
+// memory written late) is undefined.  SA_ETIMEOUT is reported either way.
 //
 // Shapes: M multiple of 128, N multiple of BN, K multiple of 64 (callers pad).
 #include <cstdint>
+#include <cstdlib>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "gelu.cuh"
 #include "sa_internal.h"
 
 namespace sa {
@@ -36,21 +42,6 @@ constexpr uint32_t kSpin = 1u << 20;  // bounded waits (each try_wait itself blo
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// erf by Hastings' rational approximation (Abramowitz and Stegun, formula 7.1.26):
-// erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x), x >= 0,
-// odd in x; its error is at most 1.5e-7, and this FP32 evaluation (approximate reciprocal
-// and exponential) adds a few units of 1e-7.  The epilogues round GELU to BF16 (8
-// significant bits) or sum it against the head's weights in FP32, far above that error.
-__device__ __forceinline__ float erf_hastings(float x) {
-    const float ax = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    return copysignf(fmaf(-poly, __expf(-ax * ax), 1.0f), x);
-}
-// GELU, erf form: z Phi(z) = z/2 (1 + erf(z / sqrt 2)).
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erf_hastings(z * 0.70710678118654752f)); }
-
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -66,10 +57,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpin; ++i)
+// Bounded wait; with an abort flag it also gives up once another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort_flag = nullptr) {
+    for (uint32_t i = 0; i < kSpin; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *(const volatile int*)abort_flag) return false;
+    }
     return false;
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -123,10 +126,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// test_stall: 0, except in the test of the timeout path: then the matrix-unit
+// thread first waits on a barrier that nothing ever arrives on (polled without
+// blocking, a bounded number of times), so that wait runs out while every
+// copy the producer issued still completes normally.
 template <int BN, class Epi>
 __global__ void __launch_bounds__(kThreads, 2)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, Epi epi,
-                     int* status) {
+                     int* status, uint32_t test_stall) {
     constexpr int kATile = kBM * kBK * 2;
     constexpr int kBTile = BN * kBK * 2;
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns (power of two >= 32)
@@ -138,7 +145,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBTile);
     uint64_t* empty = full + kStages;
     uint64_t* done = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* never = done + 1;  // test_stall: armed by nobody
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -151,6 +159,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             mbar_init(&empty[s], 1);
         }
         mbar_init(done, 1);
+        mbar_init(never, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         int issued = 0;
         for (int kt = 0; kt < KT; ++kt) {
             const int s = kt % kStages;
-            if (kt >= kStages && !mbar_wait(&empty[s], ((kt / kStages) - 1) & 1)) {
+            if (kt >= kStages && !mbar_wait(&empty[s], ((kt / kStages) - 1) & 1, abort_flag)) {
                 atomicExch(abort_flag, 1);
                 break;
             }
@@ -188,6 +197,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         // ---- MMA issuer
         constexpr uint32_t idesc = idesc_bf16(kBM, BN);
         bool ok = true;
+        if (test_stall) {
+            bool got = false;
+            for (int i = 0; i < 4096 && !got; ++i) got = mbar_test_wait(never, 0);
+            if (!got) {
+                atomicExch(abort_flag, 1);
+                ok = false;
+            }
+        }
         for (int kt = 0; kt < KT && ok; ++kt) {
             const int s = kt % kStages;
             if (!mbar_wait(&full[s], (kt / kStages) & 1) || *(volatile int*)abort_flag) {
@@ -229,7 +246,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     // the row's sum: first half + second half, in that order
     if (Epi::kReduces && half == 0 && have && !*(volatile int*)abort_flag) epi.finish(row, n0, acc + red[quad * 32 + lane]);
-    if (threadIdx.x == 0 && *(volatile int*)abort_flag && status) atomicExch(status, 4);  // SA_ETIMEOUT
+    // SA_ETIMEOUT, unless an earlier error of the run is already recorded
+    if (threadIdx.x == 0 && *(volatile int*)abort_flag && status) atomicCAS(status, 0, 4);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
@@ -335,7 +353,7 @@ bool make_tmap(CUtensorMap* m, const void* ptr, int rows, int K, int ld, int box
 template <int BN>
 size_t gemm_smem() {
     constexpr int kStages = stages_for<BN>();
-    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 2) * 8 + 16;
 }
 
 template <int BN, class Epi>
@@ -349,7 +367,11 @@ cudaError_t launch_gemm(const void* A, int lda, const void* B, int ldb, int M, i
     cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(N / BN, M / kBM);
-    gemm_bf16_kernel<BN, Epi><<<grid, kThreads, smem, s>>>(ta, tb, K, epi, status);
+    // Test of the timeout path only: SA_GEMM_TEST_STALL=1 makes one wait of the
+    // matrix-unit thread run out (see test_stall), so the kernel must report SA_ETIMEOUT.
+    const char* t = std::getenv("SA_GEMM_TEST_STALL");
+    const uint32_t test_stall = (t && t[0] == '1') ? 1u : 0u;
+    gemm_bf16_kernel<BN, Epi><<<grid, kThreads, smem, s>>>(ta, tb, K, epi, status, test_stall);
     return cudaGetLastError();
 }
 

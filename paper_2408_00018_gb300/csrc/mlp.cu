@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/sa.h"
+#include "gelu.cuh"
 #include "sa_device.cuh"
 #include "sa_internal.h"
 
@@ -27,10 +28,9 @@ namespace {
 constexpr int kH = kMlpHidden;
 constexpr uint32_t kTagMlpInit = 2u;
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
+// GELU and its derivative: the forms of gelu.cuh, which the GEMM epilogues evaluate.
+__device__ __forceinline__ float gelu(float z) { return gelu_f(z); }
+__device__ __forceinline__ float gelu_grad(float z) { return gelu_grad_f(z); }
 
 __global__ void cast_kernel(const float* __restrict__ p, int n, int np, __nv_bfloat16* W1b, __nv_bfloat16* W2b,
                             __nv_bfloat16* W2tb) {

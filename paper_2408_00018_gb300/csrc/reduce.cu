@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kArgminThreads) argmin_restart_kernel(const Pr
             if (improve) P.scal[kFInc] = b.v;
         }
     } else if (t == 0) {
-        A.run->status = 5;  // SA_ENUMERIC
+        atomicCAS(&A.run->status, 0, 5);  // SA_ENUMERIC (the first error raised in a run is kept)
     }
     if (t == 0) {
         P.log_argmin[level] = ok ? b.i : -1;

@@ -87,6 +87,8 @@ struct Group {
     int n_max = 1;
     bool f64_terms = false;  // FP64 group: a problem keeps per-coordinate factors (twice the state)
     int block = 32;        // threads per block
+    int lanes = 32;        // group layout (kSweepF32Warp): lanes per chain
+    bool cache = true;     // group layout: separable terms cached beside the state
     size_t smem = 0;       // dynamic shared memory per block
     std::vector<int> probs;
     std::vector<WorkItem> items;
@@ -142,7 +144,6 @@ struct sa_handle {
     // delayed acceptance with the surrogate (schedule.surrogate == 1)
     bool da = false;
     DaDev dd{};
-    int* gemm_status = nullptr;  // status word of the tensor-core GEMMs (looked up once, outside capture)
 };
 
 namespace {
@@ -264,6 +265,17 @@ int pick_unroll(int cost, int n) {
     return 1;
 }
 
+// Steps whose randomness the chain-per-thread FP32 sweep draws as one batch
+// (16, or 1 for one group of U steps at a time).  SA_RAND_BATCH overrides it
+// for tuning runs; the decisions are the same for every choice.
+int pick_rand_batch() {
+    if (const char* e = std::getenv("SA_RAND_BATCH")) {
+        const int r = std::atoi(e);
+        if (r == 1 || r == 16) return r;
+    }
+    return 16;
+}
+
 // FP32 sweep layout: one chain per warp (32 consecutive steps per group)
 // pays when a group rarely touches a coordinate twice and the cost has no
 // global running sums.  SA_WARP_MODE=0/1 overrides for tuning runs.
@@ -279,6 +291,30 @@ bool pick_warp_mode(int cost, int n) {
     // (2.05 ms vs 2.11 ms per level on the Schwefel workload); above that the
     // thread layout's shared memory per chain leaves too few warps per SM.
     return n > 256;
+}
+
+// Group layout of the FP32 sweep for a dimension bucket: lanes per chain,
+// cached terms, threads per block.  The block holds about 64 KiB of chain
+// state (three blocks per SM) and at least 8 chains.  SA_CHAIN_LANES (2, 4, 8,
+// 32), SA_TERM_CACHE (0/1) and SA_GROUP_BLOCK (threads) override it for
+// tuning runs; every choice gives the same decisions.
+struct GroupLayout { int lanes; bool cache; int block; };
+GroupLayout pick_group_layout(int n) {
+    GroupLayout g{4, false, 0};
+    if (const char* e = std::getenv("SA_CHAIN_LANES")) {
+        const int v = std::atoi(e);
+        if (v == 2 || v == 4 || v == 8 || v == 32) g.lanes = v;
+    }
+    if (const char* e = std::getenv("SA_TERM_CACHE")) g.cache = e[0] == '1';
+    if (g.lanes == 32) g.cache = true;
+    if (g.lanes == 2) g.cache = false;
+    const int per_chain = (g.cache ? 2 : 1) * 4 * (n + 1);
+    int b = (65536 / per_chain) * g.lanes;
+    if (const char* e = std::getenv("SA_GROUP_BLOCK")) b = std::atoi(e);
+    b = (b / 32) * 32;
+    b = std::min(256, std::max(b, std::max(32, 8 * g.lanes)));
+    g.block = b;
+    return g;
 }
 
 // Bound on the FP32 error of one accepted step's dF over the whole box (the
@@ -298,10 +334,12 @@ cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
     const int num = (int)g.items.size();
     if (num == 0) return cudaSuccess;
     if (g.kind == kSweepF64) return launch_sweep_f64(a, num, g.block, g.smem, s);
-    if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.smem, s);
+    if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.lanes, g.cache, g.block, g.smem, s);
     if (g.kind == kSweepRot) return launch_sweep_rot(a, num, g.smem, s);
     if (g.kind == kSweepDA)
-        return launch_da_level(a, h->dd, h->probs[h->dd.problem].chains, h->L, kDaTrainSteps, kDaLr, h->gemm_status, s);
+        // the GEMMs report a timeout in the run's own status word, which every sa_run reads
+        return launch_da_level(a, h->dd, h->probs[h->dd.problem].chains, h->L, kDaTrainSteps, kDaLr,
+                               &h->d_run->status, s);
     return launch_sweep_f32(a, num, g.block, g.smem, s);
 }
 
@@ -332,7 +370,7 @@ cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
 // Work items of a group for its current block shape (tiles of one problem's
 // chains), largest problems first; uploaded on the handle's stream.
 sa_status set_group_items(sa_handle* h, Group& g) {
-    const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block()
+    const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block(g.lanes, g.block)
                          : (g.kind == kSweepRot || g.kind == kSweepDA) ? sweep_rot_chains_per_block()
                                                                        : g.block;
     std::vector<int> order = g.probs;
@@ -351,14 +389,14 @@ sa_status set_group_items(sa_handle* h, Group& g) {
 }
 
 size_t group_smem(const Group& g) {
-    if (g.kind == kSweepF32Warp) return sweep_f32w_smem_bytes(g.n_max);
+    if (g.kind == kSweepF32Warp) return sweep_f32w_smem_bytes(g.n_max, g.lanes, g.cache, g.block);
     if (g.kind == kSweepRot) return sweep_rot_smem_bytes(g.n_max);
     if (g.kind == kSweepF64) return sweep_f64_smem_bytes(g.n_max, g.block, g.f64_terms);
     return sweep_f32_smem_bytes(g.n_max, g.block);
 }
 
 cudaError_t group_set_smem(const Group& g) {
-    if (g.kind == kSweepF32Warp) return sweep_f32w_set_smem(g.smem);
+    if (g.kind == kSweepF32Warp) return sweep_f32w_set_smem(g.lanes, g.cache, g.smem);
     if (g.kind == kSweepRot) return sweep_rot_set_smem(g.smem);
     if (g.kind == kSweepF64) return sweep_f64_set_smem(g.smem);
     return sweep_f32_set_smem(g.smem);
@@ -523,7 +561,6 @@ sa_status setup_da(sa_handle* h) {
     mlp_work_carve(reinterpret_cast<void*>(((uintptr_t)wbase + 1023) & ~(uintptr_t)1023), D.batch, D.np, D.work);
     D.mid = mid;
     D.inv_half = ih;
-    if (!(h->gemm_status = gemm_status_ptr())) return SA_ECUDA;
     D.mlp.n = n;
     D.mlp.np = D.np;
     D.b3 = D.mlp.p + mlp_offsets(n).b3;
@@ -620,8 +657,14 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (Group& g : h->groups) {
         for (int p : g.probs) g.n_max = std::max(g.n_max, h->probs[p].n);
-        g.block = g.kind == kSweepF32Warp ? 256 : g.kind == kSweepRot ? 32 * sweep_rot_chains_per_block()
-                                                                        : pick_block(h->precision, g.n_max);
+        if (g.kind == kSweepF32Warp) {
+            const GroupLayout gl = pick_group_layout(g.n_max);
+            g.lanes = gl.lanes;
+            g.cache = gl.cache;
+        }
+        g.block = g.kind == kSweepF32Warp ? pick_group_layout(g.n_max).block
+                  : g.kind == kSweepRot   ? 32 * sweep_rot_chains_per_block()
+                                          : pick_block(h->precision, g.n_max);
         g.smem = g.kind == kSweepDA ? 0 : group_smem(g);
         if ((int)g.smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
         if (g.kind != kSweepDA && group_set_smem(g) != cudaSuccess) return SA_ECUDA;
@@ -678,6 +721,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         d.hi_u = hi32[0];
         d.sig_u = sig32[0];
         d.unroll = pick_unroll(hp.cost, n);
+        d.rand_batch = pick_rand_batch();
         d.warp_mode = 0;
         d.kappa = step_kappa(hp.cost, n, lo32, hi32);
         double *dlo, *dhi, *dsig, *xb64, *xinc, *scal, *pval, *lf, *lfi;
@@ -1194,6 +1238,21 @@ sa_status sa_da_trace(sa_handle* h, int32_t level, float* ft0_out, float* ftp_ou
     return SA_OK;
 }
 
+sa_status sa_da_network(sa_handle* h, float* params_out, float* ms_out, float* mid_out, float* inv_half_out) {
+    if (!h) return SA_EINVAL;
+    if (h->failed != SA_OK) return SA_ESTATE;
+    if (!h->da || h->levels_done < 1) return SA_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SA_ECUDA);
+    const int n = h->probs[h->dd.problem].n;
+    const int64_t P = mlp_offsets(n).total;
+    if ((params_out && cudaMemcpy(params_out, h->dd.mlp.p, sizeof(float) * P, cudaMemcpyDeviceToHost)) ||
+        (ms_out && cudaMemcpy(ms_out, h->dd.ms, sizeof(float) * 2, cudaMemcpyDeviceToHost)) ||
+        (mid_out && cudaMemcpy(mid_out, h->dd.mid, sizeof(float) * n, cudaMemcpyDeviceToHost)) ||
+        (inv_half_out && cudaMemcpy(inv_half_out, h->dd.inv_half, sizeof(float) * n, cudaMemcpyDeviceToHost)))
+        return fail(h, SA_ECUDA);
+    return SA_OK;
+}
+
 sa_status sa_level_log(sa_handle* h, int32_t problem, int64_t* argmin, double* f_level, double* f_inc, int64_t* t_ns,
                        int32_t cap, int32_t* count) {
     if (!h || cap < 0) return SA_EINVAL;
@@ -1414,11 +1473,13 @@ sa_status sa_autotune(sa_handle* h, double* ms_out) {
     double total = 0.0;
     static const int kBudgets[] = {16384, 32768, 65536, 114688};
     static const int kUnrolls[] = {1, 2, 4};
-    struct Shape { int kind, block, unroll; };
+    struct Shape { int kind, block, unroll, lanes; bool cache; };
     // Apply a launch shape to a group (block, shared memory, work items, per-problem unroll).
     auto apply = [h](Group& g, const Shape& c) -> sa_status {
         g.kind = c.kind;
         g.block = c.block;
+        g.lanes = c.lanes;
+        g.cache = c.cache;
         g.smem = group_smem(g);
         if (group_set_smem(g) != cudaSuccess) return SA_ECUDA;
         sa_status s2 = set_group_items(h, g);
@@ -1438,11 +1499,23 @@ sa_status sa_autotune(sa_handle* h, double* ms_out) {
             b = std::min(256, std::max(32, (b / 32) * 32));
             if (b == last_block) continue;
             last_block = b;
-            for (int u : kUnrolls) cands.push_back(Shape{kSweepF32, b, u});
+            for (int u : kUnrolls) cands.push_back(Shape{kSweepF32, b, u, 32, true});
         }
         bool eligible = true;
         for (int p : g.probs) eligible = eligible && warp_eligible(h->probs[p].cost);
-        if (eligible) cands.push_back(Shape{kSweepF32Warp, 256, 1});
+        if (eligible) {
+            // group layouts: lanes per chain x cached terms, ~64 KiB of state per block
+            static const int kLanes[] = {2, 4, 8, 32};
+            for (int ln : kLanes)
+                for (int ch = 0; ch < 2; ++ch) {
+                    if (!sweep_f32w_layout_ok(ln, ch == 1)) continue;
+                    const int per_chain = (ch ? 2 : 1) * 4 * (g.n_max + 1);
+                    int b = ((65536 / per_chain) * ln / 32) * 32;
+                    b = std::min(256, std::max(b, std::max(32, 8 * ln)));
+                    if ((int)sweep_f32w_smem_bytes(g.n_max, ln, ch == 1, b) > 227 * 1024) continue;
+                    cands.push_back(Shape{kSweepF32Warp, b, 1, ln, ch == 1});
+                }
+        }
         double best = 1e30;
         Shape best_shape = cands[0];
         for (const Shape& c : cands) {
@@ -1484,9 +1557,10 @@ int32_t sa_describe(const sa_handle* h, char* buf, size_t len) {
         const Group& g = h->groups[i];
         int u = g.probs.empty() ? 1 : h->pd[g.probs[0]].unroll;
         char tmp[256];
-        std::snprintf(tmp, sizeof(tmp), "%s{\"kind\":\"%s\",\"problems\":%zu,\"n_max\":%d,\"block\":%d,\"smem\":%zu,\"unroll\":%d,\"items\":%zu}",
+        std::snprintf(tmp, sizeof(tmp), "%s{\"kind\":\"%s\",\"problems\":%zu,\"n_max\":%d,\"block\":%d,\"smem\":%zu,\"unroll\":%d,\"items\":%zu,\"lanes\":%d,\"cache\":%d}",
                       i ? "," : "", g.kind == kSweepF64 ? "fp64" : g.kind == kSweepF32Warp ? "fp32_warp" : g.kind == kSweepRot ? "rot_warp" : "fp32_thread",
-                      g.probs.size(), g.n_max, g.block, g.smem, u, g.items.size());
+                      g.probs.size(), g.n_max, g.block, g.smem, u, g.items.size(),
+                      g.kind == kSweepF32Warp ? g.lanes : (g.kind == kSweepF32 ? 1 : 32), g.cache ? 1 : 0);
         s += tmp;
     }
     s += "]";

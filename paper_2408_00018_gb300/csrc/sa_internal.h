@@ -32,6 +32,7 @@ struct ProbDev {
     int32_t nblk_argmin;  // blocks of the argmin kernel for this problem
     int32_t uniform;      // 1: every coordinate has the same [lo, hi] (scalars below are used)
     int32_t unroll;       // steps evaluated together per chain in the FP32 sweep (1, 2 or 4)
+    int32_t rand_batch;   // FP32 chain-per-thread sweep: steps whose randomness is drawn as one batch (1 or 16)
     int32_t warp_mode;    // FP32 sweep: 0 = one chain per thread, 1 = one chain per warp
     float kappa;          // warp mode: bound on the FP32 error of one accepted step's dF
     float lo_u, hi_u, sig_u;  // the uniform box and sigma_frac (hi - lo) in FP32
@@ -154,10 +155,15 @@ size_t crossover_blocks(int64_t chains);
 cudaError_t launch_reset(ProbDev* probs, int num_probs, RunDev* run, cudaStream_t s);
 cudaError_t launch_stamp_start(RunDev* run, cudaStream_t s);
 cudaError_t sweep_f32_set_smem(size_t bytes);
-cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, size_t smem, cudaStream_t s);
-size_t sweep_f32w_smem_bytes(int n);
-cudaError_t sweep_f32w_set_smem(size_t bytes);
-int sweep_f32w_chains_per_block();
+// Group layout of the FP32 sweep: `lanes` (G) lanes run one chain, `cache` keeps the
+// separable terms beside the state; the built (G, cache) pairs are (32, on), (8, on/off),
+// (4, on/off) and (2, off).  block: threads per block (a multiple of 32, <= 256).
+bool sweep_f32w_layout_ok(int lanes, bool cache);
+cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, int lanes, bool cache, int block, size_t smem,
+                              cudaStream_t s);
+size_t sweep_f32w_smem_bytes(int n, int lanes, bool cache, int block);
+cudaError_t sweep_f32w_set_smem(int lanes, bool cache, size_t bytes);
+int sweep_f32w_chains_per_block(int lanes, int block);
 cudaError_t sweep_f64_set_smem(size_t bytes);
 cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, const double* Q, int k, const double* x0,
                        double* x_out, double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s);

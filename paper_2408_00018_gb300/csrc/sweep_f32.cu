@@ -156,14 +156,16 @@ struct Ctx {
     int boundary;
     float neg_T_ln2;  // -T ln 2: tau = -T ln u3 = neg_T_ln2 * log2(u3)
     float kappa;      // bound on the FP32 error of any accepted step's dF over the box (Schwefel, Rastrigin)
-    uint32_t level, chain, pid, key0, key1;
+    PhiloxFixed pf;     // the parts of the step's Philox rounds 1-2 fixed for the chain and level
+    const uint32_t* rk; // the sweep key of every Philox round (kernel parameters)
 };
 
 // Randomness of step s: coordinate, Gaussian deviate, acceptance threshold.
 // UP: the move is a uniform redraw of the coordinate (z = u2) instead of a Gaussian step.
 template <bool UP>
 __device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
-    const uint4 w = philox4x32_10(make_uint4(s, C.level, C.chain, C.pid), C.key0, C.key1);
+    // = philox4x32_10((s, level, chain, problem), key) bit for bit
+    const uint4 w = philox_step(s, C.pf, C.rk);
     p.d = coord_of(w.x, C.n);
     const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
     if (UP) {
@@ -243,7 +245,14 @@ __device__ __forceinline__ bool conflicts(int dk, int dj) {
     return dk == dj;
 }
 
-template <int COST, bool UB, int U, bool UP>
+// R: steps whose randomness (Philox block, coordinate, Gaussian deviate,
+// acceptance threshold) is drawn together before any of them is evaluated.
+// The randomness does not depend on the chain's state, so the R draws are
+// independent of each other and of the evaluations: drawing them as one batch
+// gives the integer-multiply pipe (the 32 x 32 -> 64-bit products of Philox)
+// R independent instruction streams per thread, where the sweep otherwise
+// has only the U speculative steps.  The decisions are unchanged.
+template <int COST, bool UB, int U, bool UP, int R>
 __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
                            float* xs, float* slo, float* shi, float* ssig, double* red, int* cand, int* ncand) {
     const int t = threadIdx.x, B = blockDim.x, n = P.n;
@@ -309,11 +318,8 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     C.boundary = A.boundary;
     C.neg_T_ln2 = (float)(-T * 0.69314718055994531);
     C.kappa = P.kappa;
-    C.level = (uint32_t)level;
-    C.chain = (uint32_t)c + P.cid0;
-    C.pid = P.pid;
-    C.key0 = A.key0;
-    C.key1 = A.key1;
+    C.rk = A.rk;
+    C.pf = philox_prep((uint32_t)level, (uint32_t)c + P.cid0, P.pid, A.rk);
 
     const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
@@ -346,6 +352,27 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             }
             return acc;
         };
+        if (R > U) {
+            for (; s + R <= L; s += R) {
+                Step p[R];
+#pragma unroll
+                for (int j = 0; j < R; ++j) propose<UP>(C, (uint32_t)(s + j), p[j]);
+#pragma unroll
+                for (int g = 0; g < R; g += U) {
+#pragma unroll
+                    for (int j = 0; j < U; ++j) evaluate<COST, UB, UP>(C, st, p[g + j]);
+                    bool acc[U];
+#pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        bool dirty = false;
+#pragma unroll
+                        for (int k = 0; k < j; ++k) dirty |= acc[k] && conflicts<COST>(p[g + k].d, p[g + j].d);
+                        if (dirty) evaluate<COST, UB, UP>(C, st, p[g + j]);
+                        acc[j] = commit(p[g + j], s + g + j);
+                    }
+                }
+            }
+        }
         if (U > 1) {
             for (; s + U <= L; s += U) {
                 Step p[U];
@@ -430,23 +457,39 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     if (t == 0) atomicAdd(P.accepts, (unsigned long long)a1);
 }
 
+template <int COST, bool UB, bool UP, int R>
+__device__ __forceinline__ void dispatch_r(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
+                                           float* xs, float* slo, float* shi, float* ssig, double* red, int* cand,
+                                           int* ncand, int u) {
+    if (UP || COST == kAckley || u <= 1)
+        sweep_tile<COST, UB, 1, UP, R>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+    else if (u >= 4 && R == 1)  // (a batch of randomness takes U = 2)
+        sweep_tile<COST, UB, 4, UP, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+    else
+        sweep_tile<COST, UB, 2, UP, R>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+}
+
 template <int COST>
 __device__ __forceinline__ void dispatch_u(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level,
                                            float* xs, float* slo, float* shi, float* ssig, double* red, int* cand,
                                            int* ncand) {
     const bool ub = P.uniform != 0;
     const int u = (COST == kAckley) ? 1 : P.unroll;
+    const bool batch = P.rand_batch > 1;
     if (A.proposal == 1) {  // uniform redraws: one step at a time
-        if (ub) sweep_tile<COST, true, 1, true>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else sweep_tile<COST, false, 1, true>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-    } else if (ub) {
-        if (u >= 4) sweep_tile<COST, true, 4, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else if (u == 2) sweep_tile<COST, true, 2, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else sweep_tile<COST, true, 1, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        if (batch) {
+            if (ub) dispatch_r<COST, true, true, 16>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, 1);
+            else dispatch_r<COST, false, true, 16>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, 1);
+        } else {
+            if (ub) dispatch_r<COST, true, true, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, 1);
+            else dispatch_r<COST, false, true, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, 1);
+        }
+    } else if (batch) {
+        if (ub) dispatch_r<COST, true, false, 16>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, u);
+        else dispatch_r<COST, false, false, 16>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, u);
     } else {
-        if (u >= 4) sweep_tile<COST, false, 4, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else if (u == 2) sweep_tile<COST, false, 2, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
-        else sweep_tile<COST, false, 1, false>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand);
+        if (ub) dispatch_r<COST, true, false, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, u);
+        else dispatch_r<COST, false, false, 1>(A, P, it, level, xs, slo, shi, ssig, red, cand, ncand, u);
     }
 }
 

@@ -1,27 +1,40 @@
 // sweep_f32w.cu -- Metropolis sweep of one temperature level, FP32 state,
-// one Markov chain per warp.
+// one Markov chain per group of G lanes (G = 2, 4, 8 or 32; G = 32 is one
+// chain per warp).
 //
-// The 32 lanes of a warp run 32 consecutive steps s0 .. s0+31 of the same
+// The G lanes of a group run G consecutive steps s0 .. s0+G-1 of the same
 // chain (the kernel of Listing 4, one step per lane): each lane draws its
 // Philox block, proposes its move and evaluates its energy difference from
 // the chain's state at the start of the group.  The group is then committed
 // in step order.  A lane whose coordinate (for Rosenbrock: the coordinate or
-// a neighbour) is also touched by an earlier lane of the group is "pending":
+// a neighbour) is also touched by an earlier lane of its group is "pending":
 // the earlier lanes are decided first, then the pending lanes are
 // re-evaluated one at a time, in step order, from the state those decisions
 // left.  Every other lane's speculative evaluation read exactly the state
 // the sequential chain would have read, so the decisions equal those of the
-// one-step-at-a-time chain.  With n coordinates about 31*32/(2n) lanes per
-// group are pending, so this layout is used for n >= 48.
+// one-step-at-a-time chain.  With n coordinates about G(G-1)/(2n) lanes per
+// group are pending.
 //
-// The chain's state is one row x[0..n) of shared memory per warp.  Only
-// separable costs without global running sums use this kernel (Schwefel,
-// Rastrigin, Rosenbrock); Ackley keeps one chain per thread.
+// The group size trades the two limits of the sweep against each other.  A
+// chain's state (n floats, plus n cached terms) lives in shared memory, so
+// the shared memory of an SM bounds the chains it holds; G lanes per chain
+// multiply the warps that hide the latency of the step's dependent Philox
+// rounds and SFU functions by G, while the pending lanes' re-evaluations
+// grow with G.  At n = 256 one chain per thread leaves ~1.5 warps per
+// scheduler; G = 4 gives four times as many at ~2% pending lanes.
+//
+// The chain's state is one row x[0..n) of shared memory per group (slot n
+// absorbs masked writes), optionally with the cache h[k] = term(x[k]) of the
+// separable costs (CACHE).  Only separable costs without global running sums
+// use this kernel (Schwefel, Rastrigin, Rosenbrock); Ackley keeps one chain
+// per thread.
 //
 // End of level: as in the chain-per-thread kernel, each chain holds
 // F_start + dS and a running bound e on its FP32 error; the chains whose
-// interval can contain the level minimum are re-evaluated in FP64 (lanes over
-// coordinates) and write their state for the argmin.
+// interval can contain the level minimum are re-evaluated in FP64, one warp
+// per candidate with the lane-strided partial sums and butterfly of the
+// chain-per-thread kernel (so the FP64 value does not depend on the layout),
+// and write their state for the argmin.
 #include <cfloat>
 #include <cmath>
 #include <math_constants.h>
@@ -32,11 +45,10 @@
 namespace sa {
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kMaxBlock = 256;
 #ifndef SA_F32W_MIN_BLOCKS
-#define SA_F32W_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
+#define SA_F32W_MIN_BLOCKS 3  // resident blocks of 256 threads per SM the register budget is sized for
 #endif
-constexpr int kWarps = kBlock / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // A register copy the compiler cannot trace back to the kernel-parameter
@@ -54,6 +66,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+template <int G> struct Log2;
+template <> struct Log2<2> { static constexpr int v = 1; };
+template <> struct Log2<4> { static constexpr int v = 2; };
+template <> struct Log2<8> { static constexpr int v = 3; };
+template <> struct Log2<32> { static constexpr int v = 5; };
+
 struct WStep {
     int d;
     float z, tau, xo, xp, dF, xm, xq, hp;
@@ -61,17 +79,18 @@ struct WStep {
 
 // Term of one coordinate in the separable costs that keep a per-coordinate
 // cache: Schwefel h(t) = t sin sqrt|t| (f = -(1/n) sum h), Rastrigin
-// g(t) = t^2 - 10 cos 2 pi t.  The cache holds exactly this function's value
-// at the stored coordinate, so reading it equals recomputing it.
+// g(t) = t^2 - 10 cos 2 pi t.  The product is rounded on its own
+// (__fmul_rn is never merged into a later addition), so the value is the
+// same whether it is read from the cache or recomputed inside a difference.
 template <int COST>
 __device__ __forceinline__ float term(float t) {
-    if (COST == kSchwefel) return t * sin_reduced(sqrt_approx(fabsf(t)));
+    if (COST == kSchwefel) return __fmul_rn(t, sin_reduced(sqrt_approx(fabsf(t))));
     return g_rastrigin(t);
 }
 
 struct WCtx {
-    float* xw;  // the warp's chain state, x[0..n)
-    float* hw;  // Schwefel/Rastrigin: term(x[k]) for every coordinate
+    float* xw;  // the group's chain state, x[0..n)
+    float* hw;  // Schwefel/Rastrigin with the cache: term(x[k]) for every coordinate
     int n;
     float inv_n;
     float lo_u, hi_u, sig_u;
@@ -100,7 +119,7 @@ __device__ __forceinline__ void wpropose(const WCtx& C, uint32_t s, WStep& p) {
 }
 
 // Move and energy difference from the chain's current state.
-template <int COST, bool UB, bool UP>
+template <int COST, bool UB, bool UP, bool CACHE>
 __device__ __forceinline__ void wevaluate(const WCtx& C, WStep& p) {
     const int d = p.d;
     const float xo = C.xw[d];
@@ -112,12 +131,10 @@ __device__ __forceinline__ void wevaluate(const WCtx& C, WStep& p) {
     xp = fminf(fmaxf(xp, lo), hi);
     p.xo = xo;
     p.xp = xp;
-    if (COST == kSchwefel) {
+    if (COST == kSchwefel || COST == kRastrigin) {
+        const float ho = CACHE ? C.hw[d] : term<COST>(xo);
         p.hp = term<COST>(xp);
-        p.dF = (C.hw[d] - p.hp) * C.inv_n;
-    } else if (COST == kRastrigin) {
-        p.hp = term<COST>(xp);
-        p.dF = p.hp - C.hw[d];
+        p.dF = COST == kSchwefel ? (ho - p.hp) * C.inv_n : p.hp - ho;
     } else {
         float dummy = 0.0f, before = 0.0f, after = 0.0f;
         p.xm = d > 0 ? C.xw[d - 1] : 0.0f;
@@ -144,15 +161,28 @@ __device__ __forceinline__ void partial64(const float* xw, int n, int k, double&
     else if (k + 1 < n) p1 += rosen64(x, (double)xw[k + 1]);
 }
 
+// Sum over the G lanes of a group (every lane of the group receives it).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
 struct ChainEnd {
     double Fa, ec;   // F_start + dS and the bound on its error
     unsigned nacc;   // accepted moves
 };
 
-template <int COST, bool UB, bool UP>
-__device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, int level, float* xw, float* hw,
-                               const float* slo, const float* shi, const float* ssig, double* block_hi) {
+// One level of the chain c held by the calling group (all 32 lanes of the
+// warp call it together; `mine` is false for a group without a chain, whose
+// lanes take part in the warp-wide votes only).
+template <int COST, bool UB, bool UP, int G, bool CACHE>
+__device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c, bool mine, int level, float* xw,
+                                float* hw, const float* slo, const float* shi, const float* ssig) {
     const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);      // position in the group = step offset
+    const int gi = lane / G;            // group within the warp
     const int n = P.n;
     const int64_t gc = P.chain_base + c;
     const double T = A.T_tab[level];
@@ -160,8 +190,10 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
     const float inv_n = 1.0f / (float)n;
 
     // ---- state at the start of the level
-    if (level == 0) {
-        for (int k = 4 * lane; k < n; k += 128) {
+    if (!mine) {
+        for (int k = gl; k <= n; k += G) xw[k] = 0.0f;
+    } else if (level == 0) {
+        for (int k = 4 * gl; k < n; k += 4 * G) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)(k >> 2), 0u, (uint32_t)c + P.cid0, P.pid), A.ikey0, A.ikey1);
             const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -174,43 +206,44 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
             }
         }
     } else if (own_start(A, level)) {  // the chain's own state (no exchange before this level)
-        for (int k = lane; k < n; k += 32) xw[k] = A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
+        for (int k = gl; k < n; k += G) xw[k] = A.X32[P.x_base + (size_t)k * (size_t)P.chains + (size_t)c];
     } else {
-        for (int k = lane; k < n; k += 32) xw[k] = P.x_best32[k];
+        for (int k = gl; k < n; k += G) xw[k] = P.x_best32[k];
     }
     __syncwarp();
-    if (COST == kSchwefel || COST == kRastrigin) {
-        for (int k = lane; k < n; k += 32) hw[k] = term<COST>(xw[k]);
+    if (CACHE && (COST == kSchwefel || COST == kRastrigin)) {
+        for (int k = gl; k < n; k += G) hw[k] = term<COST>(xw[k]);
         __syncwarp();
     }
 
-    double Fs;
+    double Fs = 0.0;
     float es = 0.0f;
-    if (level == 0 || own_start(A, level)) {
-        // FP32 value of f at the start point with a bound on its error
+    if (level == 0 || own_start(A, level)) {  // warp-uniform
+        // FP32 value of f at the start point with a bound on its error; the
+        // group sums run on every lane of the warp (a group without a chain adds zeros)
         float sum = 0.0f, sabs = 0.0f, e = 0.0f;
-        for (int k = lane; k < n; k += 32) {
-            const float x = xw[k];
-            float g;
-            if (COST == kSchwefel) {
-                g = hw[k];
-                e += fabsf(x) * fmaf(sqrt_approx(fabsf(x)), 4.8e-7f, 2.6e-6f);
-            } else if (COST == kRastrigin) {
-                g = hw[k];
-                e += 2.4e-5f + fabsf(g) * 1.2e-7f;
-            } else {
-                g = k + 1 < n ? rosen_term(x, xw[k + 1], e) : 0.0f;
+        if (mine) {
+            for (int k = gl; k < n; k += G) {
+                const float x = xw[k];
+                float g;
+                if (COST == kSchwefel) {
+                    g = term<COST>(x);
+                    e += fabsf(x) * fmaf(sqrt_approx(fabsf(x)), 4.8e-7f, 2.6e-6f);
+                } else if (COST == kRastrigin) {
+                    g = term<COST>(x);
+                    e += 2.4e-5f + fabsf(g) * 1.2e-7f;
+                } else {
+                    g = k + 1 < n ? rosen_term(x, xw[k + 1], e) : 0.0f;
+                }
+                sum += g;
+                sabs += fabsf(g);
             }
-            sum += g;
-            sabs += fabsf(g);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sum += __shfl_xor_sync(kFull, sum, o);
-            sabs += __shfl_xor_sync(kFull, sabs, o);
-            e += __shfl_xor_sync(kFull, e, o);
-        }
-        const float rnd = ((float)(n / 32) + 6.0f) * 1.2e-7f;  // sequential + tree summation rounding
+        sum = group_sum<G>(sum);
+        sabs = group_sum<G>(sabs);
+        e = group_sum<G>(e);
+        // sequential sums of ceil(n/G) terms, then log2 G tree levels
+        const float rnd = ((float)((n + G - 1) / G) + (float)Log2<G>::v + 1.0f) * 1.2e-7f;
         if (COST == kSchwefel) {
             const float F = -sum * inv_n;
             Fs = (double)F;
@@ -250,41 +283,45 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
     C.rk = rk;
     const float kappa = P.kappa;
 
-    const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
+    const bool tracing = mine && (A.bits != nullptr) && level < A.trace_levels;
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     const unsigned lt = lanemask_lt();
-    // Per-lane sums of the accepted differences (lane l holds the steps
-    // s = l mod 32) and of the bounds on their FP32 errors; reduced once at the end.
+    const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (gi * G);
+    // Per-lane sums of the accepted differences (lane gl holds the steps
+    // s = gl mod G) and of the bounds on their FP32 errors; reduced once at the end.
     float dS = 0.0f, e = 0.0f;
-    unsigned nacc = 0;
+    unsigned nacc = 0, bw = 0;
     const int L = (int)opaque((uint32_t)A.L);
-    for (int s0 = 0; s0 < L; s0 += 32) {
-        const int s = s0 + lane;
-        const bool live = s < L;
+    for (int s0 = 0; s0 < L; s0 += G) {
+        const int s = s0 + gl;
+        const bool live = mine && s < L;
         WStep p;
         wpropose<UP>(C, (uint32_t)s, p);
-        wevaluate<COST, UB, UP>(C, p);
+        wevaluate<COST, UB, UP, CACHE>(C, p);
         // earlier lanes of the group whose step can change what this lane's evaluation read
         unsigned earlier;
-        const int key = live ? p.d : -1 - lane;
         if (COST == kRosenbrock) {
+            const int key = live ? p.d : -1 - lane;
             earlier = 0u;
-            for (int k = 0; k < 31; ++k) {
-                const int dk = __shfl_sync(kFull, key, k);
-                earlier |= ((k < lane) && dk >= p.d - 1 && dk <= p.d + 1) ? (1u << k) : 0u;
+#pragma unroll
+            for (int k = 0; k < G - 1; ++k) {
+                const int dk = __shfl_sync(kFull, key, k, G);
+                earlier |= ((k < gl) && dk >= p.d - 1 && dk <= p.d + 1) ? (1u << (gi * G + k)) : 0u;
             }
         } else {
+            // the group's index in the key keeps the groups of a warp apart
+            const int key = live ? ((gi << 24) | p.d) : -1 - lane;
             earlier = __match_any_sync(kFull, key) & lt;  // every lane takes part, live or not
         }
         const bool pend = live && earlier != 0u;
         bool acc = live && !pend && (p.dF < p.tau);
         __syncwarp();  // every speculative read happens before any write
         // Branch-free commit: lanes that do not accept write to the scratch
-        // slot n of their row.  Accepting lanes write distinct coordinates
-        // (each is the first lane of the group to touch its coordinate).
+        // slot n of their row.  Accepting lanes of a group write distinct
+        // coordinates (each is the first lane of its group to touch its coordinate).
         int slot = acc ? p.d : n;
         xw[slot] = p.xp;
-        if (COST == kSchwefel || COST == kRastrigin) hw[slot] = p.hp;
+        if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = p.hp;
         // pending lanes, in rounds: a lane goes once every earlier conflicting
         // lane is decided; the whole warp evaluates, the going lanes keep it
         unsigned undecided = __ballot_sync(kFull, pend);
@@ -292,14 +329,14 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
             __syncwarp();
             const bool go = ((undecided >> lane) & 1u) && (earlier & undecided) == 0u;
             WStep q = p;
-            wevaluate<COST, UB, UP>(C, q);
+            wevaluate<COST, UB, UP, CACHE>(C, q);
             const bool a2 = q.dF < q.tau;
             if (go) p = q;
             acc = go ? a2 : acc;
             __syncwarp();
             slot = (go && a2) ? q.d : n;
             xw[slot] = q.xp;
-            if (COST == kSchwefel || COST == kRastrigin) hw[slot] = q.hp;
+            if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = q.hp;
             undecided &= ~__ballot_sync(kFull, go);
         }
         __syncwarp();
@@ -307,119 +344,92 @@ __device__ ChainEnd warp_chain(const SweepArgs& A, const ProbDev& P, int64_t c, 
         dS += acc ? p.dF : 0.0f;
         e += acc ? bnd + fabsf(dS) * 1.2e-7f : 0.0f;
         nacc += acc ? 1u : 0u;
-        if (tracing) {
-            const unsigned accm = __ballot_sync(kFull, acc);
-            if (lane == 0) mybits[s0 >> 5] = accm;
+        if (A.bits != nullptr && level < A.trace_levels) {  // warp-uniform
+            const unsigned accm = __ballot_sync(kFull, acc) & gmask;
+            bw |= (G == 32 ? accm : accm >> (gi * G)) << (s0 & 31);
+            if (((s0 & 31) + G == 32) || s0 + G >= L) {
+                if (tracing && gl == 0) mybits[s0 >> 5] = bw;
+                bw = 0;
+            }
         }
     }
-    // lane sums -> chain sums (five tree levels: their rounding is bounded by 5 u sum|dS_lane|)
-    float dabs = fabsf(dS);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        dS += __shfl_xor_sync(kFull, dS, o);
-        dabs += __shfl_xor_sync(kFull, dabs, o);
-        e += __shfl_xor_sync(kFull, e, o);
-        nacc += __shfl_xor_sync(kFull, nacc, o);
-    }
-    e += 5.0f * 1.2e-7f * dabs;
+    (void)gmask;
+    // lane sums -> chain sums (log2 G tree levels: their rounding is bounded by log2(G) u sum|dS_lane|)
+    float dabs = group_sum<G>(fabsf(dS));
+    dS = group_sum<G>(dS);
+    e = group_sum<G>(e);
+    nacc = group_sum<G>(nacc);
+    e += (float)Log2<G>::v * 1.2e-7f * dabs;
 
-    // ---- candidates for the FP64 argmin
     const double Fa = Fs + (double)dS;
     const double ec = (double)es + (double)e;
-    const bool finite = isfinite(Fa);
-    if (lane == 0) block_hi[threadIdx.x >> 5] = finite ? Fa + ec : CUDART_INF;
     return ChainEnd{Fa, ec, nacc};
 }
 
-// After every warp of the block has finished its chain: one atomicMin per
-// block on the device-wide threshold, then each warp's candidate test.
-template <int COST>
-__device__ void warp_chain_finish(const SweepArgs& A, const ProbDev& P, int64_t c, int level, const float* xw,
-                                  double Fa, double ec, double M, unsigned nacc, unsigned* block_acc) {
-    const int lane = threadIdx.x & 31;
-    const int n = P.n;
-    const int64_t gc = P.chain_base + c;
-    const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
-    const bool finite = isfinite(Fa);
-    if (finite && (tracing || level == A.full_level || A.crossover || Fa - ec <= M)) {
-        double p1 = 0.0;
-        for (int k = lane; k < n; k += 32) partial64<COST>(xw, n, k, p1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p1 += __shfl_xor_sync(kFull, p1, o);
-        if (lane == 0) {
-            A.F[gc] = COST == kSchwefel ? -(p1 / (double)n) : (COST == kRastrigin ? 10.0 * (double)n + p1 : p1);
-        }
-        float* dst = A.X32 + P.x_base + c;
-        for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xw[k];
-    } else {
-        if (lane == 0) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
-        if (keep_states(A)) {  // every chain keeps its state for the next level
-            float* dst = A.X32 + P.x_base + c;
-            for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xw[k];
-        }
+template <int COST, int G, bool CACHE>
+__device__ __forceinline__ ChainEnd dispatch_chain(const SweepArgs& A, const ProbDev& P, int64_t c, bool mine, int level,
+                                                   float* xw, float* hw, const float* slo, const float* shi,
+                                                   const float* ssig, bool ub, bool up) {
+    if (up) {
+        return ub ? group_chain<COST, true, true, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig)
+                  : group_chain<COST, false, true, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig);
     }
-    if (lane == 0) atomicAdd(block_acc, nacc);
+    return ub ? group_chain<COST, true, false, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig)
+              : group_chain<COST, false, false, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig);
 }
 
-__global__ void __launch_bounds__(kBlock, SA_F32W_MIN_BLOCKS) sweep_f32w_kernel(SweepArgs A) {
+template <int G, bool CACHE>
+__global__ void __launch_bounds__(kMaxBlock, SA_F32W_MIN_BLOCKS) sweep_f32g_kernel(SweepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kMaxChains = kMaxBlock / G;
     __shared__ unsigned block_acc;
-    __shared__ double block_hi[kWarps];
+    __shared__ double chain_hi[kMaxChains];
     __shared__ double block_M;
+    __shared__ int cand[kMaxChains];
+    __shared__ int ncand;
     const WorkItem it = A.items[blockIdx.x];
     const ProbDev& P = A.probs[it.problem];
     const int level = A.run->level;
     const int n = P.n;
-    const int warp = threadIdx.x >> 5;
-    float* xs = reinterpret_cast<float*>(smem_raw);       // [kWarps][n] states
-    float* hs = xs + (size_t)kWarps * (n + 1);             // [kWarps][n + 1] cached terms
-    float* slo = hs + (size_t)kWarps * (n + 1);
+    const int CB = blockDim.x / G;              // chains per block
+    const int cb = threadIdx.x / G;             // this group's chain
+    const int gl = threadIdx.x & (G - 1);
+    float* xs = reinterpret_cast<float*>(smem_raw);                    // [CB][n + 1] states
+    float* hs = xs + (size_t)CB * (n + 1);                             // [CB][n + 1] cached terms (CACHE)
+    float* slo = hs + (CACHE ? (size_t)CB * (n + 1) : 0);
     float* shi = slo + n;
     float* ssig = shi + n;
     const bool ub = P.uniform != 0;
     const bool up = A.proposal == 1;
-    if (threadIdx.x == 0) block_acc = 0u;
-    if (threadIdx.x < kWarps) block_hi[threadIdx.x] = CUDART_INF;
+    if (threadIdx.x == 0) { block_acc = 0u; ncand = 0; }
     if (!ub) {
         const float sl = (float)A.s_tab[level];
-        for (int k = threadIdx.x; k < n; k += kBlock) { slo[k] = P.lo32[k]; shi[k] = P.hi32[k]; ssig[k] = P.sig32[k] * sl; }
+        for (int k = threadIdx.x; k < n; k += blockDim.x) { slo[k] = P.lo32[k]; shi[k] = P.hi32[k]; ssig[k] = P.sig32[k] * sl; }
     }
     __syncthreads();
-    const bool mine = warp < it.count;
-    float* xw = xs + (size_t)warp * (n + 1);  // row of n coordinates plus the scratch slot n
-    float* hw = hs + (size_t)warp * (n + 1);
-    const int64_t c = it.c0 + warp;
-    ChainEnd end{0.0, 0.0, 0u};
-    if (mine) {
+    const bool mine = cb < it.count;
+    const bool warp_busy = (threadIdx.x & ~31) / G < it.count;  // the warp's first group has a chain
+    float* xw = xs + (size_t)cb * (n + 1);  // row of n coordinates plus the scratch slot n
+    float* hw = hs + (size_t)cb * (n + 1);
+    const int64_t c = it.c0 + cb;
+    ChainEnd end{CUDART_INF, 0.0, 0u};
+    if (warp_busy) {
         switch (P.cost) {
-        case kSchwefel:
-            end = up ? (ub ? warp_chain<kSchwefel, true, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                           : warp_chain<kSchwefel, false, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi))
-                     : (ub ? warp_chain<kSchwefel, true, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                           : warp_chain<kSchwefel, false, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi));
-            break;
-        case kRastrigin:
-            end = up ? (ub ? warp_chain<kRastrigin, true, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                           : warp_chain<kRastrigin, false, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi))
-                     : (ub ? warp_chain<kRastrigin, true, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                           : warp_chain<kRastrigin, false, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi));
-            break;
-        case kRosenbrock:
-            end = up ? (ub ? warp_chain<kRosenbrock, true, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                           : warp_chain<kRosenbrock, false, true>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi))
-                     : (ub ? warp_chain<kRosenbrock, true, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi)
-                           : warp_chain<kRosenbrock, false, false>(A, P, c, level, xw, hw, slo, shi, ssig, block_hi));
-            break;
+        case kSchwefel: end = dispatch_chain<kSchwefel, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig, ub, up); break;
+        case kRastrigin: end = dispatch_chain<kRastrigin, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig, ub, up); break;
+        case kRosenbrock: end = dispatch_chain<kRosenbrock, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig, ub, up); break;
         default:
             if ((threadIdx.x & 31) == 0) A.run->status = 1;
             break;
         }
     }
+    const bool finite = mine && isfinite(end.Fa);
+    if (gl == 0 && cb < kMaxChains) chain_hi[cb] = finite ? end.Fa + end.ec : CUDART_INF;
     __syncthreads();
     // one atomicMin per block on the device-wide threshold M = min(F + e)
     if (threadIdx.x == 0) {
-        double bmin = block_hi[0];
-        for (int w = 1; w < kWarps; ++w) bmin = fmin(bmin, block_hi[w]);
+        double bmin = chain_hi[0];
+        for (int j = 1; j < CB; ++j) bmin = fmin(bmin, chain_hi[j]);
         double M = bmin;
         if (bmin < CUDART_INF) {
             const unsigned long long old = atomicMin(P.level_min, dbl_key(bmin));
@@ -430,35 +440,92 @@ __global__ void __launch_bounds__(kBlock, SA_F32W_MIN_BLOCKS) sweep_f32w_kernel(
         block_M = M;
     }
     __syncthreads();
+    const bool tracing = (A.bits != nullptr) && level < A.trace_levels;
+    const int64_t gc = P.chain_base + c;
     if (mine) {
-        switch (P.cost) {
-        case kSchwefel: warp_chain_finish<kSchwefel>(A, P, c, level, xw, end.Fa, end.ec, block_M, end.nacc, &block_acc); break;
-        case kRastrigin: warp_chain_finish<kRastrigin>(A, P, c, level, xw, end.Fa, end.ec, block_M, end.nacc, &block_acc); break;
-        case kRosenbrock: warp_chain_finish<kRosenbrock>(A, P, c, level, xw, end.Fa, end.ec, block_M, end.nacc, &block_acc); break;
-        default: break;
+        if (finite && (tracing || level == A.full_level || A.crossover || end.Fa - end.ec <= block_M)) {
+            if (gl == 0) cand[atomicAdd(&ncand, 1)] = cb;
+        } else {
+            if (gl == 0) A.F[gc] = finite ? CUDART_INF : CUDART_NAN;
+            if (keep_states(A)) {  // every chain keeps its state for the next level
+                float* dst = A.X32 + P.x_base + c;
+                for (int k = gl; k < n; k += G) dst[(size_t)k * (size_t)P.chains] = xw[k];
+            }
         }
+        if (gl == 0) atomicAdd(&block_acc, end.nacc);
     }
     __syncthreads();
+    // one warp per candidate: lane-strided FP64 partial sums in index order, then the butterfly
+    const int lane = threadIdx.x & 31;
+    const int nc = ncand;
+    for (int j = threadIdx.x >> 5; j < nc; j += blockDim.x >> 5) {
+        const int tc = cand[j];
+        const float* xr = xs + (size_t)tc * (n + 1);
+        double p1 = 0.0;
+        switch (P.cost) {
+        case kSchwefel: for (int k = lane; k < n; k += 32) partial64<kSchwefel>(xr, n, k, p1); break;
+        case kRastrigin: for (int k = lane; k < n; k += 32) partial64<kRastrigin>(xr, n, k, p1); break;
+        default: for (int k = lane; k < n; k += 32) partial64<kRosenbrock>(xr, n, k, p1); break;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p1 += __shfl_xor_sync(kFull, p1, o);
+        const int64_t cc = it.c0 + tc;
+        if (lane == 0) {
+            A.F[P.chain_base + cc] = P.cost == kSchwefel ? -(p1 / (double)n)
+                                   : (P.cost == kRastrigin ? 10.0 * (double)n + p1 : p1);
+        }
+        float* dst = A.X32 + P.x_base + cc;
+        for (int k = lane; k < n; k += 32) dst[(size_t)k * (size_t)P.chains] = xr[k];
+    }
     if (threadIdx.x == 0 && block_acc) atomicAdd(P.accepts, (unsigned long long)block_acc);
 }
 
-}  // namespace
-
-int sweep_f32w_chains_per_block() { return kWarps; }
-
-size_t sweep_f32w_smem_bytes(int n) { return (2 * (size_t)kWarps * (n + 1) + 3 * (size_t)n) * sizeof(float); }
-
-cudaError_t sweep_f32w_set_smem(size_t bytes) {
-    static size_t current = 0;
+// The instantiated (G, CACHE) layouts.
+template <int G, bool CACHE>
+cudaError_t launch_g(const SweepArgs& a, int num_items, int block, size_t smem, cudaStream_t s) {
+    sweep_f32g_kernel<G, CACHE><<<num_items, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+template <int G, bool CACHE>
+cudaError_t set_smem_g(size_t bytes) {
+    static size_t current = 0;  // the limit only grows, so earlier graphs stay valid
     if (bytes <= current) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(sweep_f32w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const cudaError_t e =
+        cudaFuncSetAttribute(sweep_f32g_kernel<G, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) current = bytes;
     return e;
 }
 
-cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, size_t smem, cudaStream_t s) {
-    sweep_f32w_kernel<<<num_items, kBlock, smem, s>>>(a);
-    return cudaGetLastError();
+}  // namespace
+
+bool sweep_f32w_layout_ok(int lanes, bool cache) {
+    return (lanes == 32 && cache) || ((lanes == 2 || lanes == 4 || lanes == 8) && !cache) ||
+           ((lanes == 4 || lanes == 8) && cache);
+}
+
+int sweep_f32w_chains_per_block(int lanes, int block) { return block / lanes; }
+
+size_t sweep_f32w_smem_bytes(int n, int lanes, bool cache, int block) {
+    const size_t cb = (size_t)(block / lanes);
+    return ((cache ? 2 : 1) * cb * (size_t)(n + 1) + 3 * (size_t)n) * sizeof(float);
+}
+
+cudaError_t sweep_f32w_set_smem(int lanes, bool cache, size_t bytes) {
+    if (lanes == 32) return set_smem_g<32, true>(bytes);
+    if (lanes == 8) return cache ? set_smem_g<8, true>(bytes) : set_smem_g<8, false>(bytes);
+    if (lanes == 4) return cache ? set_smem_g<4, true>(bytes) : set_smem_g<4, false>(bytes);
+    if (lanes == 2 && !cache) return set_smem_g<2, false>(bytes);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, int lanes, bool cache, int block, size_t smem,
+                              cudaStream_t s) {
+    if (block < 32 || block > kMaxBlock || (block & 31) != 0 || !sweep_f32w_layout_ok(lanes, cache))
+        return cudaErrorInvalidValue;
+    if (lanes == 32) return launch_g<32, true>(a, num_items, block, smem, s);
+    if (lanes == 8) return cache ? launch_g<8, true>(a, num_items, block, smem, s) : launch_g<8, false>(a, num_items, block, smem, s);
+    if (lanes == 4) return cache ? launch_g<4, true>(a, num_items, block, smem, s) : launch_g<4, false>(a, num_items, block, smem, s);
+    return launch_g<2, false>(a, num_items, block, smem, s);
 }
 
 }  // namespace sa

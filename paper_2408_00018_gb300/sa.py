@@ -102,7 +102,9 @@ SIGNATURES = {
     "sa_argmin_scratch_bytes": (_SZ, [_I64]),
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
     "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
+    "sa_pipe_rate": (ctypes.c_int, [_I32, _I32, _V, _V, _V]),
     "sa_da_trace": (ctypes.c_int, [_V, _I32, _V, _V]),
+    "sa_da_network": (ctypes.c_int, [_V, _V, _V, _V, _V]),
     "sa_set_chain_offset": (ctypes.c_int, [_V, _I64]),
     "sa_restart_point": (ctypes.c_int, [_V, _I32, _V, _V]),
     "sa_set_restart": (ctypes.c_int, [_V, _I32, _V, _D, _I64]),
@@ -285,6 +287,19 @@ class Handle:
         ftp = np.zeros((self.L, self.chains), np.float32)
         _check(load().sa_da_trace(self._ptr, level, ft0.ctypes.data, ftp.ctypes.data), "sa_da_trace")
         return ft0, ftp
+
+    def da_network(self):
+        """The surrogate network of the last completed level (sa_da_network):
+        (params [sa_mlp_param_count(n)], (mu, sigma), mid [n], inv_half [n]), FP32."""
+        lib = load()
+        P = int(lib.sa_mlp_param_count(self.n))
+        p = np.zeros(P, np.float32)
+        ms = np.zeros(2, np.float32)
+        mid = np.zeros(self.n, np.float32)
+        ih = np.zeros(self.n, np.float32)
+        _check(lib.sa_da_network(self._ptr, p.ctypes.data, ms.ctypes.data, mid.ctypes.data, ih.ctypes.data),
+               "sa_da_network")
+        return p, (float(ms[0]), float(ms[1])), mid, ih
 
     def checkpoint(self) -> bytes:
         lib = load()
@@ -469,6 +484,21 @@ def argmin_f64_static(F):
     _check(load().sa_argmin_f64_static(ctypes.c_void_p(F.data_ptr()), F.numel(), ctypes.c_void_p(idx.data_ptr()),
                                        ctypes.c_void_p(val.data_ptr()), _current_stream()), "sa_argmin_f64_static")
     return idx, val
+
+
+# ---------------------------------------------------------------- pipe rates (roofline)
+PIPE_OPS = {"sin": 0, "cos": 1, "lg2": 2, "ex2": 3, "sqrt": 4, "rsqrt": 5, "imad_wide": 6, "imad_hi": 7,
+            "imad_lo": 8, "lop3": 9, "ffma": 10, "dfma": 11, "philox": 12}
+
+
+def pipe_rate(op: str, iters: int = 4096):
+    """sa_pipe_rate: measured (operations per clock per SM, operations per second)
+    of one pipe of the current GPU (Philox: whole blocks)."""
+    per_clk = ctypes.c_double()
+    per_s = ctypes.c_double()
+    _check(load().sa_pipe_rate(PIPE_OPS[op], iters, _current_stream(), ctypes.byref(per_clk), ctypes.byref(per_s)),
+           "sa_pipe_rate")
+    return per_clk.value, per_s.value
 
 
 # ---------------------------------------------------------------- surrogate network

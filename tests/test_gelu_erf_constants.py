@@ -8,7 +8,7 @@ import re
 
 import numpy as np
 
-SRC = os.path.join(os.path.dirname(__file__), "..", "paper_2408_00018_gb300", "csrc", "gemm_tc.cu")
+SRC = os.path.join(os.path.dirname(__file__), "..", "paper_2408_00018_gb300", "csrc", "gelu.cuh")
 
 
 def _kernel_constants():

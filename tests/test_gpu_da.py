@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import surrogate as S
 from paper_2408_00018_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -39,9 +40,78 @@ def _create(sa, cost, n, C, L, K, T0, rho, seed, Q, trace_levels=0, surrogate=1,
     return sa.create(cost, lo, hi, n, C, L, sch, seed=seed, Q=Q)
 
 
+def _bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _net_values(net, X, n, scale=1.0):
+    """The surrogate's values at the rows of X by the FP64 oracle network, with the
+    GPU's rounding of its operands: inputs (x - mid) / half formed in FP32 and
+    rounded to BF16, weights W1, W2 rounded to BF16.  Returns (y, f~) with
+    f~ = mu + sigma y.  scale != 1 plants a wrong input scaling (tests of this check)."""
+    p, (mu, sig), mid, ih = net
+    Xs = ((np.asarray(X, np.float32) - mid) * ih).astype(np.float32) * np.float32(scale)
+    q = np.array(p, np.float64)
+    W1, b1, W2, b2, w3, b3 = S.unpack(q, n)
+    W1[:] = _bf16(W1)
+    W2[:] = _bf16(W2)
+    y, _ = S.forward(q, _bf16(Xs), n)
+    return y, mu + sig * y
+
+
+def _surrogate_mismatch(net, X, ft_gpu, n, scale=1.0):
+    """Largest |network output of the GPU's f~ - the oracle network's output| over the
+    rows, in units of the BF16 bound of the forward test (1e-2 (max |y| + 1))."""
+    mu, sig = net[1]
+    y, _ = _net_values(net, X, n, scale)
+    y_gpu = (np.asarray(ft_gpu, np.float64) - mu) / sig
+    return float(np.abs(y_gpu - y).max() / (1e-2 * (np.abs(y).max() + 1.0)))
+
+
+def _check_da_level(p, level, bits, ft0, ftp, L, starts, chains, plant=0):
+    """Chain-by-chain replay of one traced delayed-acceptance level by the oracle,
+    from the GPU's start states and with the GPU's surrogate values.  Returns
+    (chains identical bit for bit, violations).  At the first differing step of a
+    chain: stage 1 (deterministic given the recorded f~) must have passed in the
+    oracle too, and the oracle's stage-2 margin |(dF - dFs) - tau| must lie within
+    the difference of the two proposals (FP32 against FP64 arithmetic of the
+    Gaussian step), the tolerance of the plain rotated path."""
+    T = oracle.temperature(p.T0, p.rho, level)
+    sigma = 0.1 * float(np.max(p.hi - p.lo)) * np.sqrt(T / p.T0)
+    gb = _bits_to_bool(bits, L)
+    full, bad = 0, []
+    for c in chains:
+        _, xo, ob, _, _, dF, tau = p.da_chain_level_trace(level, c, float(ft0[c]), ftp[:, c].astype(np.float64),
+                                                         starts(c), plant=plant)
+        ob = _bits_to_bool(ob, L)
+        diff = np.nonzero(ob != gb[c])[0]
+        if diff.size == 0:
+            full += 1
+            continue
+        s = int(diff[0])
+        if np.isnan(dF[s]):  # the oracle's stage 1 rejected where the GPU went on to stage 2
+            bad.append(("stage1", level, c, s))
+            continue
+        prev = np.nonzero(gb[c][:s])[0]  # accepted steps before s (identical on both sides)
+        ft_cur = float(ftp[prev[-1], c]) if prev.size else float(ft0[c])
+        dFs = float(ftp[s, c]) - ft_cur
+        G = float(np.abs(oracle.grad(p.cost, xo, p.Q)).max()) + 1.0
+        tol = 1e-4 * (abs(dF[s] - dFs) + abs(tau[s])) + 1e-4 * sigma * G
+        if abs((dF[s] - dFs) - tau[s]) > tol:
+            bad.append(("stage2", level, c, s, float(dF[s] - dFs), float(tau[s]), tol))
+    return full, bad
+
+
 @pytest.mark.parametrize("cost,n,C,box", [("rot_schwefel", 64, 256, "uniform"), ("rot_rastrigin", 40, 130, "uniform"),
                                           ("rot_schwefel", 24, 70, "per-coordinate")])
 def test_da_decisions_match_oracle_replay(sa, cost, n, C, box):
+    """Every chain of three traced levels against the oracle's replay (see
+    _check_da_level), and the surrogate values the sweep used against the FP64
+    oracle network with the level's parameters: at every start state and at the
+    proposals of the first steps.  Planted mistakes in the oracle -- a stage-2
+    sign error, an input scaled by the full instead of the half width of the box
+    -- must each be caught."""
     L, K, T0, rho, seed = 150, 3, 30.0, 0.6, 4
     Q = inputs.rotation(n, 2)
     lo, hi = inputs.box(cost, n)
@@ -52,23 +122,48 @@ def test_da_decisions_match_oracle_replay(sa, cost, n, C, box):
     p = oracle.Problem(cost, n, lo, hi, chains=C, L=L, T0=T0, rho=rho, seed=seed, Q=Q, mode=1)
     start = lambda c: p.init_point(c).astype(np.float32).astype(np.float64)
     total_full = total = 0
+    planted_caught = 0
     for level in range(K):
         h.run(1)
         X, F = h.trace_states(level)
-        bits = _bits_to_bool(h.trace(level), L)
+        bits = h.trace(level)
         ft0, ftp = h.da_trace(level)
+        full, bad = _check_da_level(p, level, bits, ft0, ftp, L, start, range(C))
+        assert not bad, bad[:5]
+        total_full += full
+        total += C
+        # a stage-2 sign error planted in the oracle is caught on some chain of the level
+        _, bad_planted = _check_da_level(p, level, bits, ft0, ftp, L, start, range(C), plant=1)
+        planted_caught += int(len(bad_planted) > 0)
         for c in range(C):
-            Fo, xo, ob, acc, ev = p.da_chain_level(level, c, float(ft0[c]), ftp[:, c].astype(np.float64), start(c))
-            ob = _bits_to_bool(ob, L)
-            total += 1
-            total_full += int(np.array_equal(ob, bits[c]))
             fx = oracle.cost(cost, X[c], Q)
             assert abs(F[c] - fx) <= 1e-9 * max(1.0, abs(fx)), (level, c)
+        # the surrogate values the sweep used: at the level's start states ...
+        net = h.da_network()
+        S0 = np.array([start(c) for c in range(C)])
+        assert _surrogate_mismatch(net, S0, ft0, n) <= 1.0
+        # ... and at every chain's proposal of steps 0 and 1 (the chain's state there is
+        # its start state, or after step 0's move when that was accepted)
+        gb = _bits_to_bool(bits, L)
+        for s in (0, 1):
+            Xp = np.empty((C, n))
+            for c in range(C):
+                x = start(c).copy()
+                if s == 1 and gb[c, 0]:
+                    d0, xp0 = p.propose_step(level, c, 0, x)
+                    x[d0] = xp0
+                d, xp = p.propose_step(level, c, s, x)
+                x[d] = xp
+                Xp[c] = x
+            assert _surrogate_mismatch(net, Xp, ftp[s], n) <= 1.0, (level, s)
+        # a planted wrong input scaling (the full width of the box instead of the half) is caught
+        assert _surrogate_mismatch(net, S0, ft0, n, scale=0.5) > 1.0
         pstar = int(h.level_log()["argmin"][level])
         assert pstar == int(np.argmin(F))
         x_restart = X[pstar].copy()
         start = lambda c, xr=x_restart: xr
     assert total_full >= 0.9 * total, (total_full, total)
+    assert planted_caught == K
     _, f, st = h.best()
     assert 0 < st["true_evals"] <= st["steps"] and st["accepts"] <= st["true_evals"]
 

@@ -67,3 +67,57 @@ def test_gemm_strided_operands_and_bad_shapes(lib):
     from paper_2408_00018_gb300 import sa
     bad = torch.zeros(100, 64, dtype=torch.bfloat16, device="cuda")
     assert _gemm(lib, bad, B, D, status) == sa.SA_EINVAL
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 128, 256)])
+def test_gemm_wait_that_runs_out_reports_timeout(lib, M, N, K, monkeypatch):
+    """The timeout path of the bounded mbarrier waits, made to run out without a
+    fault: every stage expects 64 bytes more than its two copies deliver, so
+    the copies land but no stage's barrier ever completes.  The kernel must
+    give up, write SA_ETIMEOUT to the status word and leave the context usable
+    (the next GEMM, without the knob, is exact).  K = 256 also makes the
+    producer run out on a stage that the matrix unit never freed."""
+    import torch
+    from paper_2408_00018_gb300 import sa
+    g = torch.Generator(device="cpu").manual_seed(11)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    D = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    monkeypatch.setenv("SA_GEMM_TEST_STALL", "1")
+    assert _gemm(lib, A, B, D, status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == sa.SA_ETIMEOUT
+    monkeypatch.delenv("SA_GEMM_TEST_STALL")
+    status.zero_()
+    assert _gemm(lib, A, B, D, status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = A.double().cpu() @ B.double().cpu().T
+    bound = K * 2.0 ** -24 * (A.double().abs().cpu() @ B.double().abs().cpu().T) + 1e-30
+    assert ((D.double().cpu() - ref).abs() <= bound).all()
+
+
+def test_surrogate_run_reports_gemm_timeout(lib, monkeypatch):
+    """A delayed-acceptance run whose surrogate GEMMs time out reports SA_ETIMEOUT
+    (the GEMMs write the run's own status word; sa_run only launches, and the
+    first call that synchronises, sa_best, reports the device's status)."""
+    import torch
+    from paper_2408_00018_gb300 import inputs, sa
+    n, C, L = 32, 256, 2
+    lo, hi = inputs.box("rot_schwefel", n)
+    sch = sa.Schedule(T0=10.0, rho=0.9, levels=1, sigma_frac=0.1, precision="fp32", surrogate=1)
+    monkeypatch.setenv("SA_GEMM_TEST_STALL", "1")  # before sa_create, which captures the level graphs
+    h = sa.create("rot_schwefel", lo, hi, n, C, L, sch, seed=3, Q=inputs.rotation(n, 1))
+    h.run()
+    with pytest.raises(sa.SAError) as err:
+        h.best()
+    assert err.value.status == sa.SA_ETIMEOUT
+    monkeypatch.delenv("SA_GEMM_TEST_STALL")
+    h.destroy()
+    torch.cuda.synchronize()
+    # the context is still usable: a fresh surrogate run completes
+    h2 = sa.create("rot_schwefel", lo, hi, n, C, L, sch, seed=3, Q=inputs.rotation(n, 1))
+    h2.run()
+    assert np.isfinite(h2.best()[1])
+    h2.destroy()

@@ -67,3 +67,24 @@ def test_static_scratch_rejects_too_large_and_null(lib):
     assert lib.sa_argmin_f64_static(ctypes.c_void_p(d.data_ptr()), too_many, ctypes.c_void_p(idx.data_ptr()),
                                     ctypes.c_void_p(d.data_ptr()), s) == sa.SA_EINVAL
     assert lib.sa_argmin_f64_static(None, 4, None, None, s) == sa.SA_EINVAL
+
+
+def test_static_scratch_at_its_maximum_count(lib):
+    """The largest count the fixed array serves (2^27 doubles, 65 536 partials):
+    the minimum sits in the last 2048-input span, so the last partial slot of
+    the array decides the result; two calls in a row, the second with the
+    minimum moved, check that stale partials never leak into a result."""
+    import torch
+    from paper_2408_00018_gb300 import sa
+    count = sa.ARGMIN_STATIC_MAX_COUNT
+    F = torch.ones(count, dtype=torch.float64, device="cuda")
+    for pos in (count - 1, count - 2048):
+        F.fill_(1.0)
+        F[pos] = -3.0
+        F[pos - 1] = -3.0 if pos == count - 2048 else 1.0  # a tie across the last span boundary
+        (a_i, a_v), (b_i, b_v) = _call_both(lib, F)
+        exp = pos - 1 if pos == count - 2048 else pos
+        assert (a_i, a_v) == (exp, -3.0)
+        assert (b_i, b_v) == (a_i, a_v)
+    del F
+    torch.cuda.empty_cache()
