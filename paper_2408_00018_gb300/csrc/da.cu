@@ -182,7 +182,7 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
     if (ftp <= ftc) {  // dFs <= 0 exactly
         pass1 = true;
     } else {
-        const float t1 = K.neg_T_ln2 * __log2f(u23f(wd.x));
+        const float t1 = K.neg_T_ln2 * lg2_approx(u23f(wd.x));
         const float M1 = fmaf(1.1e-6f, t1, fmaf(4.4e-7f, K.Tf, 2.4e-7f * d32));
         if (d32 < t1 - M1) {
             pass1 = true;

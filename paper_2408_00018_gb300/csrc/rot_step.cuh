@@ -46,14 +46,14 @@ __device__ __forceinline__ float sin_taylor(float x) {
 // sin(2 pi r) for |r| < 2^22: r - rint(r) is exact, the SFU sine then runs on [-pi, pi].
 __device__ __forceinline__ float sin2pi_red(float r) {
     const float f = r - rintf(r);
-    return __sinf(6.28318530717958648f * f);
+    return sin_approx(6.28318530717958648f * f);
 }
 // cos(r) for |r| < ~64, reduced like sin_reduced.
 __device__ __forceinline__ float cos_reduced(float r) {
     const float k = rintf(r * 0.15915494309189535f);
     float t = fmaf(-k, 6.28318548202514648f, r);
     t = fmaf(-k, -1.7484555314695172e-7f, t);
-    return __cosf(t);
+    return cos_approx(t);
 }
 
 // The proposal of step s (Sec. 2.1, Step 2): coordinate d, Gaussian step of the
@@ -75,15 +75,15 @@ __device__ __forceinline__ RotMove rot_propose(uint4 w, const float* x, const Pr
     float sig, lo, hi;
     if (P.uniform) { sig = P.sig_u * sl; lo = P.lo_u; hi = P.hi_u; }
     else { sig = P.sig32[m.d] * sl; lo = P.lo32[m.d]; hi = P.hi32[m.d]; }
-    m.tau = neg_T_ln2 * __log2f(u23f(w.w));
+    m.tau = neg_T_ln2 * lg2_approx(u23f(w.w));
     m.w3 = w.w;
     m.xo = x[m.d];
     float xp;
     if (uprop) {
         xp = fmaf(hi - lo, u23f(w.z), lo);
     } else {
-        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u23f(w.y)));
-        const float z = -r * __cosf(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
+        const float r = sqrt_approx(-1.3862943611198906f * lg2_approx(u23f(w.y)));
+        const float z = -r * cos_approx(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
         xp = fmaf(sig, z, m.xo);
     }
     if (boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);

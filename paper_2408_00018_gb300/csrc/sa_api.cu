@@ -287,20 +287,25 @@ bool pick_warp_mode(int cost, int n) {
         if (e[0] == '0') return false;
         if (e[0] == '1') return true;
     }
-    // Default before autotuning.  At n = 256 the two layouts are within 3%
-    // (2.05 ms vs 2.11 ms per level on the Schwefel workload); above that the
-    // thread layout's shared memory per chain leaves too few warps per SM.
-    return n > 256;
+    // Default before autotuning, from measured levels of 262144 chains on this
+    // GPU: the chain-per-thread layout up to n = 128 (Schwefel n = 128: 1.43 ms
+    // per level against 1.60 ms with 4 lanes per chain); above it its shared
+    // memory per chain leaves too few warps per SM (n = 256: 1.83 ms against
+    // 1.55 ms with 4 lanes per chain; n = 512, 131072 chains: 1.53 ms against
+    // 0.91 ms with 8).
+    return n > 128;
 }
 
 // Group layout of the FP32 sweep for a dimension bucket: lanes per chain,
-// cached terms, threads per block.  The block holds about 64 KiB of chain
-// state (three blocks per SM) and at least 8 chains.  SA_CHAIN_LANES (2, 4, 8,
-// 32), SA_TERM_CACHE (0/1) and SA_GROUP_BLOCK (threads) override it for
-// tuning runs; every choice gives the same decisions.
+// cached terms, threads per block.  The block size maximises the chains an
+// SM holds (its shared memory, 1 KiB reserved per block, 2048 threads and the
+// kernel's register budget of 80 per thread), larger blocks on ties, at least
+// 8 chains per block.  SA_CHAIN_LANES (2, 4, 8, 32), SA_TERM_CACHE (0/1) and
+// SA_GROUP_BLOCK (threads) override it for tuning runs; every choice gives the
+// same decisions.
 struct GroupLayout { int lanes; bool cache; int block; };
 GroupLayout pick_group_layout(int n) {
-    GroupLayout g{4, false, 0};
+    GroupLayout g{n > 256 ? 8 : 4, false, 0};
     if (const char* e = std::getenv("SA_CHAIN_LANES")) {
         const int v = std::atoi(e);
         if (v == 2 || v == 4 || v == 8 || v == 32) g.lanes = v;
@@ -308,12 +313,23 @@ GroupLayout pick_group_layout(int n) {
     if (const char* e = std::getenv("SA_TERM_CACHE")) g.cache = e[0] == '1';
     if (g.lanes == 32) g.cache = true;
     if (g.lanes == 2) g.cache = false;
-    const int per_chain = (g.cache ? 2 : 1) * 4 * (n + 1);
-    int b = (65536 / per_chain) * g.lanes;
-    if (const char* e = std::getenv("SA_GROUP_BLOCK")) b = std::atoi(e);
-    b = (b / 32) * 32;
-    b = std::min(256, std::max(b, std::max(32, 8 * g.lanes)));
-    g.block = b;
+    constexpr size_t kSmemPerSm = 228 * 1024, kReserved = 1024;
+    int best_b = 8 * g.lanes < 32 ? 32 : 8 * g.lanes;
+    long best_chains = -1;
+    for (int b = best_b; b <= 256; b += 32) {
+        const size_t smem = sweep_f32w_smem_bytes(n, g.lanes, g.cache, b) + 1024;  // + the kernel's static arrays
+        if (smem > 227 * 1024) break;
+        const long by_smem = (long)(kSmemPerSm / (smem + kReserved));
+        const long by_threads = 2048 / b, by_regs = 65536 / (80L * b);
+        const long blocks = std::min(by_smem, std::min(by_threads, by_regs));
+        const long chains = blocks * (b / g.lanes);
+        if (chains >= best_chains) { best_chains = chains; best_b = b; }
+    }
+    g.block = best_b;
+    if (const char* e = std::getenv("SA_GROUP_BLOCK")) {
+        const int v = (std::atoi(e) / 32) * 32;
+        if (v >= 32 && v <= 256 && v >= 8 * g.lanes) g.block = v;
+    }
     return g;
 }
 

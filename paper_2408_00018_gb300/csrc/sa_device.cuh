@@ -86,6 +86,26 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// The SFU's sine, cosine and base-2 logarithm with subnormal inputs and
+// results flushed to zero (one SFU instruction each, without the fix-ups the
+// subnormal-preserving forms add).  Every argument here is a normal number
+// or zero except by a coincidence of size below 2^-126, where flushing moves
+// the result by less than 2^-126: far inside every error bound of the sweep.
+__device__ __forceinline__ float sin_approx(float x) {
+    float r;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float r;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // sin(r) for 0 <= r <= ~64: two-constant Cody-Waite reduction by 2 pi, then the
 // SFU sine on [-pi, pi].
@@ -93,12 +113,12 @@ __device__ __forceinline__ float sin_reduced(float r) {
     const float k = rintf(r * 0.15915494309189535f);
     float t = fmaf(-k, 6.28318548202514648f, r);
     t = fmaf(-k, -1.7484555314695172e-7f, t);
-    return __sinf(t);
+    return sin_approx(t);
 }
 // cos(2 pi t) for any |t| < 2^22: t - rint(t) is exact, the SFU cosine then runs on [-pi, pi].
 __device__ __forceinline__ float cos2pi(float t) {
     const float f = t - rintf(t);
-    return __cosf(6.28318530717958648f * f);
+    return cos_approx(6.28318530717958648f * f);
 }
 
 // ---------------------------------------------------------------------------

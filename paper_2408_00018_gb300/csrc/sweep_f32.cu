@@ -172,11 +172,11 @@ __device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
         p.z = u2;  // uniform redraw: x' = lo + u2 (hi - lo)
     } else {
         // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
-        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
-        p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+        const float r = sqrt_approx(-1.3862943611198906f * lg2_approx(u1));
+        p.z = -r * cos_approx(6.28318530717958648f * (u2 - 0.5f));
     }
     // u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3   (tau > 0, so dF <= 0 is always accepted)
-    p.tau = C.neg_T_ln2 * __log2f(u3);
+    p.tau = C.neg_T_ln2 * lg2_approx(u3);
 }
 
 // Move and energy difference of a proposed step from the chain's current state.

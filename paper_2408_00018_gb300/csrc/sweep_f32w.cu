@@ -111,11 +111,11 @@ __device__ __forceinline__ void wpropose(const WCtx& C, uint32_t s, WStep& p) {
         p.z = u2;  // uniform redraw: x' = lo + u2 (hi - lo)
     } else {
         // Box-Muller, cosine branch: z = sqrt(-2 ln u1) cos(2 pi u2) = -sqrt(..) cos(2 pi (u2 - 1/2)).
-        const float r = sqrt_approx(-1.3862943611198906f * __log2f(u1));
-        p.z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+        const float r = sqrt_approx(-1.3862943611198906f * lg2_approx(u1));
+        p.z = -r * cos_approx(6.28318530717958648f * (u2 - 0.5f));
     }
     // u3 < exp(-dF/T)  <=>  dF < tau = -T ln u3
-    p.tau = C.neg_T_ln2 * __log2f(u3);
+    p.tau = C.neg_T_ln2 * lg2_approx(u3);
 }
 
 // Move and energy difference from the chain's current state.
@@ -283,7 +283,8 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
     C.rk = rk;
     const float kappa = P.kappa;
 
-    const bool tracing = mine && (A.bits != nullptr) && level < A.trace_levels;
+    const bool trace_on = (A.bits != nullptr) && level < A.trace_levels;  // warp-uniform
+    const bool tracing = mine && trace_on;
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     const unsigned lt = lanemask_lt();
     const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (gi * G);
@@ -292,59 +293,104 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
     float dS = 0.0f, e = 0.0f;
     unsigned nacc = 0, bw = 0;
     const int L = (int)opaque((uint32_t)A.L);
-    for (int s0 = 0; s0 < L; s0 += G) {
+    // one round: steps s0 .. s0 + G - 1, one per lane (live: the lane's step exists)
+    auto round = [&](int s0, bool live) {
         const int s = s0 + gl;
-        const bool live = mine && s < L;
         WStep p;
         wpropose<UP>(C, (uint32_t)s, p);
         wevaluate<COST, UB, UP, CACHE>(C, p);
-        // earlier lanes of the group whose step can change what this lane's evaluation read
-        unsigned earlier;
-        if (COST == kRosenbrock) {
-            const int key = live ? p.d : -1 - lane;
-            earlier = 0u;
+        bool acc, pend;
+        if (G < 32) {
+            // pending: an earlier lane of the group changes what this lane's evaluation
+            // read (G - 1 shuffles within the group; a warp-wide match costs far more on
+            // this GPU).  Schwefel, Rastrigin: an earlier lane with the same coordinate
+            // whose speculative evaluation accepts -- a rejected move leaves the state as
+            // it was, and if that earlier lane is itself pending, so is this one (its
+            // cause has this coordinate too).  Rosenbrock: any earlier lane on the
+            // coordinate or a neighbour (a neighbour's cause need not be one).
+            const bool acc_spec = live && (p.dF < p.tau);
+            const int key = COST == kRosenbrock ? (live ? p.d : -1 - lane) : (live ? (p.d << 1) | (acc_spec ? 1 : 0) : -1);
+            const int want = (p.d << 1) | 1;
+            bool hit = false;
 #pragma unroll
-            for (int k = 0; k < G - 1; ++k) {
-                const int dk = __shfl_sync(kFull, key, k, G);
-                earlier |= ((k < gl) && dk >= p.d - 1 && dk <= p.d + 1) ? (1u << (gi * G + k)) : 0u;
+            for (int k = 1; k < G; ++k) {
+                const int dk = __shfl_up_sync(kFull, key, k, G);
+                hit |= (gl >= k) && (COST == kRosenbrock ? (dk >= p.d - 1 && dk <= p.d + 1) : dk == want);
+            }
+            pend = live && hit;
+            acc = acc_spec && !pend;
+            // Branch-free commit, with no barrier after the speculative reads:
+            // lanes that do not accept write to the scratch slot n of their row,
+            // and an accepting lane is the first of its group to touch its
+            // coordinate, so no other lane's speculative read of this round saw
+            // it (a later lane that did is pending and reads again below).
+            const int slot = acc ? p.d : n;
+            xw[slot] = p.xp;
+            if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = p.hp;
+            // pending lanes, by position in the group: the lane at position j reads
+            // again once the lanes before it have committed
+            const unsigned pendm = __ballot_sync(kFull, pend);
+            if (pendm) {
+                constexpr unsigned kRep = G == 2 ? 0x55555555u : (G == 4 ? 0x11111111u : 0x01010101u);
+#pragma unroll 1
+                for (int pos = 1; pos < G; ++pos) {
+                    if (!(pendm & (kRep << pos))) continue;
+                    __syncwarp();
+                    WStep q = p;
+                    wevaluate<COST, UB, UP, CACHE>(C, q);
+                    const bool go = pend && gl == pos;
+                    const bool a2 = q.dF < q.tau;
+                    if (go) p = q;
+                    acc = go ? a2 : acc;
+                    __syncwarp();
+                    const int slot2 = (go && a2) ? q.d : n;
+                    xw[slot2] = q.xp;
+                    if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot2] = q.hp;
+                }
             }
         } else {
-            // the group's index in the key keeps the groups of a warp apart
-            const int key = live ? ((gi << 24) | p.d) : -1 - lane;
-            earlier = __match_any_sync(kFull, key) & lt;  // every lane takes part, live or not
+            // one chain per warp: the lanes sharing a coordinate, by a warp-wide match
+            const int key = live ? p.d : -1 - lane;
+            unsigned earlier;
+            if (COST == kRosenbrock) {
+                earlier = 0u;
+                for (int k = 0; k < 31; ++k) {
+                    const int dk = __shfl_sync(kFull, key, k);
+                    earlier |= ((k < lane) && dk >= p.d - 1 && dk <= p.d + 1) ? (1u << k) : 0u;
+                }
+            } else {
+                earlier = __match_any_sync(kFull, key) & lt;  // every lane takes part, live or not
+            }
+            pend = live && earlier != 0u;
+            acc = live && !pend && (p.dF < p.tau);
+            __syncwarp();  // every speculative read happens before any write
+            int slot = acc ? p.d : n;
+            xw[slot] = p.xp;
+            if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = p.hp;
+            // pending lanes, in rounds: a lane goes once every earlier conflicting
+            // lane is decided; the whole warp evaluates, the going lanes keep it
+            unsigned undecided = __ballot_sync(kFull, pend);
+            while (undecided) {
+                __syncwarp();
+                const bool go = ((undecided >> lane) & 1u) && (earlier & undecided) == 0u;
+                WStep q = p;
+                wevaluate<COST, UB, UP, CACHE>(C, q);
+                const bool a2 = q.dF < q.tau;
+                if (go) p = q;
+                acc = go ? a2 : acc;
+                __syncwarp();
+                slot = (go && a2) ? q.d : n;
+                xw[slot] = q.xp;
+                if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = q.hp;
+                undecided &= ~__ballot_sync(kFull, go);
+            }
         }
-        const bool pend = live && earlier != 0u;
-        bool acc = live && !pend && (p.dF < p.tau);
-        __syncwarp();  // every speculative read happens before any write
-        // Branch-free commit: lanes that do not accept write to the scratch
-        // slot n of their row.  Accepting lanes of a group write distinct
-        // coordinates (each is the first lane of its group to touch its coordinate).
-        int slot = acc ? p.d : n;
-        xw[slot] = p.xp;
-        if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = p.hp;
-        // pending lanes, in rounds: a lane goes once every earlier conflicting
-        // lane is decided; the whole warp evaluates, the going lanes keep it
-        unsigned undecided = __ballot_sync(kFull, pend);
-        while (undecided) {
-            __syncwarp();
-            const bool go = ((undecided >> lane) & 1u) && (earlier & undecided) == 0u;
-            WStep q = p;
-            wevaluate<COST, UB, UP, CACHE>(C, q);
-            const bool a2 = q.dF < q.tau;
-            if (go) p = q;
-            acc = go ? a2 : acc;
-            __syncwarp();
-            slot = (go && a2) ? q.d : n;
-            xw[slot] = q.xp;
-            if (CACHE && (COST == kSchwefel || COST == kRastrigin)) hw[slot] = q.hp;
-            undecided &= ~__ballot_sync(kFull, go);
-        }
-        __syncwarp();
+        __syncwarp();  // this round's writes before the next round's reads
         const float bnd = COST == kRosenbrock ? rosen_bound(C, p) : kappa;
         dS += acc ? p.dF : 0.0f;
         e += acc ? bnd + fabsf(dS) * 1.2e-7f : 0.0f;
         nacc += acc ? 1u : 0u;
-        if (A.bits != nullptr && level < A.trace_levels) {  // warp-uniform
+        if (trace_on) {
             const unsigned accm = __ballot_sync(kFull, acc) & gmask;
             bw |= (G == 32 ? accm : accm >> (gi * G)) << (s0 & 31);
             if (((s0 & 31) + G == 32) || s0 + G >= L) {
@@ -352,7 +398,10 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
                 bw = 0;
             }
         }
-    }
+    };
+    int s0 = 0;
+    for (; s0 + G <= L; s0 += G) round(s0, mine);  // full rounds
+    if (s0 < L) round(s0, mine && s0 + gl < L);    // the last, partial round
     (void)gmask;
     // lane sums -> chain sums (log2 G tree levels: their rounding is bounded by log2(G) u sum|dS_lane|)
     float dabs = group_sum<G>(fabsf(dS));

@@ -235,14 +235,25 @@ def test_schwefel_n256_full_size_level0_sampled(sa):
 @pytest.mark.parametrize("cost", ["schwefel", "rastrigin", "ackley", "rosenbrock"])
 @pytest.mark.parametrize("n", [3, 20, 100])
 def test_fp32_speculative_groups_are_exact(sa, cost, n, monkeypatch):
-    """Evaluating U steps of a chain together and committing them in order
-    gives exactly the one-step-at-a-time chain, for U = 1, 2, 4."""
+    """Evaluating several steps of a chain together and committing them in order
+    gives exactly the one-step-at-a-time chain: the chain-per-thread layout with
+    U = 1, 2, 4 steps per group and with the randomness of 16 steps drawn as one
+    batch, and the group layouts of 2, 4, 8 and 32 lanes per chain, with and
+    without the cached terms, all give the same accept bits, argmins and result."""
     C, L, K = 300, 97, 3   # L not a multiple of 4 or 32: partial groups at the end
     results = []
-    # (chain-per-warp layout, steps per group of the chain-per-thread layout)
-    for wm, u in (("0", "1"), ("0", "2"), ("0", "4"), ("1", "1")):
+    # (group layout, steps per group of the chain-per-thread layout, randomness batch, lanes, cached terms)
+    shapes = [("0", "1", "1", "4", "0"), ("0", "2", "1", "4", "0"), ("0", "4", "1", "4", "0"), ("0", "2", "16", "4", "0"),
+              ("0", "1", "16", "4", "0")]
+    if cost != "ackley":
+        shapes += [("1", "1", "1", ln, ch) for ln, ch in (("2", "0"), ("4", "0"), ("4", "1"), ("8", "0"), ("8", "1"),
+                                                         ("32", "1"))]
+    for wm, u, r, ln, ch in shapes:
         monkeypatch.setenv("SA_WARP_MODE", wm)
         monkeypatch.setenv("SA_UNROLL", u)
+        monkeypatch.setenv("SA_RAND_BATCH", r)
+        monkeypatch.setenv("SA_CHAIN_LANES", ln)
+        monkeypatch.setenv("SA_TERM_CACHE", ch)
         g = _run_gpu(sa, cost, n, C, L, K, 30.0, 0.8, 13, "fp32", trace_levels=K)
         results.append((g["bits"], g["log"]["argmin"], g["f"], g["x"]))
         g["h"].destroy()
