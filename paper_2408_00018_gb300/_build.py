@@ -35,6 +35,7 @@ UNITS = {
     "da.cu": [],
     "crossover.cu": ["-fmad=false"],
     "pipes.cu": [],
+    "sweep_batch.cu": [],
 }
 
 

@@ -10,50 +10,12 @@
 #include <cstdint>
 #include <math_constants.h>
 
+#include "restart.cuh"
 #include "sa_device.cuh"
 #include "sa_internal.h"
 
 namespace sa {
 namespace {
-
-struct VI {
-    double v;
-    int64_t i;
-};
-
-// (v, i) better than (w, j): smaller value, then smaller index; NaN never wins.
-__device__ __forceinline__ bool better(double v, int64_t i, double w, int64_t j) {
-    return v < w || (v == w && i < j);
-}
-
-__device__ __forceinline__ VI warp_argmin(VI a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_xor_sync(0xffffffffu, a.v, o);
-        const long long j = __shfl_xor_sync(0xffffffffu, (long long)a.i, o);
-        if (better(w, j, a.v, a.i)) { a.v = w; a.i = j; }
-    }
-    return a;
-}
-
-// Block argmin; result valid in every thread.
-__device__ VI block_argmin(VI a, VI* red) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    a = warp_argmin(a);
-    __syncthreads();
-    if (lane == 0) red[wid] = a;
-    __syncthreads();
-    VI b = red[0];
-    for (int k = 1; k < nw; ++k)
-        if (better(red[k].v, red[k].i, b.v, b.i)) b = red[k];
-    return b;
-}
-
-__device__ __forceinline__ long long globaltimer_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 __global__ void __launch_bounds__(kArgminThreads) argmin_restart_kernel(const ProbDev* __restrict__ probs, SweepArgs A,
                                                                         int precision) {
@@ -96,61 +58,7 @@ __global__ void __launch_bounds__(kArgminThreads) argmin_restart_kernel(const Pr
         if (better(v, i, b.v, b.i)) { b.v = v; b.i = i; }
     }
     b = block_argmin(b, red);
-    const int level = A.run->level;
-    if (t == 0) s_old_inc = P.scal[kFInc];
-    __syncthreads();
-    const double old_inc = s_old_inc;
-    const bool ok = (b.i != INT64_MAX) && isfinite(b.v);
-    const int n = P.n;
-    if (ok) {
-        const bool improve = b.v < old_inc;
-        double p1 = 0.0, p2 = 0.0;
-        for (int k = t; k < n; k += kArgminThreads) {
-            double xb;
-            if (precision == 0) {
-                xb = A.X64[P.x_base + (size_t)k * (size_t)C + (size_t)b.i];
-                P.x_best64[k] = xb;
-            } else {
-                const float xf = A.X32[P.x_base + (size_t)k * (size_t)C + (size_t)b.i];
-                P.x_best32[k] = xf;
-                xb = (double)xf;
-            }
-            if (improve) P.x_inc[k] = xb;
-            if (P.cost == kAckley) {
-                p1 += xb * xb;
-                p2 += cos(6.283185307179586 * xb);
-            }
-        }
-        if (P.cost == kAckley) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-                p2 += __shfl_xor_sync(0xffffffffu, p2, o);
-            }
-            if ((t & 31) == 0) { s_red2[t >> 5] = p1; s_red2[32 + (t >> 5)] = p2; }
-            __syncthreads();
-            if (t == 0) {
-                double q1 = 0.0, q2 = 0.0;
-                for (int k = 0; k < kArgminThreads / 32; ++k) { q1 += s_red2[k]; q2 += s_red2[32 + k]; }
-                P.scal[kS1] = q1;
-                P.scal[kS2] = q2;
-            }
-        }
-        if (t == 0) {
-            P.scal[kFBest] = b.v;
-            if (improve) P.scal[kFInc] = b.v;
-        }
-    } else if (t == 0) {
-        atomicCAS(&A.run->status, 0, 5);  // SA_ENUMERIC (the first error raised in a run is kept)
-    }
-    if (t == 0) {
-        P.log_argmin[level] = ok ? b.i : -1;
-        P.log_f[level] = ok ? b.v : CUDART_NAN;
-        P.log_finc[level] = (ok && b.v < old_inc) ? b.v : old_inc;
-        P.log_t[level] = globaltimer_ns();
-        *P.level_min = 0xFFF0000000000000ull;  // ordered key of +inf
-        *P.done = 0u;
-    }
+    finish_problem_level(P, A, precision, b, s_red2, &s_old_inc);
 }
 
 __global__ void level_end_kernel(RunDev* run) {
@@ -173,6 +81,7 @@ __global__ void reset_kernel(ProbDev* probs, int num_probs, RunDev* run) {
     if (p == 0) {
         run->level = 0;
         run->status = 0;
+        run->probs_done = 0;
     }
 }
 

@@ -45,7 +45,7 @@ struct HostProb {
 // Problems whose sweep runs as one kernel launch with one block shape.  A
 // batch of problems of uneven dimension is split by n into groups; within a
 // level the groups' sweeps run concurrently on forked streams.
-enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2, kSweepRot = 3, kSweepDA = 4 };
+enum GroupKind { kSweepF64 = 0, kSweepF32 = 1, kSweepF32Warp = 2, kSweepRot = 3, kSweepDA = 4, kSweepBatch = 5 };
 
 // Delayed acceptance: training per level and buffer sizes.
 constexpr int kDaTrainSteps = 128;
@@ -171,6 +171,18 @@ sa_status h2d(sa_handle* h, T* dst, const T* src, size_t count) {
     if (count == 0) return SA_OK;
     h->h2d_bytes += (int64_t)(count * sizeof(T));
     return cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream) == cudaSuccess ? SA_OK : SA_ECUDA;
+}
+
+bool batch_level_ok(const sa_handle* h) {
+    if (const char* e = std::getenv("SA_BATCH_LEVEL"))
+        if (e[0] == '0') return false;
+    if (h->precision == SA_FP64 || h->sch.surrogate || h->probs.size() < 2) return false;
+    for (const HostProb& p : h->probs) {
+        if (!(p.cost == SA_SCHWEFEL || p.cost == SA_RASTRIGIN || p.cost == SA_ACKLEY || p.cost == SA_ROSENBROCK))
+            return false;
+        if (batch_smem_bytes(p.cost, p.n) > 200 * 1024) return false;
+    }
+    return true;
 }
 
 uint64_t fnv(uint64_t h, const void* p, size_t len) {
@@ -333,6 +345,12 @@ GroupLayout pick_group_layout(int n) {
     return g;
 }
 
+// Does a handle run its FP32 levels as one launch each (the batched level
+// kernel)?  Batches of more than one problem of the separable costs, whose
+// largest tile fits a block.  SA_BATCH_LEVEL=0 keeps the launch per dimension
+// group instead (tuning runs and the tests that compare the two).
+bool batch_level_ok(const sa_handle* h);
+
 // Bound on the FP32 error of one accepted step's dF over the whole box (the
 // per-step bounds of sa_device.cuh at their largest), used by the warp layout.
 float step_kappa(int cost, int n, const std::vector<float>& lo32, const std::vector<float>& hi32) {
@@ -352,6 +370,7 @@ cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
     if (g.kind == kSweepF64) return launch_sweep_f64(a, num, g.block, g.smem, s);
     if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.lanes, g.cache, g.block, g.smem, s);
     if (g.kind == kSweepRot) return launch_sweep_rot(a, num, g.smem, s);
+    if (g.kind == kSweepBatch) return launch_batch_level(a, num, (int)h->probs.size(), g.smem, s);
     if (g.kind == kSweepDA)
         // the GEMMs report a timeout in the run's own status word, which every sa_run reads
         return launch_da_level(a, h->dd, h->probs[h->dd.problem].chains, h->L, kDaTrainSteps, kDaLr,
@@ -386,6 +405,27 @@ cudaError_t launch_sweep(sa_handle* h, cudaStream_t s) {
 // Work items of a group for its current block shape (tiles of one problem's
 // chains), largest problems first; uploaded on the handle's stream.
 sa_status set_group_items(sa_handle* h, Group& g) {
+    if (g.kind == kSweepBatch) {
+        // every tile of every problem in one launch, largest problems first; each
+        // problem's tiles take its own layout and capacity (batch_tile_capacity)
+        std::vector<int> order = g.probs;
+        std::sort(order.begin(), order.end(), [h](int a, int b) { return h->probs[a].chains > h->probs[b].chains; });
+        g.items.clear();
+        for (int p : order) {
+            int lanes = 0;
+            const int cap = batch_tile_capacity(h->probs[p].cost, h->probs[p].n, &lanes);
+            int32_t slot = 0;
+            for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += cap, ++slot) {
+                const int64_t cnt = h->probs[p].chains - c0 < cap ? h->probs[p].chains - c0 : cap;
+                g.items.push_back(WorkItem{p, (int32_t)cnt, c0, lanes, slot});
+            }
+            h->pd[p].items = slot;
+        }
+        if (g.items.size() > g.items_cap) return SA_EINVAL;
+        h->h2d_bytes += (int64_t)(g.items.size() * sizeof(WorkItem));
+        return cudaMemcpyAsync(g.d_items, g.items.data(), g.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                               h->stream) == cudaSuccess ? SA_OK : SA_ECUDA;
+    }
     const int per_item = g.kind == kSweepF32Warp ? sweep_f32w_chains_per_block(g.lanes, g.block)
                          : (g.kind == kSweepRot || g.kind == kSweepDA) ? sweep_rot_chains_per_block()
                                                                        : g.block;
@@ -395,7 +435,7 @@ sa_status set_group_items(sa_handle* h, Group& g) {
     for (int p : order)
         for (int64_t c0 = 0; c0 < h->probs[p].chains; c0 += per_item) {
             const int64_t cnt = h->probs[p].chains - c0 < per_item ? h->probs[p].chains - c0 : per_item;
-            g.items.push_back(WorkItem{p, (int32_t)cnt, c0});
+            g.items.push_back(WorkItem{p, (int32_t)cnt, c0, 0, 0});
         }
     if (g.items.size() > g.items_cap) return SA_EINVAL;
     if (g.items.empty()) return SA_OK;
@@ -405,6 +445,7 @@ sa_status set_group_items(sa_handle* h, Group& g) {
 }
 
 size_t group_smem(const Group& g) {
+    if (g.kind == kSweepBatch) return g.smem;  // the largest tile of the batch (set at creation)
     if (g.kind == kSweepF32Warp) return sweep_f32w_smem_bytes(g.n_max, g.lanes, g.cache, g.block);
     if (g.kind == kSweepRot) return sweep_rot_smem_bytes(g.n_max);
     if (g.kind == kSweepF64) return sweep_f64_smem_bytes(g.n_max, g.block, g.f64_terms);
@@ -412,6 +453,7 @@ size_t group_smem(const Group& g) {
 }
 
 cudaError_t group_set_smem(const Group& g) {
+    if (g.kind == kSweepBatch) return batch_set_smem(g.smem);
     if (g.kind == kSweepF32Warp) return sweep_f32w_set_smem(g.lanes, g.cache, g.smem);
     if (g.kind == kSweepRot) return sweep_rot_set_smem(g.smem);
     if (g.kind == kSweepF64) return sweep_f64_set_smem(g.smem);
@@ -422,6 +464,8 @@ cudaError_t group_set_smem(const Group& g) {
 constexpr int kBucketBounds[] = {16, 32, 64, 128, 256, 512, 1 << 30};
 
 cudaError_t launch_level_tail(sa_handle* h, cudaStream_t s) {
+    // the batched level kernel ends every problem's level and cools by itself
+    if (h->groups.size() == 1 && h->groups[0].kind == kSweepBatch) return cudaSuccess;
     cudaError_t e = launch_argmin_restart(h->args, h->d_probs, (int)h->probs.size(), h->max_argmin_blocks,
                                           h->precision == SA_FP64 ? 0 : 1, s);
     // rotated costs: y_best = Q x_best and F(y_best) for the next level
@@ -644,6 +688,14 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
             h->groups[0].probs.push_back(p);
             if (sweep_f64_keeps_terms(h->probs[p].cost)) h->groups[0].f64_terms = true;
         }
+    } else if (batch_level_ok(h)) {
+        h->groups.resize(1);
+        Group& g = h->groups[0];
+        g.kind = kSweepBatch;
+        for (int p = 0; p < P; ++p) {
+            g.probs.push_back(p);
+            g.smem = std::max(g.smem, batch_smem_bytes(h->probs[p].cost, h->probs[p].n));
+        }
     } else {
         // one group per (dimension bucket, class) pair: class 0 = thread
         // layout only, 1 = costs the chain-per-warp layout serves (no global
@@ -680,6 +732,7 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         }
         g.block = g.kind == kSweepF32Warp ? pick_group_layout(g.n_max).block
                   : g.kind == kSweepRot   ? 32 * sweep_rot_chains_per_block()
+                  : g.kind == kSweepBatch ? kBatchThreads
                                           : pick_block(h->precision, g.n_max);
         g.smem = g.kind == kSweepDA ? 0 : group_smem(g);
         if ((int)g.smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
@@ -750,7 +803,8 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
             (st = dalloc(h, &dlo32, n)) || (st = dalloc(h, &dhi32, n)) || (st = dalloc(h, &dsig32, n)) ||
             (st = dalloc(h, &xb64, n)) || (st = dalloc(h, &xb32, n)) || (st = dalloc(h, &xinc, n)) ||
             (st = dalloc(h, &scal, kNumScalars)) || (st = dalloc(h, &lmin, 1)) || (st = dalloc(h, &done, 1)) ||
-            (st = dalloc(h, &pval, d.nblk_argmin)) || (st = dalloc(h, &pidx, d.nblk_argmin)) ||
+            (st = dalloc(h, &pval, std::max<int64_t>(d.nblk_argmin, (hp.chains + 31) / 32))) ||
+            (st = dalloc(h, &pidx, std::max<int64_t>(d.nblk_argmin, (hp.chains + 31) / 32))) ||
             (st = dalloc(h, &la, h->levels_total)) || (st = dalloc(h, &lf, h->levels_total)) ||
             (st = dalloc(h, &lfi, h->levels_total)) || (st = dalloc(h, &lt, h->levels_total)) ||
             (st = dalloc(h, &acc, 1)))
@@ -1508,6 +1562,18 @@ sa_status sa_autotune(sa_handle* h, double* ms_out) {
     };
     for (Group& g : h->groups) {
         if (g.kind == kSweepF64 || g.kind == kSweepRot) continue;  // one shape only
+        if (g.kind == kSweepBatch) {  // one shape (each problem's layout is fixed): time one level
+            float ms = 0.f;
+            if (launch_reset(h->d_probs, (int)h->probs.size(), h->d_run, h->stream) != cudaSuccess ||
+                cudaEventRecord(e0, h->stream) != cudaSuccess || launch_group(h, g, h->stream) != cudaSuccess ||
+                cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = SA_ECUDA;
+                break;
+            }
+            total += ms;
+            continue;
+        }
         std::vector<Shape> cands;
         int last_block = -1;
         for (int budget : kBudgets) {
@@ -1574,7 +1640,7 @@ int32_t sa_describe(const sa_handle* h, char* buf, size_t len) {
         int u = g.probs.empty() ? 1 : h->pd[g.probs[0]].unroll;
         char tmp[256];
         std::snprintf(tmp, sizeof(tmp), "%s{\"kind\":\"%s\",\"problems\":%zu,\"n_max\":%d,\"block\":%d,\"smem\":%zu,\"unroll\":%d,\"items\":%zu,\"lanes\":%d,\"cache\":%d}",
-                      i ? "," : "", g.kind == kSweepF64 ? "fp64" : g.kind == kSweepF32Warp ? "fp32_warp" : g.kind == kSweepRot ? "rot_warp" : "fp32_thread",
+                      i ? "," : "", g.kind == kSweepF64 ? "fp64" : g.kind == kSweepF32Warp ? "fp32_warp" : g.kind == kSweepRot ? "rot_warp" : g.kind == kSweepBatch ? "fp32_batch_level" : "fp32_thread",
                       g.probs.size(), g.n_max, g.block, g.smem, u, g.items.size(),
                       g.kind == kSweepF32Warp ? g.lanes : (g.kind == kSweepF32 ? 1 : 32), g.cache ? 1 : 0);
         s += tmp;

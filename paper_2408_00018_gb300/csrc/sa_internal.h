@@ -48,8 +48,9 @@ struct ProbDev {
     double* scal;         // [kNumScalars]
     unsigned long long* level_min;  // candidate threshold of the current level (ordered key)
     unsigned int* done;   // last-block-done counter of the argmin
-    double* part_val;     // [nblk_argmin] partial minima
-    int64_t* part_idx;    // [nblk_argmin]
+    double* part_val;     // [max(nblk_argmin, items)] partial minima
+    int64_t* part_idx;    // [max(nblk_argmin, items)]
+    int32_t items;        // batched level kernel: the problem's tiles in the launch
     int64_t* log_argmin;  // [levels]
     double* log_f;        // [levels]
     double* log_finc;     // [levels]
@@ -79,12 +80,16 @@ struct RunDev {
     int32_t level;   // level index the next sweep runs
     int32_t status;  // sa_status raised on the device (0 = ok)
     long long t_start;  // device clock (ns) when the current run's level 0 started
+    int32_t probs_done;  // batched level kernel: problems whose level has ended in the current launch
+    int32_t pad;
 };
 
 struct WorkItem {
     int32_t problem;
     int32_t count;   // chains in this tile
     int64_t c0;      // first chain (problem-local index)
+    int32_t lanes;   // batched level kernel: lanes per chain (2, 4, 8), or 0 for one chain per thread
+    int32_t slot;    // batched level kernel: the tile's index among its problem's tiles
 };
 
 struct SweepArgs {
@@ -164,6 +169,16 @@ cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, int lanes, bool
 size_t sweep_f32w_smem_bytes(int n, int lanes, bool cache, int block);
 cudaError_t sweep_f32w_set_smem(int lanes, bool cache, size_t bytes);
 int sweep_f32w_chains_per_block(int lanes, int block);
+// One launch per level for a batch of FP32 problems: every tile of every problem
+// (item.lanes: 2, 4 or 8 lanes per chain, or 0 for one chain per thread with
+// item.count <= the tile's capacity), then each problem's last tile to finish
+// ends the problem's level (argmin, restart point, incumbent) and the last
+// problem advances the level.  256 threads per block.
+constexpr int kBatchThreads = 256;
+int batch_tile_capacity(int cost, int n, int* lanes);
+size_t batch_smem_bytes(int cost, int n);
+cudaError_t batch_set_smem(size_t bytes);
+cudaError_t launch_batch_level(const SweepArgs& a, int num_items, int num_probs, size_t smem, cudaStream_t s);
 cudaError_t sweep_f64_set_smem(size_t bytes);
 cudaError_t launch_pgd(int cost, int n, const double* lo, const double* hi, const double* Q, int k, const double* x0,
                        double* x_out, double* f_out, int* it_out, int max_iter, double tol, cudaStream_t s);

@@ -57,15 +57,20 @@ def test_fp64_batch_bit_parity_per_problem(sa):
             assert st["steps"] == pr["chains"] * L * K
 
 
-def test_fp32_batch_per_problem_against_oracle(sa):
+@pytest.mark.parametrize("one_launch", [True, False])
+def test_fp32_batch_per_problem_against_oracle(sa, one_launch, monkeypatch):
     spec = [("schwefel", 3, 96), ("rastrigin", 20, 130), ("ackley", 40, 64), ("rosenbrock", 100, 70),
             ("schwefel", 200, 64), ("rastrigin", 300, 40), ("schwefel", 600, 33)]
     probs = _problems(spec)
     L, T0, seed = 120, 20.0, 23
     sch = sa.Schedule(T0=T0, rho=0.9, levels=1, precision="fp32", trace_levels=1)
+    monkeypatch.setenv("SA_BATCH_LEVEL", "1" if one_launch else "0")
     with sa.create_batch(probs, L, sch, seed=seed) as h:
         groups = h.describe()
-        assert len(groups) >= 5  # problems are split by dimension
+        if one_launch:  # one launch per level for the whole batch
+            assert len(groups) == 1 and groups[0]["kind"] == "fp32_batch_level"
+        else:
+            assert len(groups) >= 5  # problems are split by dimension
         h.run()
         bits = h.trace(0)
         states = h.trace_states(0)
@@ -122,3 +127,72 @@ def test_batch_of_the_generated_workload_runs(sa):
             x, f, st = h.best(p)
             assert np.isfinite(f) and (x >= pr["lo"]).all() and (x <= pr["hi"]).all()
             assert abs(oracle.cost(pr["cost"], x) - f) <= 1e-9 * max(1.0, abs(f))
+
+
+def test_one_launch_level_equals_dimension_groups(sa, monkeypatch):
+    """The batched level kernel (one launch per level: every tile of every
+    problem, each problem's level ended by its last tile) gives the same accept
+    bits, argmins, results and visited states as one launch per dimension group
+    with the separate argmin: partial tiles, every cost, every tile layout."""
+    spec = [("schwefel", 3, 300), ("rastrigin", 20, 257), ("ackley", 40, 100), ("ackley", 300, 70),
+            ("rosenbrock", 100, 129), ("schwefel", 200, 65), ("rastrigin", 300, 40), ("schwefel", 520, 33),
+            ("rosenbrock", 400, 31)]
+    probs = _problems(spec)
+    L, K = 97, 4
+    sch = sa.Schedule(T0=25.0, rho=0.8, levels=K, precision="fp32", trace_levels=K)
+    res = []
+    for one in ("1", "0"):
+        monkeypatch.setenv("SA_BATCH_LEVEL", one)
+        with sa.create_batch(probs, L, sch, seed=7) as h:
+            h.run()
+            res.append(([h.trace(l) for l in range(K)], [h.best(p)[:2] for p in range(len(probs))],
+                        [h.level_log(p) for p in range(len(probs))], h.describe()))
+    (b1, best1, log1, d1), (b0, best0, log0, d0) = res
+    assert len(d1) == 1 and len(d0) > 1
+    for l in range(K):
+        for p in range(len(probs)):
+            assert np.array_equal(b1[l][p], b0[l][p]), (l, p)
+    for p in range(len(probs)):
+        assert best1[p][1] == best0[p][1] and np.array_equal(best1[p][0], best0[p][0]), p
+        assert np.array_equal(log1[p]["argmin"], log0[p]["argmin"])
+        assert np.array_equal(log1[p]["f_inc"], log0[p]["f_inc"])
+
+
+def test_generated_draw_at_its_chain_counts_against_oracle(sa):
+    """64 problems of the batched workload's generator at their own chain counts
+    (256 .. 16384), one launch per level: per problem, sampled chains of a traced
+    level against the FP64 oracle (identical decisions except where the oracle's
+    own margin is within the FP32 error), and the FP64 batch of the same draw
+    decision for decision."""
+    probs = inputs.batch_problems(count=64, seed=0)
+    L, T0, seed = 200, 20.0, 0
+    sch = sa.Schedule(T0=T0, rho=0.9, levels=1, precision="fp32", trace_levels=1)
+    with sa.create_batch(probs, L, sch, seed=seed) as h:
+        assert h.describe()[0]["kind"] == "fp32_batch_level"
+        h.run()
+        bits = h.trace(0)
+        for p, pr in enumerate(probs):
+            gb = _bits_to_bool(bits[p], L)
+            op = oracle.Problem(pr["cost"], pr["n"], pr["lo"], pr["hi"], chains=pr["chains"], L=L, T0=T0, rho=0.9,
+                                seed=seed, problem=p, mode=1)
+            for c in (0, pr["chains"] // 2, pr["chains"] - 1):
+                _, _, ob, dF, tau = op.chain_steps(0, c)
+                diff = np.nonzero(_bits_to_bool(ob, L) != gb[c])[0]
+                if diff.size:
+                    s = diff[0]
+                    assert abs(dF[s] - tau[s]) <= 1e-3 * (abs(dF[s]) + abs(tau[s])) + 0.05, (p, c, s)
+            x, f, _ = h.best(p)
+            assert abs(oracle.cost(pr["cost"], x) - f) <= 1e-9 * max(1.0, abs(f))
+    # FP64: every accept bit of the sampled chains equals the oracle's (full evaluation, same order)
+    L64 = 40
+    sch64 = sa.Schedule(T0=T0, rho=0.9, levels=1, precision="fp64", trace_levels=1)
+    with sa.create_batch(probs, L64, sch64, seed=seed) as h:
+        h.run()
+        bits = h.trace(0)
+        for p, pr in enumerate(probs):
+            gb = _bits_to_bool(bits[p], L64)
+            op = oracle.Problem(pr["cost"], pr["n"], pr["lo"], pr["hi"], chains=pr["chains"], L=L64, T0=T0,
+                                rho=0.9, seed=seed, problem=p, mode=0)
+            for c in (0, pr["chains"] - 1):
+                _, _, _, ob = op.chain_level(0, c, trace=True)
+                assert np.array_equal(_bits_to_bool(ob, L64), gb[c]), (p, c)
