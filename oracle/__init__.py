@@ -95,6 +95,7 @@ def lib():
             L.sao_da_chain_level.restype = f64
             L.sao_da_chain_level_steps.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp, vp]
             L.sao_da_chain_level_steps.restype = f64
+            L.sao_rotate.argtypes = [i32, vp, vp, vp]
             L.sao_proposal.argtypes = [ctypes.POINTER(Cfg), i32, i64, i32, vp, vp, vp]
             L.sao_da_chain_level_trace.argtypes = [ctypes.POINTER(Cfg), i32, i64, vp, f64, vp, vp, vp, vp, vp, vp, i32]
             L.sao_da_chain_level_trace.restype = f64
@@ -153,6 +154,15 @@ def cost(name_or_id, x, Q=None, table=None) -> float:
     Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
     t, rows = _table(table)
     return lib().sao_cost(cid, x.size, _p(x), _p(Qa), _p(t), rows)
+
+
+def rotate(Q, x) -> np.ndarray:
+    """y = Q x in FP64, each y_i summed over j in index order (the rotated costs' transform)."""
+    Qa = np.ascontiguousarray(Q, dtype=np.float64)
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(xa.size)
+    lib().sao_rotate(xa.size, _p(Qa), _p(xa), _p(y))
+    return y
 
 
 def grad(name_or_id, x, Q=None) -> np.ndarray:

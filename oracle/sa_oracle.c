@@ -151,6 +151,9 @@ static void rotate(int n, const double* Q, const double* x, double* y) {
     }
 }
 
+/* y = Q x (the rotated costs' transform), exposed for the tests of the GPU's batched transform. */
+void sao_rotate(int32_t n, const double* Q, const double* x, double* y) { rotate(n, Q, x, y); }
+
 /* ---- the rest of the Appendix (Tests 2-12 and 15-19), x[0] is the paper's x_1 ---- */
 
 /* Test 2, Branin: (x2 - 5.1 x1^2 / (4 pi^2) + 5 x1 / pi - 6)^2 + 10 (1 - 1/(8 pi)) cos x1 + 10. */

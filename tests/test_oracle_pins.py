@@ -369,3 +369,20 @@ def test_periodic_exchange_between_the_two_extremes():
     # level 2 restarts every chain from level 1's best: a synchronous level from that state
     r = mk().run(1, level0=2, x_best=mk(exchange_every=2).run(2)["x_best"])
     assert r["f_level"][0] == per["f_level"][2]
+
+
+def test_rotate_identity_permutation_and_linearity():
+    """The oracle's y = Q x: the identity and a permutation give x and the permuted x
+    exactly; a scaled sum of two vectors gives the same sum of their images."""
+    rng = np.random.default_rng(3)
+    n = 9
+    x = rng.standard_normal(n)
+    assert np.array_equal(oracle.rotate(np.eye(n), x), x)
+    perm = rng.permutation(n)
+    P = np.eye(n)[perm]
+    assert np.array_equal(oracle.rotate(P, x), x[perm])
+    Q = rng.standard_normal((n, n))
+    u, v = rng.standard_normal(n), rng.standard_normal(n)
+    lhs = oracle.rotate(Q, 2.0 * u + v)
+    rhs = 2.0 * oracle.rotate(Q, u) + oracle.rotate(Q, v)
+    assert np.abs(lhs - rhs).max() <= 1e-12 * (np.abs(Q) @ (2 * np.abs(u) + np.abs(v))).max()
