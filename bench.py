@@ -153,6 +153,9 @@ def parse():
                     help="the learned-surrogate workload (rotated Schwefel n = 128, 131072 chains, L = 2000, 150 "
                          "levels) in full, plain Metropolis and delayed acceptance, each with the hybrid's projected "
                          "gradients from the 64 best final states: time-to-target against the best FP64 value found")
+    ap.add_argument("--surrogate-forward", action="store_true",
+                    help="time the surrogate's forward pass at the delayed-acceptance step's shape (131072 rows of "
+                         "n = 128): the one-kernel tensor-core pass against the two GEMMs with fused epilogues")
     ap.add_argument("--hybrid", action="store_true",
                     help="the hybrid SA of Table 10 instead: annealing stopped early, then Nelder-Mead or projected "
                          "gradients from its best final states (one JSON line per function)")
@@ -783,16 +786,94 @@ def run_gemm_route(args):
     with sa.create(cfg["cost"], lo, hi, n, C, L, sch, seed=cfg["seed"], Q=inputs.rotation(n, cfg["q_seed"])) as h:
         h.run()
         h.reset()
-        sweep_ms, _ = h.profile()
+        sweep_ms, level_ms = h.profile()
     rank1 = float(np.mean(sweep_ms[1:]))  # levels >= 1 (level 0 also reads X0, Y0)
+    # level 0 with the run's start-up work (initial states, costs, the transform Y0 = X0 Q^T)
+    level0 = {"level_ms_other_levels": float(np.mean(level_ms[1:])), "tensor_split": float(level_ms[0])}
+    # the level-0 transform Y0 = X0 Q^T alone (exact BF16 slices, 21 tcgen05 products into
+    # double-float pairs), and level 0 of a run whose transform is the FP64 product instead
+    X32 = (torch.rand(C, n, generator=g) * 10.24 - 5.12).cuda()
+    Q64 = torch.as_tensor(inputs.rotation(n, cfg["q_seed"]), dtype=torch.float64).cuda()
+    for _ in range(3):
+        Y, st = sa.rotate_rows(X32, Q64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        Y, st = sa.rotate_rows(X32, Q64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rot_ms = e0.elapsed_time(e1) / 5
+    del Y, X32
+    prev = os.environ.get("SA_ROT_TC")
+    os.environ["SA_ROT_TC"] = "0"
+    try:
+        with sa.create(cfg["cost"], lo, hi, n, C, L, sch, seed=cfg["seed"], Q=inputs.rotation(n, cfg["q_seed"])) as h:
+            h.run()
+            h.reset()
+            _, ms64 = h.profile()
+        level0["fp64"] = float(ms64[0])
+    finally:
+        if prev is None:
+            del os.environ["SA_ROT_TC"]
+        else:
+            os.environ["SA_ROT_TC"] = prev
     peak = 1736.1
     print(json.dumps({"metric": "rotated costs: GEMM route vs rank-1 route (rotated Rastrigin n = 1024)",
                       "shape": {"C": C, "n": n, "L": L}, "flops_per_step": flops, "gemm": res,
                       "bf16_peak_tflops_sustained": peak,
                       "rank1_sweep_ms_per_level": rank1,
+                      "level0_transform": {"ms": rot_ms, "slice_products": 21,
+                                           "tflops_bf16": 21 * flops / (rot_ms * 1e-3) / 1e12},
+                      "level0_ms": level0,
                       "note": "the GEMM route's time is the BF16 product alone: BF16 inputs carry 8 "
                               "significant bits, so nearly every decision would go to the FP64 re-check; an "
                               "error-free split needs at least 3 products"}), flush=True)
+
+
+def run_surrogate_forward(args):
+    """The surrogate's forward pass f~(X) for the 131072 candidate rows (n = 128) that every
+    delayed-acceptance step evaluates: sa_mlp_forward (BF16 cast of the weights, packing of X,
+    the forward pass, the head's final sum) with the fused one-kernel pass and with the two
+    GEMMs, CUDA events after warm-up.  The forward pass alone is 8.6e10 flops."""
+    import numpy as np
+    import torch
+    from paper_2408_00018_gb300 import _build, sa
+
+    _build.build()
+    n, B = 128, 131072
+    p = torch.empty(sa.mlp_param_count(n), dtype=torch.float32, device="cuda")
+    sa.mlp_init(p, n, seed=1)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = (torch.rand(B, n, generator=g) * 2 - 1).cuda()
+    stream = torch.cuda.current_stream()
+    res = {}
+    prev = os.environ.get("SA_MLP_FUSED")
+    try:
+        for name, flag in (("fused", "1"), ("two_gemms", "0")):
+            os.environ["SA_MLP_FUSED"] = flag
+            for _ in range(5):
+                y = sa.mlp_forward(p, n, X)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 50
+            e0.record(stream)
+            for _ in range(reps):
+                y = sa.mlp_forward(p, n, X)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = {"us_per_call": e0.elapsed_time(e1) / reps * 1e3, "y_checksum": float(y.double().sum())}
+    finally:
+        if prev is None:
+            os.environ.pop("SA_MLP_FUSED", None)
+        else:
+            os.environ["SA_MLP_FUSED"] = prev
+    flops = 2.0 * B * 512 * (n + 512)
+    print(json.dumps({"metric": "surrogate forward pass (131072 x 128 -> 512 -> 512 -> 1)", "rows": B, "n": n,
+                      "flops": flops, "calls": res,
+                      "note": "per sa_mlp_forward call: weight cast, input packing, forward pass, head sum; the "
+                              "forward kernels alone are in the ncu launch list"}), flush=True)
 
 
 def run_paper_schwefel(args):
@@ -954,6 +1035,9 @@ def main():
         return
     if args.paper_schwefel:
         run_paper_schwefel(args)
+        return
+    if args.surrogate_forward:
+        run_surrogate_forward(args)
         return
     if args.suite:
         run_suite(args)

@@ -243,8 +243,10 @@ sa_status sa_reset(sa_handle* h);
  * Run up to `levels` further levels like sa_run, but launch the kernels one
  * by one (no graph) with CUDA events around them on the handle's stream, and
  * return per level the sweep kernel's time (sweep_ms[l]) and the whole level's
- * time (level_ms[l]) in milliseconds; arrays host [levels], may be NULL.
- * Synchronises.  Errors as sa_run.
+ * time (level_ms[l]) in milliseconds; arrays host [levels], may be NULL.  When
+ * the call starts at level 0, level_ms[0] also holds the run's start-up work
+ * (the initial states, their costs and, for rotated costs, the transform
+ * Y0 = X0 Q^T).  Synchronises.  Errors as sa_run.
  */
 sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* level_ms);
 
@@ -452,6 +454,30 @@ sa_status sa_mlp_loss_grad(const float* d_params, int32_t n, const float* d_X, c
                            float* d_grad, float* d_loss, void* stream);
 sa_status sa_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t count, int32_t step,
                       float lr, float beta1, float beta2, float eps, void* stream);
+
+/*
+ * Kernel-level entry point: the rotated costs' level-0 transform (the candidate
+ * transform y = Q x of the mixed-precision path, for rotated costs f(x) = F(Q x))
+ * on the tensor cores, for a batch of states at once: Y = X Q^T, each element
+ * as a double-float pair.  Every row of X and of Q is split into six slices of
+ * integers of magnitude <= 128 on a common power-of-two scale per row, held
+ * exactly in BF16; each product of two slices accumulates exactly in FP32 (its
+ * partial sums are integers below 2^24), and the 21 slice pairs of order <= 7
+ * are summed into the pairs.  Against the exact product each element errs by at
+ * most 7.1 n 2^(E + F - 48) (the dropped slice pairs and the slices'
+ * remainders), 2^E > max |x| of its row and 2^F > max |q| of its coordinate,
+ * plus the pairs' rounding, 2^-42 sum_j |x_j q_j|, while 2^(E + F) >= 2^-72:
+ * smaller scales fall below the FP32 range of the pairs and are flushed.
+ *   d_X   device, FP32 [rows x n], row-major (the states)
+ *   d_Q   device, FP64 [n x n], row-major
+ *   d_Y   device, FP32 [rows x n x 2]: element (r, i) as (hi, lo), hi + lo ~ (X Q^T)[r][i]
+ *   d_status  device int (may be NULL): SA_ETIMEOUT if a bounded wait of the GEMMs ran out
+ * Shapes: n a multiple of 64, n <= 1024, rows a multiple of 128.  Allocates its
+ * workspace stream-ordered.  Errors: SA_EINVAL (NULL pointer, other shapes),
+ * SA_ENOMEM, SA_ECUDA.
+ */
+sa_status sa_rotate_rows(const float* d_X, int64_t rows, int32_t n, const double* d_Q, float* d_Y,
+                         int32_t* d_status, void* stream);
 
 /*
  * Kernel-level entry point: Philox4x32-10 (Salmon et al., SC'11) blocks for

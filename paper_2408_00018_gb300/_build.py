@@ -36,6 +36,8 @@ UNITS = {
     "crossover.cu": ["-fmad=false"],
     "pipes.cu": [],
     "sweep_batch.cu": [],
+    "rot_tc.cu": [],
+    "mlp_fused.cu": [],
 }
 
 

@@ -539,22 +539,12 @@ cudaError_t launch_da_level(const SweepArgs& A, const DaDev& Dc, int64_t chains,
     const int cblocks = (int)((chains + kWarpsDA - 1) / kWarpsDA);
     da_clear_bits_kernel<<<grid_for(chains * A.words, 256), 256, 0, s>>>(A, D);
     da_start_kernel<<<cblocks, 32 * kWarpsDA, 0, s>>>(A, D);
-    MlpWork w{};
-    w.A1 = D.A1;  // the inference activations: Cp rows (the training workspace holds only a batch)
-    e = launch_gemm_bias_gelu(D.xs, D.np, D.mlp.W1b, D.np, D.Cp, kMlpHidden, D.np, D.mlp.p + o.b1, w.A1, kMlpHidden,
-                              nullptr, 0, status, s);
-    if (e == cudaSuccess)
-        e = launch_gemm_bias_gelu_dot(w.A1, kMlpHidden, D.mlp.W2b, kMlpHidden, D.Cp, kMlpHidden, kMlpHidden,
-                                      D.mlp.p + o.b2, D.mlp.p + o.w3, D.part, nullptr, 0, status, s);
+    e = mlp_infer(D.mlp, D.xs, D.Cp, D.A1, D.part, status, s);
     if (e != cudaSuccess) return e;
     da_ft_kernel<<<(int)((chains + 255) / 256), 256, 0, s>>>(A, D, D.mlp.p + o.b3);
     for (int st = 0; st < L && e == cudaSuccess; ++st) {
         da_patch_kernel<<<(int)((chains + 255) / 256), 256, 0, s>>>(A, D, st);
-        e = launch_gemm_bias_gelu(D.xs, D.np, D.mlp.W1b, D.np, D.Cp, kMlpHidden, D.np, D.mlp.p + o.b1, w.A1, kMlpHidden,
-                                  nullptr, 0, status, s);
-        if (e == cudaSuccess)
-            e = launch_gemm_bias_gelu_dot(w.A1, kMlpHidden, D.mlp.W2b, kMlpHidden, D.Cp, kMlpHidden, kMlpHidden,
-                                          D.mlp.p + o.b2, D.mlp.p + o.w3, D.part, nullptr, 0, status, s);
+        e = mlp_infer(D.mlp, D.xs, D.Cp, D.A1, D.part, status, s);
         if (e == cudaSuccess) {
             da_step_kernel<<<D.step_blocks, 32 * kWarpsDA, da_step_smem(D.mlp.n), s>>>(A, D, st);
             // states along the level (and at its end) feed the training buffer

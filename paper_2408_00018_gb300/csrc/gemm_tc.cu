@@ -27,6 +27,7 @@
 
 #include "gelu.cuh"
 #include "sa_internal.h"
+#include "tc_sm103.cuh"
 
 namespace sa {
 namespace {
@@ -38,94 +39,6 @@ constexpr int kBK = 64;
 template <int BN>
 __host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : 3; }
 constexpr int kThreads = 256;  // 8 warps: all of them run the epilogue, two per TMEM lane quadrant
-constexpr uint32_t kSpin = 1u << 20;  // bounded waits (each try_wait itself blocks for a while)
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait; with an abort flag it also gives up once another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort_flag = nullptr) {
-    for (uint32_t i = 0; i < kSpin; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (abort_flag && *(const volatile int*)abort_flag) return false;
-    }
-    return false;
-}
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row atoms of 1024 bytes (stride-dimension byte offset).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
-    d |= (uint64_t)1 << 16;                     // leading-dimension byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride-dimension byte offset
-    d |= (uint64_t)1 << 46;                     // descriptor version
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 32 lanes x 16 columns of 32-bit accumulator -> 16 registers per thread (its row).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-        "[%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
 // test_stall: 0, except in the test of the timeout path: then the matrix-unit
 // thread first waits on a barrier that nothing ever arrives on (polled without
 // blocking, a bounded number of times), so that wait runs out while every
@@ -138,6 +51,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int kBTile = BN * kBK * 2;
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns (power of two >= 32)
     constexpr int kStages = stages_for<BN>();
+    static_assert(!Epi::kStaged || kThreads * 17 * 4 <= kStages * kATile, "staging area beyond the A stages");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
@@ -186,7 +100,17 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (*(volatile int*)abort_flag) break;
             mbar_expect_tx(&full[s], kATile + kBTile);
             tma_load_2d(sA + s * kATile, &tmA, &full[s], kt * kBK, m0);
-            tma_load_2d(sB + s * kBTile, &tmB, &full[s], kt * kBK, n0);
+            if constexpr (Epi::kStaged) {
+                if (epi.dual) {  // two products: B's rows b_row1 + .. and b_row2 + .. of one output column tile
+                    const int nc = blockIdx.x * (BN / 2);
+                    tma_load_2d(sB + s * kBTile, &tmB, &full[s], kt * kBK, epi.b_row1 + nc);
+                    tma_load_2d(sB + s * kBTile + kBTile / 2, &tmB, &full[s], kt * kBK, epi.b_row2 + nc);
+                } else {
+                    tma_load_2d(sB + s * kBTile, &tmB, &full[s], kt * kBK, n0);
+                }
+            } else {
+                tma_load_2d(sB + s * kBTile, &tmB, &full[s], kt * kBK, n0);
+            }
             issued = kt + 1;
         }
         // on abort: wait (bounded) for every copy issued, so none lands after the CTA exits
@@ -222,6 +146,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         umma_commit(done);  // arrives once every MMA issued above has completed
     }
+    if constexpr (Epi::kStaged)
+        if (warp >= 2) {
+            if (epi.dual) epi.prefetch(m0, blockIdx.x * (BN / 2), BN / 2, threadIdx.x - 64, kThreads - 64);
+            else epi.prefetch(m0, n0, BN, threadIdx.x - 64, kThreads - 64);
+        }
     __syncwarp();
 
     // ---- epilogue: warp w reads accumulator lanes 32 q .. 32 q + 31 (tile rows), q = w mod 4,
@@ -234,11 +163,36 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (!have) atomicExch(abort_flag, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (have && !*(volatile int*)abort_flag) {
+        // a staging epilogue gets 32 x 17 floats per warp of the pipeline's shared
+        // memory, idle once every matrix operation has completed
+        float* scratch = reinterpret_cast<float*>(base) + warp * (32 * 17);
+        const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+        bool dual = false;
+        if constexpr (Epi::kStaged) dual = epi.dual;
+        if (dual) {
+            // columns [0, BN/2) and [BN/2, BN) hold two products of the same output
+            // columns: the second (the smaller) is added first
+            if constexpr (Epi::kStaged) {
+                const int nc = blockIdx.x * (BN / 2);
 #pragma unroll 1
-        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
-            epi(row, n0 + c, v, acc);
+                for (int c = half * (BN / 4); c < (half + 1) * (BN / 4); c += 16) {
+                    float v[16];
+                    tmem_ld16(tl + (uint32_t)(c + BN / 2), v);
+                    epi.staged(m0 + quad * 32, nc + c, v, scratch, lane, epi.shift2);
+                    tmem_ld16(tl + (uint32_t)c, v);
+                    epi.staged(m0 + quad * 32, nc + c, v, scratch, lane, epi.shift);
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+                float v[16];
+                tmem_ld16(tl + (uint32_t)c, v);
+                if constexpr (Epi::kStaged)
+                    epi.staged(m0 + quad * 32, n0 + c, v, scratch, lane, epi.shift);
+                else
+                    epi(row, n0 + c, v, acc);
+            }
         }
         if (Epi::kReduces && half == 1) red[quad * 32 + lane] = acc;
     }
@@ -257,6 +211,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // adds into acc, and finish() stores the row's sum over the tile.
 struct EpiStoreF32 {
     static constexpr bool kReduces = false;
+    static constexpr bool kStaged = false;
     float* D;
     int ldd;
     __device__ __forceinline__ void finish(int, int, float) const {}
@@ -270,6 +225,7 @@ struct EpiStoreF32 {
 // Surrogate layer: z = acc + bias; stores gelu(z) as BF16 (and z as FP32 when Z != nullptr).
 struct EpiBiasGelu {
     static constexpr bool kReduces = false;
+    static constexpr bool kStaged = false;
     const float* bias;
     __nv_bfloat16* A;
     int lda;
@@ -277,25 +233,33 @@ struct EpiBiasGelu {
     int ldz;
     __device__ __forceinline__ void finish(int, int, float) const {}
     __device__ __forceinline__ void operator()(int row, int col, const float* v, float&) const {
-        __align__(16) __nv_bfloat16 a[16];
+        uint32_t a[8];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float z = v[j] + bias[col + j];
-            if (Z) Z[(size_t)row * ldz + col + j] = z;
-            a[j] = __float2bfloat16_rn(gelu_f(z));
+        for (int j = 0; j < 16; j += 2) {
+            const f32x2_t z = f2_add(f2_pack(v[j], v[j + 1]), f2_pack(bias[col + j], bias[col + j + 1]));
+            const float2 g = f2_unpack(gelu2(z));
+            if (Z) {
+                const float2 zz = f2_unpack(z);
+                Z[(size_t)row * ldz + col + j] = zz.x;
+                Z[(size_t)row * ldz + col + j + 1] = zz.y;
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(g.x, g.y);
+            a[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
         }
         uint4* dst = reinterpret_cast<uint4*>(A + (size_t)row * lda + col);
-        dst[0] = reinterpret_cast<const uint4*>(a)[0];
-        dst[1] = reinterpret_cast<const uint4*>(a)[1];
+        dst[0] = make_uint4(a[0], a[1], a[2], a[3]);
+        dst[1] = make_uint4(a[4], a[5], a[6], a[7]);
     }
 };
 
 // Surrogate output head: part[row][n0 / BN] = sum over the tile's columns of
-// gelu(acc + b) w, in a fixed order (per 16 columns sequentially, the chunks of
-// each column half in turn, then first half + second half), so it is
-// deterministic; stores z as FP32 when Z != nullptr.
+// gelu(acc + b) w, in a fixed order (per 16 columns: the even and the odd columns
+// each in order, then even + odd; the 16-column groups of each column half in
+// turn; then first half + second half), so it is deterministic; stores z as FP32
+// when Z != nullptr.
 struct EpiBiasGeluDot {
     static constexpr bool kReduces = true;
+    static constexpr bool kStaged = false;
     const float* bias;
     const float* w;
     float* part;
@@ -307,49 +271,84 @@ struct EpiBiasGeluDot {
         part[(size_t)row * nparts + n0 / tile] = total;
     }
     __device__ __forceinline__ void operator()(int row, int col, const float* v, float& acc) const {
-        float s = 0.0f;
+        f32x2_t s = f2_splat(0.0f);  // even and odd columns, each summed in order
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float z = v[j] + bias[col + j];
-            if (Z) Z[(size_t)row * ldz + col + j] = z;
-            s = fmaf(gelu_f(z), w[col + j], s);
+        for (int j = 0; j < 16; j += 2) {
+            const f32x2_t z = f2_add(f2_pack(v[j], v[j + 1]), f2_pack(bias[col + j], bias[col + j + 1]));
+            if (Z) {
+                const float2 zz = f2_unpack(z);
+                Z[(size_t)row * ldz + col + j] = zz.x;
+                Z[(size_t)row * ldz + col + j + 1] = zz.y;
+            }
+            s = f2_fma(gelu2(z), f2_pack(w[col + j], w[col + j + 1]), s);
         }
-        acc += s;
+        const float2 se = f2_unpack(s);
+        acc += se.x + se.y;
+    }
+};
+
+// Exact split product (the rotated costs' level-0 transform): Y (double-float
+// pairs (hi, lo), [M x N], leading dimension ldy) += (A . B^T) 2^(er[row] +
+// fq[col] - shift).  A and B hold BF16 integer slices of magnitude <= 128, so
+// every product is an integer of magnitude <= 2^14 and, for K <= 1024, every
+// partial sum of the FP32 accumulator is an integer of magnitude <= 2^24: the
+// accumulator is exact, and so is its scaling by a power of two.  The pair
+// takes it by TwoSum and Fast2Sum (explicitly rounded, never contracted).
+__device__ __forceinline__ float2 dd_add(float2 a, float b) {
+    const float s = __fadd_rn(a.x, b);
+    const float bb = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const float t = __fadd_rn(a.y, e);
+    const float hi = __fadd_rn(s, t);
+    return make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
+}
+struct EpiAccumPair {
+    static constexpr bool kReduces = false;
+    static constexpr bool kStaged = true;
+    float2* Y;
+    int ldy;
+    const int* er;
+    const int* fq;
+    int shift;
+    // two products per tile (B's rows b_row1 + c and b_row2 + c for output column c,
+    // scaled by shift and shift2), or one (B's rows = the output columns)
+    bool dual;
+    int b_row1, b_row2, shift2, b_rows;  // b_rows: rows of B (its tensor map)
+    __device__ __forceinline__ void finish(int, int, float) const {}
+    // 2^e as an FP32 number, for e >= -126 (smaller scales flush to zero: below the pairs' range)
+    __device__ __forceinline__ static float pow2(int e) { return e < -126 ? 0.0f : __int_as_float((e + 127) << 23); }
+    // The warp's 32 rows row0 .. row0 + 31 (lane i holds row row0 + i) and the 16
+    // columns col .. col + 15 go through shared memory (rows 17 floats apart: no
+    // bank conflicts either way), so that each half-warp reads and writes one
+    // row's 16 pairs, 128 contiguous bytes, instead of 32 rows 8 KB apart.
+    __device__ __forceinline__ void staged(int row0, int col, const float* v, float* s, int lane, int sh) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) s[lane * 17 + j] = v[j];
+        __syncwarp();
+        const int j = lane & 15, h = lane >> 4;
+        const int f = fq[col + j] - sh;
+        float2* y = Y + (size_t)(row0 + 16 * h) * ldy + col + j;  // rows i and i + 16: banks 17 i + j, 17 i + 16 + j
+        float2 cur[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) cur[i] = y[(size_t)i * ldy];  // all loads in flight before the first store
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int r = i + 16 * h;
+            y[(size_t)i * ldy] = dd_add(cur[i], __fmul_rn(s[r * 17 + j], pow2(er[row0 + r] + f)));
+        }
+        __syncwarp();
+    }
+    // Issued by the warps idle during the main loop: the tile's rows of Y into L2,
+    // so the epilogue's reads find them there.
+    __device__ __forceinline__ void prefetch(int m0, int n0, int bn, int t, int nt) const {
+        for (int r = t; r < 128; r += nt)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Y + (size_t)(m0 + r) * ldy + n0),
+                         "r"((unsigned)(bn * sizeof(float2)))
+                         : "memory");
     }
 };
 
 // ---- host side ------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-// Tensor map of a row-major [rows x K] BF16 matrix with leading dimension ld
-// (elements), boxes of box_rows x 64 elements, 128-byte swizzle.
-bool make_tmap(CUtensorMap* m, const void* ptr, int rows, int K, int ld, int box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int BN>
 size_t gemm_smem() {
     constexpr int kStages = stages_for<BN>();
@@ -359,14 +358,22 @@ size_t gemm_smem() {
 template <int BN, class Epi>
 cudaError_t launch_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const Epi& epi, int* status,
                         cudaStream_t s) {
-    if (M % kBM || N % BN || K % kBK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    bool dual = false;
+    int b_rows = N;
+    if constexpr (Epi::kStaged) {
+        dual = epi.dual;
+        if (dual) b_rows = epi.b_rows;
+    }
+    const int bn = dual ? BN / 2 : BN;  // output columns per tile
+    if (M % kBM || N % bn || K % kBK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
     if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || (lda * 2) % 16 || (ldb * 2) % 16) return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
-    if (!make_tmap(&ta, A, M, K, lda, kBM) || !make_tmap(&tb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
+    if (!make_tmap(&ta, A, M, K, lda, kBM) || !make_tmap(&tb, B, b_rows, K, ldb, dual ? BN / 2 : BN))
+        return cudaErrorInvalidValue;
     const size_t smem = gemm_smem<BN>();
     cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(N / BN, M / kBM);
+    dim3 grid(N / bn, M / kBM);
     // Test of the timeout path only: SA_GEMM_TEST_STALL=1 makes one wait of the
     // matrix-unit thread run out (see test_stall), so the kernel must report SA_ETIMEOUT.
     const char* t = std::getenv("SA_GEMM_TEST_STALL");
@@ -401,6 +408,27 @@ cudaError_t launch_gemm_bias_gelu_dot(const void* A, int lda, const void* B, int
     if (N % 128) return cudaErrorInvalidValue;
     EpiBiasGeluDot epi{bias, w, part, N / 128, 128, Z, ldz};
     return launch_gemm<128>(A, lda, B, ldb, M, N, K, epi, status, s);
+}
+
+cudaError_t launch_gemm_accum_pair(const void* A, int lda, const void* B, int ldb, float2* Y, int ldy, int M, int N,
+                                   int K, const int* er, const int* fq, int shift, int* status, cudaStream_t s) {
+    if (K > 1024) return cudaErrorInvalidValue;  // beyond it the accumulator is no longer exact
+    EpiAccumPair epi{Y, ldy, er, fq, shift, false, 0, 0, 0, N};
+    if (N % 128 == 0) return launch_gemm<128>(A, lda, B, ldb, M, N, K, epi, status, s);
+    return launch_gemm<64>(A, lda, B, ldb, M, N, K, epi, status, s);
+}
+
+// Two products of one launch: Y += (A . B1^T) 2^(er + fq - shift2), then
+// Y += (A . B2^T) 2^(er + fq - shift1), B1 = B's rows b_row2 .. b_row2 + N - 1 and
+// B2 = its rows b_row1 .. (B has b_rows rows); one pass over Y in HBM (the
+// second addition finds the rows in L2).  N multiple of 128.
+cudaError_t launch_gemm_accum_pair2(const void* A, int lda, const void* B, int ldb, int b_rows, int b_row1, int b_row2,
+                                    float2* Y, int ldy, int M, int N, int K, const int* er, const int* fq, int shift1,
+                                    int shift2, int* status, cudaStream_t s) {
+    if (K > 1024 || N % 128) return cudaErrorInvalidValue;
+    if (b_row1 < 0 || b_row2 < 0 || b_row1 + N > b_rows || b_row2 + N > b_rows) return cudaErrorInvalidValue;
+    EpiAccumPair epi{Y, ldy, er, fq, shift1, true, b_row1, b_row2, shift2, b_rows};
+    return launch_gemm<256>(A, lda, B, ldb, M, N, K, epi, status, s);
 }
 
 int* gemm_status_ptr() {

@@ -13,6 +13,7 @@
 //             dZ1 = dA1 o g'(Z1);     dW1 = dZ1^T X
 // Column sums (bias gradients, dw3) and the loss are reduced in fixed order.
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -236,6 +237,23 @@ cudaError_t mlp_forward(const MlpDev& m, const void* Xb, int Bp, MlpWork& w, flo
     return launch_gemm_bias_gelu_dot(w.A1, kH, m.W2b, kH, Bp, kH, kH, m.p + o.b2, m.p + o.w3, part, w.Z2, kH, status, s);
 }
 
+// The fused forward pass where it applies, unless SA_MLP_FUSED=0 selects the two GEMMs.
+bool mlp_use_fused(int np, int Bp) {
+    const char* env = std::getenv("SA_MLP_FUSED");
+    return !(env && env[0] == '0') && mlp_fused_ok(np, Bp);
+}
+
+cudaError_t mlp_infer(const MlpDev& m, const void* Xb, int Bp, __nv_bfloat16* A1, float* part, int* status,
+                      cudaStream_t s) {
+    const MlpOffsets o = mlp_offsets(m.n);
+    if (mlp_use_fused(m.np, Bp))
+        return launch_mlp_fused(Xb, m.np, Bp, m.W1b, m.W2b, m.p + o.b1, m.p + o.b2, m.p + o.w3, part, status, s);
+    if (!A1) return cudaErrorInvalidValue;  // no workspace for the hidden activations
+    cudaError_t e = launch_gemm_bias_gelu(Xb, m.np, m.W1b, m.np, Bp, kH, m.np, m.p + o.b1, A1, kH, nullptr, 0, status, s);
+    if (e != cudaSuccess) return e;
+    return launch_gemm_bias_gelu_dot(A1, kH, m.W2b, kH, Bp, kH, kH, m.p + o.b2, m.p + o.w3, part, nullptr, 0, status, s);
+}
+
 cudaError_t mlp_finish_y(const MlpDev& m, const float* part, int B, float* y, cudaStream_t s) {
     const MlpOffsets o = mlp_offsets(m.n);
     finish_y_kernel<<<(B + 255) / 256, 256, 0, s>>>(part, m.p + o.b3, B, y);
@@ -346,6 +364,29 @@ cudaError_t scratch_alloc(Scratch& sc, MlpDev& m, int Bp, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// The same for inference only: BF16 weights, the packed inputs, the head's partial
+// sums and, where the two-GEMM forward pass runs, its hidden activations.
+cudaError_t infer_alloc(Scratch& sc, MlpDev& m, int Bp, cudaStream_t s) {
+    const size_t wbytes = ((size_t)kH * m.np + 2 * (size_t)kH * kH) * 2;
+    const size_t xbytes = (size_t)Bp * m.np * 2, pbytes = (size_t)Bp * 4 * sizeof(float);
+    const bool fused = mlp_use_fused(m.np, Bp);
+    const size_t abytes = fused ? 0 : (size_t)Bp * kH * 2;
+    auto up = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
+    cudaError_t e = cudaMallocAsync(&sc.base, up(wbytes) + up(xbytes) + up(pbytes) + abytes, s);
+    if (e != cudaSuccess) return e;
+    char* p = static_cast<char*>(sc.base);
+    m.W1b = reinterpret_cast<__nv_bfloat16*>(p);
+    m.W2b = m.W1b + (size_t)kH * m.np;
+    m.W2tb = m.W2b + (size_t)kH * kH;
+    p += up(wbytes);
+    sc.w.Xb = reinterpret_cast<__nv_bfloat16*>(p);
+    p += up(xbytes);
+    sc.w.part = reinterpret_cast<float*>(p);
+    p += up(pbytes);
+    sc.w.A1 = abytes ? reinterpret_cast<__nv_bfloat16*>(p) : nullptr;
+    return cudaSuccess;
+}
+
 sa_status to_status(cudaError_t e) {
     if (e == cudaSuccess) return SA_OK;
     if (e == cudaErrorInvalidValue) { cudaGetLastError(); return SA_EINVAL; }
@@ -373,12 +414,12 @@ sa_status sa_mlp_forward(const float* d_params, int32_t n, const float* d_X, int
     m.p = const_cast<float*>(d_params);
     const int Bp = (B + 127) / 128 * 128;
     Scratch sc;
-    cudaError_t e = scratch_alloc(sc, m, Bp, s);
+    cudaError_t e = infer_alloc(sc, m, Bp, s);
     if (e != cudaSuccess) return to_status(e);
     int* st = gemm_status_ptr();
     e = mlp_cast(m, s);
     if (e == cudaSuccess) e = mlp_pack(d_X, B, n, Bp, m.np, sc.w.Xb, s);
-    if (e == cudaSuccess) e = mlp_forward(m, sc.w.Xb, Bp, sc.w, sc.w.part, st, s);
+    if (e == cudaSuccess) e = mlp_infer(m, sc.w.Xb, Bp, sc.w.A1, sc.w.part, st, s);
     if (e == cudaSuccess) e = mlp_finish_y(m, sc.w.part, B, d_y, s);
     cudaFreeAsync(sc.base, s);
     return to_status(e);

@@ -1,6 +1,8 @@
 // rot_prep.cu -- FP64 transforms of the rotated costs f(x) = F(Q x):
 //   * level 0: the chains' random initial points X0 (FP32, [chains][n]) and
-//     Y0 = X0 Q^T in FP64 (tiled GEMM), stored as double-float pairs;
+//     Y0 = X0 Q^T, stored as double-float pairs: on the tensor cores by the
+//     exact split product of rot_tc.cu where the shape allows, else in FP64
+//     (tiled GEMM);
 //   * every restart: y_best = Q x_best in FP64 and F(y_best) (one thread per
 //     rotated coordinate, partial sums reduced by the last block to finish).
 // Every dot product runs over j = 0..n-1 in index order.
@@ -140,12 +142,13 @@ __global__ void __launch_bounds__(kRestartThreads) rot_restart_kernel(ProbDev* p
 }  // namespace
 
 cudaError_t launch_rot_level0(const ProbDev* d_prob, const ProbDev& hp, const SweepArgs& a, float* x0, float2* y0,
-                              cudaStream_t s) {
+                              void* tc_work, int* status, cudaStream_t s) {
     const int64_t work = hp.chains * (int64_t)((hp.n + 3) / 4);
     const int64_t blocks = std::min<int64_t>((work + 255) / 256, 152 * 16);
     rot_init_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_prob, a.ikey0, a.ikey1, x0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (tc_work) return launch_rot_tc(x0, hp.chains, hp.n, hp.q64, y0, tc_work, status, s);
     const dim3 grid((unsigned)((hp.n + kBN - 1) / kBN), (unsigned)std::min<int64_t>((hp.chains + kBM - 1) / kBM, 65535));
     rot_y0_kernel<<<grid, kGemmThreads, 0, s>>>(d_prob, x0, y0);
     return cudaGetLastError();

@@ -40,6 +40,7 @@ struct HostProb {
     std::vector<double> table;  // Tests 11, 18, 19: table_rows x (n + 1)
     int32_t table_rows = 0;
     ProbDev dev;  // with device pointers
+    void* tc_work = nullptr;  // rotated costs: workspace of the tensor-core level-0 transform (or NULL)
 };
 
 // Problems whose sweep runs as one kernel launch with one block shape.  A
@@ -574,6 +575,13 @@ sa_status setup_rot(sa_handle* h, HostProb& hp, ProbDev& d) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SA_ECUDA;  // host temporaries die here
     d.q64 = q64; d.qt64 = qt64; d.qt_hi = qth; d.qt_lo = qtl; d.ybest_hi = ybh; d.ybest_lo = ybl;
     d.x0 = x0; d.y0 = y0; d.rechecks = rech; d.rot_done = rdone; d.rot_part = rpart;
+    // the level-0 transform on the tensor cores where the shape allows (SA_ROT_TC=0: the FP64 GEMM)
+    const char* tc_env = std::getenv("SA_ROT_TC");
+    if (rot_tc_shape_ok(hp.chains, n) && !(tc_env && tc_env[0] == '0')) {
+        unsigned char* w;
+        if ((st = dalloc(h, &w, rot_tc_work_bytes(hp.chains, n)))) return st;
+        hp.tc_work = w;
+    }
     float qm = (float)qmax;
     if ((double)qm < qmax) qm = std::nextafterf(qm, INFINITY);
     d.qmax = qm;
@@ -949,7 +957,7 @@ cudaError_t launch_level0_prep(sa_handle* h, cudaStream_t s) {
         const HostProb& hp = h->probs[p];
         if (is_rot(hp.cost))
             e = launch_rot_level0(h->d_probs + p, hp.dev, h->args, const_cast<float*>(hp.dev.x0),
-                                  const_cast<float2*>(hp.dev.y0), s);
+                                  const_cast<float2*>(hp.dev.y0), hp.tc_work, &h->d_run->status, s);
     }
     return e;
 }
@@ -1052,14 +1060,17 @@ sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* lev
     const int remaining = h->levels_total - h->levels_done;
     if (remaining <= 0) return SA_ESTATE;
     const int k = (levels == -1 || levels > remaining) ? remaining : levels;
-    std::vector<cudaEvent_t> ev(3 * (size_t)k, nullptr);
+    std::vector<cudaEvent_t> ev(3 * (size_t)k + 1, nullptr);  // the last one: before the start-up work
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             for (auto& f : ev) if (f) cudaEventDestroy(f);
             return fail(h, SA_ECUDA);
         }
     sa_status st = SA_OK;
-    if (h->levels_done == 0 && launch_level0_prep(h, h->stream) != cudaSuccess) st = SA_ECUDA;
+    const bool from0 = h->levels_done == 0;
+    if (cudaEventRecord(ev[3 * (size_t)k], h->stream) != cudaSuccess ||
+        (from0 && launch_level0_prep(h, h->stream) != cudaSuccess))
+        st = SA_ECUDA;
     for (int l = 0; l < k && st == SA_OK; ++l) {
         if (cudaEventRecord(ev[3 * l], h->stream) != cudaSuccess || launch_sweep(h, h->stream) != cudaSuccess ||
             cudaEventRecord(ev[3 * l + 1], h->stream) != cudaSuccess || launch_level_tail(h, h->stream) != cudaSuccess ||
@@ -1072,7 +1083,7 @@ sa_status sa_profile(sa_handle* h, int32_t levels, double* sweep_ms, double* lev
     for (int l = 0; l < k && st == SA_OK; ++l) {
         float a = 0.f, b = 0.f;
         if (cudaEventElapsedTime(&a, ev[3 * l], ev[3 * l + 1]) != cudaSuccess ||
-            cudaEventElapsedTime(&b, ev[3 * l], ev[3 * l + 2]) != cudaSuccess) {
+            cudaEventElapsedTime(&b, ev[(l == 0 && from0) ? 3 * (size_t)k : 3 * l], ev[3 * l + 2]) != cudaSuccess) {
             st = SA_ECUDA;
             break;
         }
@@ -1091,6 +1102,22 @@ sa_status sa_gemm_bf16(const void* d_A, int32_t lda, const void* d_B, int32_t ld
     int* st = d_status ? d_status : gemm_status_ptr();
     const cudaError_t e = launch_gemm_bf16_f32(d_A, lda, d_B, ldb, d_D, ldd, M, N, K, st, static_cast<cudaStream_t>(stream));
     if (e == cudaErrorInvalidValue) { cudaGetLastError(); return SA_EINVAL; }
+    return e == cudaSuccess ? SA_OK : SA_ECUDA;
+}
+
+sa_status sa_rotate_rows(const float* d_X, int64_t rows, int32_t n, const double* d_Q, float* d_Y, int32_t* d_status,
+                         void* stream) {
+    if (!d_X || !d_Q || !d_Y || rows < 1 || n < 1) return SA_EINVAL;
+    if (!rot_tc_shape_ok(rows, n)) return SA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* w = nullptr;
+    if (cudaMallocAsync(&w, rot_tc_work_bytes(rows, n), s) != cudaSuccess) {
+        cudaGetLastError();
+        return SA_ENOMEM;
+    }
+    int* st = d_status ? d_status : gemm_status_ptr();
+    const cudaError_t e = launch_rot_tc(d_X, rows, n, d_Q, reinterpret_cast<float2*>(d_Y), w, st, s);
+    cudaFreeAsync(w, s);
     return e == cudaSuccess ? SA_OK : SA_ECUDA;
 }
 

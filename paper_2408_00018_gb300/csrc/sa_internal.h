@@ -194,6 +194,20 @@ cudaError_t launch_topk(double* F, int64_t count, int k, int64_t* idx, cudaStrea
 cudaError_t launch_gemm_bf16_f32(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
                                  int* status, cudaStream_t s);
 int* gemm_status_ptr();
+// Y (double-float pairs, [M x N], leading dimension ldy) += (A . B^T) 2^(er[row] + fq[col] - shift),
+// for BF16 integer slices of magnitude <= 128 and K <= 1024 (the exact split product of rot_tc.cu).
+cudaError_t launch_gemm_accum_pair(const void* A, int lda, const void* B, int ldb, float2* Y, int ldy, int M, int N,
+                                   int K, const int* er, const int* fq, int shift, int* status, cudaStream_t s);
+cudaError_t launch_gemm_accum_pair2(const void* A, int lda, const void* B, int ldb, int b_rows, int b_row1, int b_row2,
+                                    float2* Y, int ldy, int M, int N, int K, const int* er, const int* fq, int shift1,
+                                    int shift2, int* status, cudaStream_t s);
+// The rotated costs' level-0 transform on the tensor cores (rot_tc.cu): Y [C x n] pairs =
+// X [C x n] (FP32) . Q^T (Q FP64 [n x n] row-major), exactly split; shapes with n % 64 == 0,
+// n <= 1024 and C % 128 == 0; work: rot_tc_work_bytes(C, n) bytes of device memory.
+size_t rot_tc_work_bytes(int64_t C, int n);
+bool rot_tc_shape_ok(int64_t C, int n);
+cudaError_t launch_rot_tc(const float* X, int64_t C, int n, const double* Q, float2* Y, void* work, int* status,
+                          cudaStream_t s);
 // Surrogate layers on the tensor-core GEMM: out = gelu(A B^T + bias) as BF16 (Z = the
 // pre-activation, FP32, optional); and part[row][t] = sum over the 128 columns of tile t
 // of gelu(A B^T + bias) w (N a multiple of 128).
@@ -212,8 +226,9 @@ cudaError_t sweep_rot_set_smem(size_t bytes);
 int sweep_rot_chains_per_block();
 cudaError_t launch_rot_restart(const ProbDev* d_prob, int n, cudaStream_t s);
 int rot_restart_blocks(int n);
+// tc_work: the tensor-core transform's workspace (rot_tc_work_bytes), or NULL for the FP64 GEMM.
 cudaError_t launch_rot_level0(const ProbDev* d_prob, const ProbDev& host_prob, const SweepArgs& a, float* x0, float2* y0,
-                              cudaStream_t s);
+                              void* tc_work, int* status, cudaStream_t s);
 
 // ---- the learned surrogate (mlp.cu) ----------------------------------------
 constexpr int kMlpHidden = 512;
@@ -265,6 +280,15 @@ struct MlpWork {
 cudaError_t mlp_cast(const MlpDev& m, cudaStream_t s);
 cudaError_t mlp_init(float* p, int n, uint64_t seed, cudaStream_t s);
 cudaError_t mlp_forward(const MlpDev& m, const void* Xb, int Bp, MlpWork& w, float* part, int* status, cudaStream_t s);
+// Inference: part [Bp x 4] of the head for the BF16 inputs Xb [Bp x np], by the fused
+// one-kernel forward pass (mlp_fused.cu) where it applies (np = 64 or 128; not when
+// SA_MLP_FUSED=0), else by the two GEMMs with A1 [Bp x 512] as their workspace.
+cudaError_t mlp_infer(const MlpDev& m, const void* Xb, int Bp, __nv_bfloat16* A1, float* part, int* status,
+                      cudaStream_t s);
+bool mlp_fused_ok(int np, int rows);
+bool mlp_use_fused(int np, int Bp);
+cudaError_t launch_mlp_fused(const void* X, int np, int rows, const void* W1, const void* W2, const float* b1,
+                             const float* b2, const float* w3, float* part, int* status, cudaStream_t s);
 cudaError_t mlp_finish_y(const MlpDev& m, const float* part, int B, float* y, cudaStream_t s);
 cudaError_t mlp_loss_grad(const MlpDev& m, const void* Xb, int B, int Bp, const float* t, MlpWork& w, float* grad,
                           float* loss, int* status, cudaStream_t s);

@@ -103,6 +103,7 @@ SIGNATURES = {
     "sa_argmin_f64": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V]),
     "sa_argmin_f64_static": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
     "sa_pipe_rate": (ctypes.c_int, [_I32, _I32, _V, _V, _V]),
+    "sa_rotate_rows": (ctypes.c_int, [_V, _I64, _I32, _V, _V, _V, _V]),
     "sa_da_trace": (ctypes.c_int, [_V, _I32, _V, _V]),
     "sa_da_network": (ctypes.c_int, [_V, _V, _V, _V, _V]),
     "sa_set_chain_offset": (ctypes.c_int, [_V, _I64]),
@@ -484,6 +485,18 @@ def argmin_f64_static(F):
     _check(load().sa_argmin_f64_static(ctypes.c_void_p(F.data_ptr()), F.numel(), ctypes.c_void_p(idx.data_ptr()),
                                        ctypes.c_void_p(val.data_ptr()), _current_stream()), "sa_argmin_f64_static")
     return idx, val
+
+
+def rotate_rows(X, Q):
+    """sa_rotate_rows: Y = X Q^T on the tensor cores as double-float pairs, for a float32 CUDA
+    tensor X [rows x n] and a float64 CUDA tensor Q [n x n]; returns Y [rows x n x 2] (hi, lo)
+    and the GEMMs' status word."""
+    import torch
+    Y = torch.empty((X.shape[0], X.shape[1], 2), dtype=torch.float32, device=X.device)
+    st = torch.zeros(1, dtype=torch.int32, device=X.device)
+    _check(load().sa_rotate_rows(_ptr(X), X.shape[0], X.shape[1], _ptr(Q), _ptr(Y), _ptr(st), _current_stream()),
+           "sa_rotate_rows")
+    return Y, st
 
 
 # ---------------------------------------------------------------- pipe rates (roofline)

@@ -43,3 +43,46 @@ def test_a_mistyped_constant_breaks_the_bound():
         b[i] *= 1.0 + 1e-5
         err = max(abs(_erf(float(x), p, b) - math.erf(float(x))) for x in xs)
         assert err > 1.5e-7, (i, err)
+
+
+def _forward_constants():
+    """The forward pass's GELU constants as the kernel source writes them: products of
+    Hastings' literals with a scale, parsed back (scale, literal) so each is checked."""
+    src = open(SRC).read()
+    p = re.search(r"kGeluP = (-?\d+\.\d+)f \* (-?\d+\.\d+)f;", src).groups()
+    b = dict((k, (float(s), float(v))) for k, s, v in
+             re.findall(r"(kGeluB\d) = (-?\d+\.\d+)f \* (-?\d+\.\d+)f", src))
+    c = float(re.search(r"kGeluC = (-?\d+\.\d+)f;", src).group(1))
+    return (float(p[0]), float(p[1])), b, c
+
+
+def test_forward_gelu_constants_are_hastings_scaled():
+    """z Phi(z) = max(z, 0) - |z| poly(t)/2 e^(-z^2/2), t = 1/(1 + p |z|/sqrt 2): the
+    forward constants are p/sqrt 2, -a_i/2 and -log2(e)/2 of the pinned erf constants."""
+    p, a = _kernel_constants()
+    (pp, inv_sqrt2), b, c = _forward_constants()
+    assert pp == p and abs(inv_sqrt2 - 1 / math.sqrt(2)) < 1e-15
+    for i in range(5):
+        scale, lit = b["kGeluB%d" % (i + 1)]
+        assert scale == -0.5 and lit == a[i]
+    assert abs(c + 0.5 / math.log(2)) < 1e-15
+
+
+def _gelu_forward(z, pp, b, c):
+    az = abs(z)
+    t = 1.0 / (1.0 + pp * az)
+    q = t * (b[0] + t * (b[1] + t * (b[2] + t * (b[3] + t * b[4]))))
+    return max(z, 0.0) + az * q * 2.0 ** (c * z * z)
+
+
+def test_forward_gelu_matches_exact_gelu_within_hastings_bound():
+    (pp, s), bd, c = _forward_constants()
+    b = [bd["kGeluB%d" % (i + 1)][0] * bd["kGeluB%d" % (i + 1)][1] for i in range(5)]
+    zs = np.linspace(-8.0, 8.0, 40001)
+    for z in zs:
+        exact = 0.5 * z * (1.0 + math.erf(z / math.sqrt(2.0)))
+        assert abs(_gelu_forward(float(z), pp * s, b, c) - exact) <= 0.5 * abs(z) * 1.5e-7 + 1e-15, z
+    # a flipped sign of the correction term is far outside the bound
+    z = 0.7
+    exact = 0.5 * z * (1.0 + math.erf(z / math.sqrt(2.0)))
+    assert abs(_gelu_forward(z, pp * s, [-x for x in b], c) - exact) > 0.1

@@ -129,3 +129,34 @@ def test_training_on_gpu_fits_a_known_function(env):
         sa.mlp_adam(p, g, m, v, k, lr=1e-3)
     err = float(((sa.mlp_forward(p, n, Xv) * sd + mu - tv) ** 2).mean())
     assert err < 0.02 * float(tv.var()) and err < 0.05 * err0, (err0, err, float(tv.var()))
+
+
+@pytest.mark.parametrize("n,B", [(128, 128 * 152 * 2 + 77), (64, 5000), (100, 1000), (37, 1), (200, 300)])
+def test_fused_forward_equals_two_gemm_path(env, n, B, monkeypatch):
+    """The one-kernel forward pass (inputs padded to 64 or 128 columns) against the two
+    GEMMs with fused epilogues: the same FP32 accumulators, the same BF16 rounding of
+    the hidden layer and the same order of the head's sums, so equal bit for bit; at
+    2 x 152 + 1 tiles every CTA of the persistent kernel runs more than one tile.
+    n = 200 (248 padded columns) takes the two-GEMM path either way."""
+    sa, torch = env
+    P = sa.mlp_param_count(n)
+    p = torch.empty(P, dtype=torch.float32, device="cuda")
+    sa.mlp_init(p, n, seed=11)
+    pn = p.cpu().numpy()
+    o = S.unpack(pn, n)
+    rng = np.random.default_rng(n + B)
+    o[1][:] = rng.standard_normal(512) * 0.3
+    o[3][:] = rng.standard_normal(512) * 0.3
+    o[4][:] = rng.standard_normal(512)
+    o[5][:] = -0.7
+    p.copy_(torch.tensor(pn))
+    X = torch.tensor(rng.uniform(-1, 1, (B, n)).astype(np.float32), device="cuda")
+    y_fused = sa.mlp_forward(p, n, X).cpu().numpy()
+    monkeypatch.setenv("SA_MLP_FUSED", "0")
+    y_two = sa.mlp_forward(p, n, X).cpu().numpy()
+    assert np.all(np.isfinite(y_fused))
+    assert np.array_equal(y_fused, y_two), np.abs(y_fused - y_two).max()
+    # and both against the FP64 oracle on a sample of rows
+    rows = rng.choice(B, size=min(B, 64), replace=False)
+    yr, _ = S.forward(_bf16_params(pn, n), _bf16(X.cpu().numpy()[rows]), n)
+    assert np.abs(y_fused[rows] - yr).max() <= 1e-2 * (np.abs(yr).max() + 1.0)
