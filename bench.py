@@ -156,6 +156,8 @@ def parse():
     ap.add_argument("--surrogate-forward", action="store_true",
                     help="time the surrogate's forward pass at the delayed-acceptance step's shape (131072 rows of "
                          "n = 128): the one-kernel tensor-core pass against the two GEMMs with fused epilogues")
+    ap.add_argument("--seeds", type=int, default=1,
+                    help="--surrogate-vs-plain: run the comparison for this many seeds (one JSON line each)")
     ap.add_argument("--hybrid", action="store_true",
                     help="the hybrid SA of Table 10 instead: annealing stopped early, then Nelder-Mead or projected "
                          "gradients from its best final states (one JSON line per function)")
@@ -635,9 +637,18 @@ def run_surrogate_vs_plain(args):
     sa.load()
     torch.cuda.set_device(0)
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_best_f.json")))["rot_schwefel_n128"]
+    seeds = [None] + list(range(1, args.seeds))  # None: the workload's own seed
+    for seed in seeds:
+        run_surrogate_vs_plain_seed(args, sa, torch, gold, seed)
+
+
+def run_surrogate_vs_plain_seed(args, sa, torch, gold, seed):
+    """One seed of the comparison (the chains' initial points and every draw)."""
     arms = {}
     for name, surrogate in (("plain", False), ("delayed_acceptance", True)):
         w = Workload("rot_schwefel_n128", 0, False, "gaussian", 64, surrogate)
+        if seed is not None:
+            w.seed = seed
         h = w.create(sa)
         torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
@@ -661,7 +672,7 @@ def run_surrogate_vs_plain(args):
     p, d = arms["plain"]["time_to_target"], arms["delayed_acceptance"]["time_to_target"]
     out = {"metric": "time-to-target of the learned-surrogate workload (1e-6 relative to the best value found)",
            "workload": "rot_schwefel_n128_c131072_L2000_K150_fp32_Q0 + projected gradients from the 64 best",
-           "data": "synthetic", "n_gpus": 1, "f_target": f_target,
+           "data": "synthetic", "n_gpus": 1, "seed": w.seed, "f_target": f_target,
            "f_target_sources": {"oracle_reduced_run_polished (2048 chains, 10 levels)": gold["f_polished"],
                                 "plain_polished": arms["plain"]["f_polished"],
                                 "delayed_acceptance_polished": arms["delayed_acceptance"]["f_polished"]},
