@@ -746,7 +746,14 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         if ((int)g.smem > max_optin) return SA_EINVAL;  // n too large for on-chip state
         if (g.kind != kSweepDA && group_set_smem(g) != cudaSuccess) return SA_ECUDA;
         const int64_t tile = (g.kind == kSweepRot || g.kind == kSweepDA) ? sweep_rot_chains_per_block() : 8;  // smallest tile
-        for (int p : g.probs) g.items_cap += (size_t)((h->probs[p].chains + tile - 1) / tile);
+        for (int p : g.probs) {
+            int64_t t = tile;
+            if (g.kind == kSweepBatch) {  // each problem's own tile capacity
+                int lanes = 0;
+                t = std::min<int64_t>(t, batch_tile_capacity(h->probs[p].cost, h->probs[p].n, &lanes));
+            }
+            g.items_cap += (size_t)((h->probs[p].chains + t - 1) / t);
+        }
         if ((st = dalloc(h, &g.d_items, g.items_cap))) return st;
         if (h->groups.size() > 1 &&
             (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -805,14 +812,18 @@ sa_status build(sa_handle* h, const sa_problem* problems, const sa_box* boxes, c
         float *dlo32, *dhi32, *dsig32, *xb32;
         unsigned long long *lmin, *acc;
         unsigned int* done;
+        // partial argmins: one per argmin block, per 32-chain tile, and per batch tile
+        int blanes = 0;
+        const int64_t bcap = std::max(1, batch_tile_capacity(hp.cost, hp.n, &blanes));
+        const int64_t nparts = std::max<int64_t>(std::max<int64_t>(d.nblk_argmin, (hp.chains + 31) / 32),
+                                                 (hp.chains + bcap - 1) / bcap);
         int64_t *pidx, *la;
         long long* lt;
         if ((st = dalloc(h, &dlo, n)) || (st = dalloc(h, &dhi, n)) || (st = dalloc(h, &dsig, n)) ||
             (st = dalloc(h, &dlo32, n)) || (st = dalloc(h, &dhi32, n)) || (st = dalloc(h, &dsig32, n)) ||
             (st = dalloc(h, &xb64, n)) || (st = dalloc(h, &xb32, n)) || (st = dalloc(h, &xinc, n)) ||
             (st = dalloc(h, &scal, kNumScalars)) || (st = dalloc(h, &lmin, 1)) || (st = dalloc(h, &done, 1)) ||
-            (st = dalloc(h, &pval, std::max<int64_t>(d.nblk_argmin, (hp.chains + 31) / 32))) ||
-            (st = dalloc(h, &pidx, std::max<int64_t>(d.nblk_argmin, (hp.chains + 31) / 32))) ||
+            (st = dalloc(h, &pval, nparts)) || (st = dalloc(h, &pidx, nparts)) ||
             (st = dalloc(h, &la, h->levels_total)) || (st = dalloc(h, &lf, h->levels_total)) ||
             (st = dalloc(h, &lfi, h->levels_total)) || (st = dalloc(h, &lt, h->levels_total)) ||
             (st = dalloc(h, &acc, 1)))

@@ -8,7 +8,10 @@
 // the group layout (2 lanes per chain up to n = 128, 4 up to 256, 8 above: 128,
 // 64 or 32 chains per tile, about 64 KiB of state each); Ackley, whose running
 // sums tie every step of a chain to the previous one, takes one chain per
-// thread with as many chains as 64 KiB of state hold.  So every tile holds
+// thread with as many chains as 64 KiB of state hold, and above n = 128, where
+// that leaves most warps without a chain, those warps draw the chains' Philox
+// blocks, deviates and thresholds ahead into a shared-memory ring, so that a
+// chain's thread runs only the dependent part of its steps.  So every tile holds
 // about the same shared memory, three blocks fit on an SM whatever their
 // problem, and the block scheduler balances the uneven problems over the GPU
 // in one grid.
@@ -33,7 +36,9 @@ __host__ __device__ inline size_t thread_tile_bytes(int n, int S) {
 }
 
 // One chain per thread, one step at a time (the register budget of this kernel
-// is sized for the group layout); S = the tile's capacity.
+// is sized for the group layout); S = the tile's chain count.  PD: the warps past the
+// chains draw the chains' randomness ahead (sweep_tile's producer/consumer form).
+template <bool PD>
 __device__ void thread_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int S, int level,
                             unsigned char* smem_raw) {
     const int n = P.n;
@@ -44,12 +49,13 @@ __device__ void thread_tile(const SweepArgs& A, const ProbDev& P, const WorkItem
     float* slo = xs + (size_t)n * S;
     float* shi = slo + n;
     float* ssig = shi + n;
+    float* ring = ssig + n;
     const bool ub = P.uniform != 0, up = A.proposal == 1;
-#define SA_TILE(COST)                                                                                            \
-    (ub ? (up ? sweep_tile<COST, true, 1, true, 1>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand)      \
-              : sweep_tile<COST, true, 1, false, 1>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand))    \
-        : (up ? sweep_tile<COST, false, 1, true, 1>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand)     \
-              : sweep_tile<COST, false, 1, false, 1>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand)))
+#define SA_TILE(COST)                                                                                                 \
+    (ub ? (up ? sweep_tile<COST, true, 1, true, 1, PD>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand, ring)   \
+              : sweep_tile<COST, true, 1, false, 1, PD>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand, ring)) \
+        : (up ? sweep_tile<COST, false, 1, true, 1, PD>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand, ring)  \
+              : sweep_tile<COST, false, 1, false, 1, PD>(A, P, it, S, level, xs, slo, shi, ssig, red, cand, ncand, ring)))
     switch (P.cost) {
     case kSchwefel: SA_TILE(kSchwefel); break;
     case kRastrigin: SA_TILE(kRastrigin); break;
@@ -74,7 +80,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_level_kernel(SweepArgs
     case 2: group_tile<2, false>(A, P, it, level, smem_raw, gsh); break;
     case 4: group_tile<4, false>(A, P, it, level, smem_raw, gsh); break;
     case 8: group_tile<8, false>(A, P, it, level, smem_raw, gsh); break;
-    default: thread_tile(A, P, it, it.count, level, smem_raw); break;
+    case 1: thread_tile<true>(A, P, it, it.count, level, smem_raw); break;
+    default: thread_tile<false>(A, P, it, it.count, level, smem_raw); break;
     }
     // this tile's partial argmin over the FP64 values its chains were given
     __syncthreads();
@@ -123,17 +130,25 @@ int batch_tile_capacity(int cost, int n, int* lanes) {
         *lanes = n <= 128 ? 2 : (n <= 256 ? 4 : 8);
         return kBatchThreads / *lanes;
     }
-    *lanes = 0;
-    int S = (int)(kTileStateBytes / (4 * (size_t)n));
-    S = S >= kBatchThreads ? kBatchThreads : (S / 32) * 32;
-    return S < 32 ? 32 : S;
+    // Ackley: one chain per thread; where the state leaves most warps without a
+    // chain (n > 128: 64 chains or fewer), those warps draw the chains' randomness
+    // ahead (lanes = 1).  Up to n = 128 the plain tile is faster (measured).
+    if (n <= 128) {
+        *lanes = 0;
+        int S = (int)(kTileStateBytes / (4 * (size_t)n));
+        S = S >= kBatchThreads ? kBatchThreads : (S / 32) * 32;
+        return S < 32 ? 32 : S;
+    }
+    *lanes = 1;
+    const int S = (int)(kTileStateBytes / (4 * (size_t)n + kPdRingBytes(1)));
+    return S < 1 ? 1 : S;
 }
 
 size_t batch_smem_bytes(int cost, int n) {
     int lanes = 0;
     const int cap = batch_tile_capacity(cost, n, &lanes);
-    if (lanes) return ((size_t)cap * (n + 1) + 3 * (size_t)n) * sizeof(float);
-    return thread_tile_bytes(n, cap);
+    if (lanes > 1) return ((size_t)cap * (n + 1) + 3 * (size_t)n) * sizeof(float);
+    return thread_tile_bytes(n, cap) + (lanes == 1 ? kPdRingBytes(cap) : 0);
 }
 
 cudaError_t batch_set_smem(size_t bytes) {

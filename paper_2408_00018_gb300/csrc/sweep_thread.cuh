@@ -143,12 +143,18 @@ __device__ float start_value32(const float* xs, int B, int n, int t, float inv_n
     return F;
 }
 
+// Producer/consumer form of the chain-per-thread tile (PD below): steps drawn ahead per
+// phase, and the ring's size for S chains (two phases of coordinate, deviate, threshold).
+constexpr int kPdSteps = 8;
+__host__ __device__ constexpr size_t kPdRingBytes(int S) { return (size_t)2 * kPdSteps * S * 12; }
+
 // One proposed step.  a, b: cost-specific values kept for the error bound
 // (Schwefel: sqrt|xo|, sqrt|xp|; Rastrigin: g(xo), g(xp); Rosenbrock: the
 // neighbours x_{d-1}, x_{d+1}; Ackley: the candidate sums).
 struct Step {
     int d;
     float z, tau, xo, xp, dF, a, b, ap;
+    float co, cp;  // Ackley: cos 2 pi xo, cos 2 pi xp
 };
 
 struct Ctx {
@@ -183,9 +189,9 @@ __device__ __forceinline__ void propose(const Ctx& C, uint32_t s, Step& p) {
     p.tau = C.neg_T_ln2 * lg2_approx(u3);
 }
 
-// Move and energy difference of a proposed step from the chain's current state.
-template <int COST, bool UB, bool UP>
-__device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step& p) {
+// The proposed step's move from the chain's current state: p.xo, p.xp.
+template <bool UB, bool UP>
+__device__ __forceinline__ void move_to(const Ctx& C, Step& p) {
     const int d = p.d;
     const float xo = C.xcol[d * C.B];
     float lo, hi, sg;
@@ -199,6 +205,22 @@ __device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step&
     xp = fminf(fmaxf(xp, lo), hi);
     p.xo = xo;
     p.xp = xp;
+}
+
+// Ackley: the part of a step's difference that depends on the running sums.
+__device__ __forceinline__ void ackley_dep(const Ctx& C, const SepState& st, Step& p) {
+    p.a = fmaf(p.xp - p.xo, p.xp + p.xo, st.s1);
+    p.b = st.s2 + (p.cp - p.co);
+    p.ap = ackley_value(p.a, p.b, C.inv_n);
+    p.dF = p.ap - st.a;
+}
+
+// Move and energy difference of a proposed step from the chain's current state.
+template <int COST, bool UB, bool UP>
+__device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step& p) {
+    move_to<UB, UP>(C, p);
+    const int d = p.d;
+    const float xo = p.xo, xp = p.xp;
     if (COST == kSchwefel) {
         const float ro = sqrt_approx(fabsf(xo)), rp = sqrt_approx(fabsf(xp));
         p.dF = (xo * sin_reduced(ro) - xp * sin_reduced(rp)) * C.inv_n;
@@ -210,10 +232,9 @@ __device__ __forceinline__ void evaluate(const Ctx& C, const SepState& st, Step&
         p.a = go;
         p.b = gp;
     } else if (COST == kAckley) {
-        p.a = st.s1 + (xp - xo) * (xp + xo);
-        p.b = st.s2 + (cos2pi(xp) - cos2pi(xo));
-        p.ap = ackley_value(p.a, p.b, C.inv_n);
-        p.dF = p.ap - st.a;
+        p.co = cos2pi(xo);
+        p.cp = cos2pi(xp);
+        ackley_dep(C, st, p);
     } else {
         float dummy = 0.0f, before = 0.0f, after = 0.0f;
         const float xm = d > 0 ? C.xcol[(d - 1) * C.B] : 0.0f;
@@ -258,9 +279,15 @@ __device__ __forceinline__ bool conflicts(int dk, int dj) {
 // has only the U speculative steps.  The decisions are unchanged.
 // S: the tile's chain capacity, the stride of the state columns (<= blockDim.x;
 // threads from S on hold no chain and take part in the block's reductions only).
-template <int COST, bool UB, int U, bool UP, int R>
+// PD (U = R = 1): the warps from ceil(S / 32) on hold no chain; they draw every chain's
+// randomness kPdSteps steps ahead into a double-buffered ring (`ring`, kPdRingBytes(S)),
+// and the chains' threads take it from there, so a chain's step is only its dependent
+// part (evaluation and commit).  The proposals are those propose() makes for the chain,
+// so the decisions equal the chain-per-thread ones bit for bit.
+template <int COST, bool UB, int U, bool UP, int R, bool PD = false>
 __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int S, int level,
-                           float* xs, float* slo, float* shi, float* ssig, double* red, int* cand, int* ncand) {
+                           float* xs, float* slo, float* shi, float* ssig, double* red, int* cand, int* ncand,
+                           float* ring = nullptr) {
     const int t = threadIdx.x, NT = blockDim.x, B = S, n = P.n;
     const bool active = t < it.count && t < S;
     const int64_t c = it.c0 + t;
@@ -331,7 +358,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     float dS = 0.0f, e = 0.0f;
     uint32_t nacc = 0;
-    if (active) {
+    if (active || PD) {
         uint32_t bw = 0;
         const int L = A.L;
         int s = 0;
@@ -358,7 +385,57 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             }
             return acc;
         };
-        if (R > U) {
+        if (PD) {
+            // ring: proposals [2][kPdSteps][S] as coordinates, deviates, thresholds
+            int* rd = reinterpret_cast<int*>(ring);
+            float* rz = ring + 2 * kPdSteps * S;
+            float* rt = rz + 2 * kPdSteps * S;
+            const int DW = (S + 31) >> 5;           // warps holding chains
+            const bool producer = (t >> 5) >= DW;  // warp-uniform
+            const int tp = t - 32 * DW, NP = NT - 32 * DW;
+            const int phases = (L + kPdSteps - 1) / kPdSteps;
+            auto produce = [&](int ph) {  // steps ph kPdSteps .. of every chain of the tile
+                const int buf = ph & 1, s0 = ph * kPdSteps;
+                const int cnt = min(kPdSteps, L - s0);
+                for (int q = tp; q < cnt * S; q += NP) {
+                    const int j = q / S, ch = q - j * S;
+                    if (ch >= it.count) continue;
+                    Ctx Cq = C;
+                    Cq.pf = philox_prep((uint32_t)level, (uint32_t)(it.c0 + ch) + P.cid0, P.pid, A.rk);
+                    Step p;
+                    propose<UP>(Cq, (uint32_t)(s0 + j), p);
+                    const int o = (buf * kPdSteps + j) * S + ch;
+                    rd[o] = p.d;
+                    rz[o] = p.z;
+                    rt[o] = p.tau;
+                }
+            };
+            if (producer) produce(0);
+            __syncthreads();
+            for (int ph = 0; ph < phases; ++ph) {  // every thread of the block: one barrier per phase
+                if (producer) {
+                    if (ph + 1 < phases) produce(ph + 1);
+                } else if (active) {
+                    const int buf = ph & 1, s0 = ph * kPdSteps;
+                    const int cnt = min(kPdSteps, L - s0);
+                    auto fetch = [&](int j, Step& p) {
+                        const int o = (buf * kPdSteps + j) * S + t;
+                        p.d = rd[o];
+                        p.z = rz[o];
+                        p.tau = rt[o];
+                    };
+                    for (int j = 0; j < cnt; ++j) {
+                        Step p;
+                        fetch(j, p);
+                        evaluate<COST, UB, UP>(C, st, p);
+                        commit(p, s0 + j);
+                    }
+                }
+                __syncthreads();
+            }
+            s = L;
+        }
+        if (!PD && R > U) {
             for (; s + R <= L; s += R) {
                 Step p[R];
 #pragma unroll
