@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "f32x2.cuh"
+
 namespace sa {
 
 // erf by Hastings' rational approximation (Abramowitz and Stegun, formula 7.1.26):
@@ -49,34 +51,6 @@ __device__ __forceinline__ float gelu_f(float z) {
     return fmaf(az, __fmul_rn(q, e), fmaxf(z, 0.0f));
 }
 
-// Pairs of FP32 lanes (packed arithmetic: one instruction for both lanes).
-typedef unsigned long long f32x2_t;
-__device__ __forceinline__ f32x2_t f2_pack(float a, float b) {
-    f32x2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 f2_unpack(f32x2_t r) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-    return make_float2(a, b);
-}
-__device__ __forceinline__ f32x2_t f2_fma(f32x2_t a, f32x2_t b, f32x2_t c) {
-    f32x2_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2_t f2_mul(f32x2_t a, f32x2_t b) {
-    f32x2_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2_t f2_add(f32x2_t a, f32x2_t b) {
-    f32x2_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2_t f2_splat(float a) { return f2_pack(a, a); }
 
 // gelu_f of both lanes of z, bit for bit.
 __device__ __forceinline__ f32x2_t gelu2(f32x2_t z) {

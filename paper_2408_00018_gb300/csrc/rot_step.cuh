@@ -14,13 +14,16 @@
 //     a - b = (|y + Delta| - |y|) / (a + b), with |y + Delta| - |y| = +-Delta
 //     when the sign does not change;
 // both are product-to-sum forms whose error scales with |Delta| instead of
-// with the size of the terms.  rot_eval64 is the FP64 difference from
+// with the size of the terms.  For an even n the hot loops take coordinate
+// pairs in packed f32x2 arithmetic (the same operations per coordinate).
+// rot_eval64 is the FP64 difference from
 // y_hi + y_lo and the FP64 Q (the re-check); rot_update applies an accepted
 // move to the pair with compensated arithmetic (TwoProd by FMA, TwoSum).
 #pragma once
 #include <cmath>
 #include <cstdint>
 
+#include "f32x2.cuh"
 #include "sa_device.cuh"
 #include "sa_internal.h"
 
@@ -116,6 +119,36 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
     float sum = 0.0f, bnd = 0.0f;
     if (COST == kRotRastrigin) {
         const bool any_big = fabsf(dh) * P.qmax * 3.14159265f >= 0.5f;  // some |pi Delta_i| may reach 1/2
+        if (!any_big && (n & 1) == 0) {
+            // lanes own coordinate pairs (i, i + 1), i = 2 lane + 64 j, in packed
+            // arithmetic: the same operations per coordinate as below; each lane sums
+            // its even and its odd coordinates apart, then adds the two (no more
+            // rounding steps than the loop below: ceil(n / 64) + 1 <= ceil(n / 32))
+            const f32x2_t dh2 = f2_splat(dh), half = f2_splat(0.5f), two = f2_splat(2.0f), k20 = f2_splat(20.0f);
+            const f32x2_t pi = f2_splat(3.14159265358979f), tpi = f2_splat(6.28318530717958648f);
+            const f32x2_t c7 = f2_splat(-1.98412698e-4f), c5 = f2_splat(8.33333333e-3f), c3 = f2_splat(-1.66666667e-1f);
+            const f32x2_t one = f2_splat(1.0f), k9 = f2_splat(9.0e-7f), k6 = f2_splat(6.0e-5f), kc = f2_splat(2.0e-4f);
+            const f32x2_t ns = f2_splat(nsum);
+            f32x2_t sum2 = f2_splat(0.0f), bnd2 = f2_splat(0.0f);
+            #pragma unroll 1
+            for (int i = 2 * lane; i < n; i += 64) {
+                const f32x2_t Y = f2_ld(yh + i), YL = f2_ld(yl + i), D = f2_mul(dh2, f2_ld(qcol + i));
+                const float2 y = f2_unpack(Y);
+                const f32x2_t M = f2_add(f2_sub(Y, f2_pack(rintf(y.x), rintf(y.y))), f2_fma(half, D, YL));
+                const float2 m = f2_unpack(M);
+                const float2 ang = f2_unpack(f2_mul(tpi, f2_sub(M, f2_pack(rintf(m.x), rintf(m.y)))));
+                const f32x2_t S1 = f2_pack(sin_approx(ang.x), sin_approx(ang.y));
+                const f32x2_t X = f2_mul(pi, D), X2 = f2_mul(X, X);
+                const f32x2_t S2 = f2_mul(X, f2_fma(X2, f2_fma(X2, f2_fma(X2, c7, c5), c3), one));
+                const f32x2_t T = f2_fma(D, f2_fma(two, Y, D), f2_mul(f2_mul(k20, S1), S2));
+                sum2 = f2_add(sum2, T);
+                const f32x2_t aD = f2_abs(D);
+                bnd2 = f2_fma(aD, f2_fma(f2_abs(Y), k9, f2_fma(aD, k6, kc)), f2_fma(ns, f2_abs(T), bnd2));
+            }
+            const float2 sp = f2_unpack(sum2), bp = f2_unpack(bnd2);
+            sum = sp.x + sp.y;
+            bnd = bp.x + bp.y;
+        } else {
         #pragma unroll 4
         for (int i = lane; i < n; i += 32) {
             const float yv = yh[i];
@@ -133,6 +166,7 @@ __device__ __forceinline__ void rot_eval32(const ProbDev& P, const float* yh, co
             const float aD = fabsf(Dl);
             // the term's error plus its share of the summation's rounding
             bnd = fmaf(aD, fmaf(fabsf(yv), 9.0e-7f, fmaf(aD, 6.0e-5f, c)), fmaf(nsum, fabsf(t), bnd));
+        }
         }
         sum = rot_wsumf(sum);
         bnd = rot_wsumf(bnd);
@@ -219,6 +253,26 @@ __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* y
     const float gmax = COST == kRotRastrigin ? fmaf(2.0f, ym + dm, 64.0f)
                                              : fmaf(0.5f, sqrt_approx(ym + dm), 1.0f) / (float)n;
     edrift = fmaf((float)n * gmax, (ym + 2.0f * dm) * 2.9e-14f, edrift);
+    if (COST == kRotRastrigin && (n & 1) == 0) {
+        // coordinate pairs in packed arithmetic: lane for lane the operations below
+        const f32x2_t dh2 = f2_splat(dh), dl2 = f2_splat(dl);
+        #pragma unroll 1
+        for (int i = 2 * lane; i < n; i += 64) {
+            const f32x2_t qh = f2_ld(qcol + i), ql = f2_ld(qlcol + i);
+            const f32x2_t ph = f2_mul(dh2, qh);  // packed products are never merged into an FMA
+            const f32x2_t pl = f2_fma(dh2, qh, f2_neg(ph));
+            const f32x2_t corr = f2_fma(dh2, ql, f2_mul(dl2, qh));
+            const f32x2_t a = f2_ld(yh + i);
+            const f32x2_t sh = f2_add(a, ph);
+            const f32x2_t t2 = f2_sub(sh, a);
+            const f32x2_t err = f2_add(f2_sub(a, f2_sub(sh, t2)), f2_sub(ph, t2));
+            const f32x2_t lo2 = f2_add(f2_ld(yl + i), f2_add(f2_add(pl, corr), err));
+            const f32x2_t nh = f2_add(sh, lo2);
+            f2_st(yh + i, nh);
+            f2_st(yl + i, f2_sub(lo2, f2_sub(nh, sh)));
+        }
+        return;
+    }
         #pragma unroll 4
         for (int i = lane; i < n; i += 32) {
         const float qh = qcol[i], ql = qlcol[i];

@@ -370,7 +370,11 @@ cudaError_t launch_group(sa_handle* h, const Group& g, cudaStream_t s) {
     if (num == 0) return cudaSuccess;
     if (g.kind == kSweepF64) return launch_sweep_f64(a, num, g.block, g.smem, s);
     if (g.kind == kSweepF32Warp) return launch_sweep_f32w(a, num, g.lanes, g.cache, g.block, g.smem, s);
-    if (g.kind == kSweepRot) return launch_sweep_rot(a, num, g.smem, s);
+    if (g.kind == kSweepRot) {
+        int costs = 0;
+        for (int p : g.probs) costs |= h->probs[p].cost == SA_ROT_RASTRIGIN ? 1 : 2;
+        return launch_sweep_rot(a, num, g.smem, costs, s);
+    }
     if (g.kind == kSweepBatch) return launch_batch_level(a, num, (int)h->probs.size(), g.smem, s);
     if (g.kind == kSweepDA)
         // the GEMMs report a timeout in the run's own status word, which every sa_run reads

@@ -220,7 +220,8 @@ cudaError_t launch_gather(const float* X32, const double* X64, int64_t x_base, i
                           int k, double* out, cudaStream_t s);
 cudaError_t launch_polish_update(ProbDev* probs, int problem, const double* xs, const double* fs, int k, cudaStream_t s);
 
-cudaError_t launch_sweep_rot(const SweepArgs& a, int num_items, size_t smem, cudaStream_t s);
+// costs: bit 0 rotated Rastrigin, bit 1 rotated Schwefel among the launch's problems
+cudaError_t launch_sweep_rot(const SweepArgs& a, int num_items, size_t smem, int costs, cudaStream_t s);
 size_t sweep_rot_smem_bytes(int n);
 cudaError_t sweep_rot_set_smem(size_t bytes);
 int sweep_rot_chains_per_block();

@@ -208,12 +208,27 @@ __device__ void rot_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& i
     }
 }
 
+// COSTS: the rotated costs the launch's problems use (bit 0 Rastrigin, bit 1
+// Schwefel), so that a launch of one cost gets a register allocation of its own.
+template <int COSTS>
 __global__ void __launch_bounds__(kBlockR) sweep_rot_kernel(SweepArgs A) {
     extern __shared__ __align__(16) float smem_rot[];
     const WorkItem it = A.items[blockIdx.x];
     const ProbDev& P = A.probs[it.problem];
-    if (P.cost == kRotRastrigin) rot_tile<kRotRastrigin>(A, P, it, smem_rot);
+    if (COSTS == 1) rot_tile<kRotRastrigin>(A, P, it, smem_rot);
+    else if (COSTS == 2) rot_tile<kRotSchwefel>(A, P, it, smem_rot);
+    else if (P.cost == kRotRastrigin) rot_tile<kRotRastrigin>(A, P, it, smem_rot);
     else rot_tile<kRotSchwefel>(A, P, it, smem_rot);
+}
+
+template <int COSTS>
+cudaError_t set_smem_rot(size_t bytes) {
+    static size_t current = 0;  // the limit only grows, so earlier graphs stay valid
+    if (bytes <= current) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(sweep_rot_kernel<COSTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) current = bytes;
+    return e;
 }
 
 }  // namespace
@@ -222,15 +237,16 @@ size_t sweep_rot_smem_bytes(int n) { return (size_t)kWarpsR * 3 * (size_t)n * si
 int sweep_rot_chains_per_block() { return kWarpsR; }
 
 cudaError_t sweep_rot_set_smem(size_t bytes) {
-    static size_t current = 0;
-    if (bytes <= current) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(sweep_rot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) current = bytes;
+    cudaError_t e = set_smem_rot<1>(bytes);
+    if (e == cudaSuccess) e = set_smem_rot<2>(bytes);
+    if (e == cudaSuccess) e = set_smem_rot<3>(bytes);
     return e;
 }
 
-cudaError_t launch_sweep_rot(const SweepArgs& a, int num_items, size_t smem, cudaStream_t s) {
-    sweep_rot_kernel<<<num_items, kBlockR, smem, s>>>(a);
+cudaError_t launch_sweep_rot(const SweepArgs& a, int num_items, size_t smem, int costs, cudaStream_t s) {
+    if (costs == 1) sweep_rot_kernel<1><<<num_items, kBlockR, smem, s>>>(a);
+    else if (costs == 2) sweep_rot_kernel<2><<<num_items, kBlockR, smem, s>>>(a);
+    else sweep_rot_kernel<3><<<num_items, kBlockR, smem, s>>>(a);
     return cudaGetLastError();
 }
 
