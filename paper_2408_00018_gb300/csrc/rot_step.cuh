@@ -253,7 +253,7 @@ __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* y
     const float gmax = COST == kRotRastrigin ? fmaf(2.0f, ym + dm, 64.0f)
                                              : fmaf(0.5f, sqrt_approx(ym + dm), 1.0f) / (float)n;
     edrift = fmaf((float)n * gmax, (ym + 2.0f * dm) * 2.9e-14f, edrift);
-    if (COST == kRotRastrigin && (n & 1) == 0) {
+    if ((n & 1) == 0) {
         // coordinate pairs in packed arithmetic: lane for lane the operations below
         const f32x2_t dh2 = f2_splat(dh), dl2 = f2_splat(dl);
         #pragma unroll 1
