@@ -436,7 +436,10 @@ sa_status sa_gemm_bf16(const void* d_A, int32_t lda, const void* d_B, int32_t ld
  * ICLR 2015).  Parameters are one FP32 device vector of sa_mlp_param_count(n)
  * elements laid out W1 [512 x n] (row-major), b1 [512], W2 [512 x 512],
  * b2 [512], w3 [512], b3 [1].  The matrix products run on the tensor cores
- * (BF16 operands, FP32 accumulation); everything else in FP32.
+ * (BF16 operands, FP32 accumulation); everything else in FP32.  erf in g is
+ * Hastings' rational approximation (Abramowitz and Stegun 7.1.26, |error| <=
+ * 1.5e-7).  sa_mlp_forward runs both layers and the head in one kernel for
+ * n <= 128 (the hidden layer never leaves the chip) and as two GEMMs above.
  *   sa_mlp_param_count  number of parameters (-1 if n < 1)
  *   sa_mlp_init         He-normal weights from Philox (stream tag 2 of seed), zero biases
  *   sa_mlp_forward      d_y[b] = f~(d_X[b]) for B rows of d_X [B x n] (FP32, device)
