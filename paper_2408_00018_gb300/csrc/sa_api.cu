@@ -330,7 +330,7 @@ GroupLayout pick_group_layout(int n) {
     int best_b = 8 * g.lanes < 32 ? 32 : 8 * g.lanes;
     long best_chains = -1;
     for (int b = best_b; b <= 256; b += 32) {
-        const size_t smem = sweep_f32w_smem_bytes(n, g.lanes, g.cache, b) + 1024;  // + the kernel's static arrays
+        const size_t smem = sweep_f32w_smem_bytes(n, g.lanes, g.cache, b) + sweep_f32w_static_bytes(g.lanes);
         if (smem > 227 * 1024) break;
         const long by_smem = (long)(kSmemPerSm / (smem + kReserved));
         const long by_threads = 2048 / b, by_regs = 65536 / (80L * b);

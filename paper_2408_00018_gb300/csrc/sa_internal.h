@@ -169,6 +169,7 @@ cudaError_t launch_sweep_f32w(const SweepArgs& a, int num_items, int lanes, bool
 size_t sweep_f32w_smem_bytes(int n, int lanes, bool cache, int block);
 cudaError_t sweep_f32w_set_smem(int lanes, bool cache, size_t bytes);
 int sweep_f32w_chains_per_block(int lanes, int block);
+size_t sweep_f32w_static_bytes(int lanes);
 // One launch per level for a batch of FP32 problems: every tile of every problem
 // (item.lanes: 2, 4 or 8 lanes per chain, or 0 for one chain per thread with
 // item.count <= the tile's capacity), then each problem's last tile to finish

@@ -12,7 +12,7 @@ namespace {
 template <int G, bool CACHE>
 __global__ void __launch_bounds__(kGroupMaxBlock, SA_F32W_MIN_BLOCKS) sweep_f32g_kernel(SweepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ GroupShared sh;
+    __shared__ GroupSharedN<kGroupMaxBlock / G> sh;
     const WorkItem it = A.items[blockIdx.x];
     group_tile<G, CACHE>(A, A.probs[it.problem], it, A.run->level, smem_raw, sh);
 }
@@ -41,6 +41,16 @@ bool sweep_f32w_layout_ok(int lanes, bool cache) {
 }
 
 int sweep_f32w_chains_per_block(int lanes, int block) { return block / lanes; }
+
+// Static shared memory of the layout's kernel (its block scratch).
+size_t sweep_f32w_static_bytes(int lanes) {
+    switch (lanes) {
+    case 2: return sizeof(GroupSharedN<kGroupMaxBlock / 2>);
+    case 4: return sizeof(GroupSharedN<kGroupMaxBlock / 4>);
+    case 8: return sizeof(GroupSharedN<kGroupMaxBlock / 8>);
+    default: return sizeof(GroupSharedN<kGroupMaxBlock / 32>);
+    }
+}
 
 size_t sweep_f32w_smem_bytes(int n, int lanes, bool cache, int block) {
     const size_t cb = (size_t)(block / lanes);

@@ -423,21 +423,26 @@ __device__ __forceinline__ ChainEnd dispatch_chain(const SweepArgs& A, const Pro
               : group_chain<COST, false, false, G, CACHE>(A, P, c, mine, level, xw, hw, slo, shi, ssig);
 }
 
-// Block-level scratch of a group tile (static shared memory of the calling kernel).
-struct GroupShared {
+// Block-level scratch of a group tile (static shared memory of the calling kernel),
+// for up to MAXC chains per block: sized by the layout, since a few hundred bytes
+// decide whether one more block fits on an SM.
+template <int MAXC>
+struct GroupSharedN {
     unsigned block_acc;
     int ncand;
     double block_M;
-    double chain_hi[kGroupMaxBlock / 2];
-    int cand[kGroupMaxBlock / 2];
+    double chain_hi[MAXC];
+    int cand[MAXC];
 };
+using GroupShared = GroupSharedN<kGroupMaxBlock / 2>;  // any layout (G >= 2)
 
 // One tile of chains in the group layout: G lanes per chain, blockDim.x / G chains.
 // smem_raw: the dynamic shared memory (state rows, cached terms, box arrays).
-template <int G, bool CACHE>
+template <int G, bool CACHE, int MAXC>
 __device__ void group_tile(const SweepArgs& A, const ProbDev& P, const WorkItem& it, int level, unsigned char* smem_raw,
-                           GroupShared& sh) {
+                           GroupSharedN<MAXC>& sh) {
     constexpr int kMaxChains = kGroupMaxBlock / G;
+    static_assert(MAXC >= kMaxChains, "block scratch smaller than the layout's chains");
     unsigned& block_acc = sh.block_acc;
     double* chain_hi = sh.chain_hi;
     double& block_M = sh.block_M;
