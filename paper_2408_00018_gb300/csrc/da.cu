@@ -145,8 +145,9 @@ struct StepConst {
 // One lockstep step of chain c.  sy: the warp's 2n floats of shared memory.  The
 // chain's pair state is copied into it asynchronously before the step's draws
 // (the copies do not depend on them), the step reads and updates it there, and
-// an accepted move writes it back.  Every lane touches only its own coordinates
-// k = lane + 32 j, so the copies need no exchange between lanes.
+// an accepted move writes it back.  The copies are lane-strided (k = lane + 32 j)
+// and the evaluation and update may take coordinates in pairs, so a warp
+// barrier separates each from the next.
 template <int COST>
 __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D, int64_t c, int level, int s,
                            const StepConst& K, float* sy, unsigned& nacc, unsigned& nev, unsigned& nre) {
@@ -241,6 +242,7 @@ __device__ void step_chain(const SweepArgs& A, const ProbDev& P, const DaDev& D,
         if (acc) {
             float edrift = 0.0f;
             rot_update<COST>(P, yh, yl, mv.d, mv.dh, mv.dl, n, lane, edrift);
+            __syncwarp();  // the update may write a coordinate another lane copies back
             for (int k = lane; k < n; k += 32) {
                 yhg[k] = yh[k];
                 ylg[k] = yl[k];
