@@ -1,6 +1,8 @@
 // rot_tc.cu -- the rotated costs' level-0 transform Y0 = X0 Q^T on the tensor
 // cores, exact to the double-float pairs the rotated sweep starts from.
 //
+// The method is the error-free splitting of a matrix product into products of
+// low-precision slices (Ozaki, Ogita, Oishi and Rump, 2012), with integer slices.
 // Every row of X0 (a chain's FP32 state) and of Q (FP64) is split into S = 6
 // slices of integers of magnitude <= 128, held exactly in BF16, on a common
 // power-of-two scale per row:
