@@ -89,8 +89,7 @@ __device__ __forceinline__ RotMove rot_propose(uint4 w, const float* x, const Pr
         const float z = -r * cos_approx(6.28318530717958648f * (u23f(w.z) - 0.5f));  // cos(2 pi u2)
         xp = fmaf(sig, z, m.xo);
     }
-    if (boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);
-    m.xp = fminf(fmaxf(xp, lo), hi);
+    m.xp = reflect_clip(xp, lo, hi, boundary == 0);
     // delta = xp - xo exactly, as dh + dl (TwoSum)
     m.dh = m.xp - m.xo;
     const float bb = m.dh - m.xp;

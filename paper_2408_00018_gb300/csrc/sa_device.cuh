@@ -74,8 +74,10 @@ __device__ __forceinline__ uint4 philox_step(uint32_t c0, const PhiloxFixed& f, 
 // Uniform in (0,1) from the top 23 bits of a word; exact in FP32 and FP64.
 // FP32 form without an integer-to-float conversion: the top 23 bits become the
 // mantissa of a number in [1, 2); subtracting 1 - 2^-24 is exact and gives (k + 1/2) 2^-23.
+// The bits 0x3F800000 | (w >> 9) come from one funnel shift of the pair
+// (0x7F, w) right by 9: the exponent field 0x7F lands above the 23 bits.
 __device__ __forceinline__ float u23f(uint32_t w) {
-    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.999999940395355225f;
+    return __uint_as_float(__funnelshift_r(w, 0x7Fu, 9)) - 0.999999940395355225f;
 }
 __device__ __forceinline__ double u23d(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 // Coordinate d = (w n) >> 32, uniform over [0, n).
@@ -105,6 +107,21 @@ __device__ __forceinline__ float lg2_approx(float x) {
     float r;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Box handling of a proposal (Sec. 2.1, Step 2): reflect once at the face it
+// crossed, then clip to [lo, hi]; or clip only.  The reflection is branch-free:
+// with a = 2 lo - xp and b = 2 hi - xp, min(max(xp, a), max(b, lo)) is a for
+// xp < lo, xp inside the box and max(b, lo) for xp > hi (the reflected point
+// already clipped from below), and it is never below lo, so the clip reduces
+// to min(., hi).  2 lo and 2 hi are exact, so a and b are the reflected points
+// rounded once, as in the case-by-case form.
+__device__ __forceinline__ float reflect_clip(float xp, float lo, float hi, bool reflect) {
+    if (reflect) {
+        const float a = 2.0f * lo - xp, b = 2.0f * hi - xp;
+        return fminf(fminf(fmaxf(xp, a), fmaxf(b, lo)), hi);
+    }
+    return fminf(fmaxf(xp, lo), hi);
 }
 
 // sin(r) for 0 <= r <= ~64: two-constant Cody-Waite reduction by 2 pi, then the

@@ -103,10 +103,10 @@ struct WCtx {
     const uint32_t* rk;  // Philox round keys (kernel parameters)
 };
 
+// The move of one step from its Philox block w.
 // UP: the move is a uniform redraw of the coordinate (z = u2) instead of a Gaussian step.
 template <bool UP>
-__device__ __forceinline__ void wpropose(const WCtx& C, uint32_t s, WStep& p) {
-    const uint4 w = philox_step(s, C.pf, C.rk);
+__device__ __forceinline__ void wpropose(const WCtx& C, const uint4& w, WStep& p) {
     p.d = coord_of(w.x, C.n);
     const float u1 = u23f(w.y), u2 = u23f(w.z), u3 = u23f(w.w);
     if (UP) {
@@ -129,8 +129,7 @@ __device__ __forceinline__ void wevaluate(const WCtx& C, WStep& p) {
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
     float xp = UP ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
-    if (C.boundary == 0) xp = xp < lo ? 2.0f * lo - xp : (xp > hi ? 2.0f * hi - xp : xp);
-    xp = fminf(fmaxf(xp, lo), hi);
+    xp = reflect_clip(xp, lo, hi, C.boundary == 0);
     p.xo = xo;
     p.xp = xp;
     if (COST == kSchwefel || COST == kRastrigin) {
@@ -292,14 +291,26 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
     const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (gi * G);
     // Per-lane sums of the accepted differences (lane gl holds the steps
     // s = gl mod G) and of the bounds on their FP32 errors; reduced once at the end.
-    float dS = 0.0f, e = 0.0f;
+    // Each accepted step adds its difference's bound plus u |dS| for the rounding
+    // of the running sum.  Where the difference's bound is the constant kappa
+    // (Schwefel, Rastrigin) the lane keeps sum |dS| over its accepted steps and
+    // forms nacc kappa + u sum |dS| once at the end.
+    float dS = 0.0f, e = 0.0f, sabs_acc = 0.0f;
     unsigned nacc = 0, bw = 0;
     const int L = (int)opaque((uint32_t)A.L);
+    // Each lane draws the Philox block of its next round's step while the
+    // current round evaluates: the block depends on the step counter alone, so
+    // its ten dependent rounds of products fill the latency of this round's
+    // loads, shuffles and SFU functions.  (The block drawn in the last round
+    // belongs to a step past L and is not used.)
+    uint4 wn = philox_step((uint32_t)gl, C.pf, C.rk);
     // one round: steps s0 .. s0 + G - 1, one per lane (live: the lane's step exists)
     auto round = [&](int s0, bool live) {
         const int s = s0 + gl;
+        const uint4 w = wn;
+        wn = philox_step((uint32_t)(s + G), C.pf, C.rk);
         WStep p;
-        wpropose<UP>(C, (uint32_t)s, p);
+        wpropose<UP>(C, w, p);
         wevaluate<COST, UB, UP, CACHE>(C, p);
         bool acc, pend;
         if (G < 32) {
@@ -382,9 +393,9 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
             }
         }
         __syncwarp();  // this round's writes before the next round's reads
-        const float bnd = COST == kRosenbrock ? rosen_bound(C, p) : kappa;
         dS += acc ? p.dF : 0.0f;
-        e += acc ? bnd + fabsf(dS) * 1.2e-7f : 0.0f;
+        if (COST == kRosenbrock) e += acc ? rosen_bound(C, p) + fabsf(dS) * 1.2e-7f : 0.0f;
+        else sabs_acc += acc ? fabsf(dS) : 0.0f;
         nacc += acc ? 1u : 0u;
         if (trace_on) {
             const unsigned accm = __ballot_sync(kFull, acc) & gmask;
@@ -399,6 +410,7 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
     for (; s0 + G <= L; s0 += G) round(s0, mine);  // full rounds
     if (s0 < L) round(s0, mine && s0 + gl < L);    // the last, partial round
     (void)gmask;
+    if (COST != kRosenbrock) e = fmaf((float)nacc, kappa, sabs_acc * 1.2e-7f);
     // lane sums -> chain sums (log2 G tree levels: their rounding is bounded by log2(G) u sum|dS_lane|)
     float dabs = group_sum<G>(fabsf(dS));
     dS = group_sum<G>(dS);

@@ -198,11 +198,7 @@ __device__ __forceinline__ void move_to(const Ctx& C, Step& p) {
     if (UB) { lo = C.lo_u; hi = C.hi_u; sg = C.sig_u; }
     else { lo = C.slo[d]; hi = C.shi[d]; sg = C.ssig[d]; }
     float xp = UP ? fmaf(hi - lo, p.z, lo) : fmaf(sg, p.z, xo);
-    if (C.boundary == 0) {  // reflect once (selects, no branch)
-        const float r1 = 2.0f * lo - xp, r2 = 2.0f * hi - xp;
-        xp = xp < lo ? r1 : (xp > hi ? r2 : xp);
-    }
-    xp = fminf(fmaxf(xp, lo), hi);
+    xp = reflect_clip(xp, lo, hi, C.boundary == 0);
     p.xo = xo;
     p.xp = xp;
 }
