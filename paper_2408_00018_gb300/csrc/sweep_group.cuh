@@ -42,6 +42,7 @@
 #include <cfloat>
 #include <cmath>
 #include <math_constants.h>
+#include <type_traits>
 
 #include "sa_device.cuh"
 #include "sa_internal.h"
@@ -304,8 +305,10 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
     // loads, shuffles and SFU functions.  (The block drawn in the last round
     // belongs to a step past L and is not used.)
     uint4 wn = philox_step((uint32_t)gl, C.pf, C.rk);
-    // one round: steps s0 .. s0 + G - 1, one per lane (live: the lane's step exists)
-    auto round = [&](int s0, bool live) {
+    // one round: steps s0 .. s0 + G - 1, one per lane (live: the lane's step exists;
+    // trace_c: std::true_type when the level records its accept bits)
+    auto round = [&](int s0, bool live, auto trace_c) {
+        constexpr bool kTrace = decltype(trace_c)::value;
         const int s = s0 + gl;
         const uint4 w = wn;
         wn = philox_step((uint32_t)(s + G), C.pf, C.rk);
@@ -316,7 +319,10 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
         if (G < 32) {
             // pending: an earlier lane of the group touches what this lane's evaluation
             // read -- its coordinate, or for Rosenbrock a neighbour (G - 1 shuffles
-            // within the group; a warp-wide match costs far more on this GPU)
+            // within the group; a warp-wide match costs far more on this GPU).  Keying
+            // the test on the earlier lanes' speculative acceptances instead would
+            // leave fewer lanes pending for the separable costs, but at this
+            // schedule's acceptance rates (about 50 to 90%) it measured slower.
             const int key = live ? p.d : -1 - lane;
             bool hit = false;
 #pragma unroll
@@ -397,7 +403,7 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
         if (COST == kRosenbrock) e += acc ? rosen_bound(C, p) + fabsf(dS) * 1.2e-7f : 0.0f;
         else sabs_acc += acc ? fabsf(dS) : 0.0f;
         nacc += acc ? 1u : 0u;
-        if (trace_on) {
+        if (kTrace) {
             const unsigned accm = __ballot_sync(kFull, acc) & gmask;
             bw |= (G == 32 ? accm : accm >> (gi * G)) << (s0 & 31);
             if (((s0 & 31) + G == 32) || s0 + G >= L) {
@@ -406,9 +412,19 @@ __device__ ChainEnd group_chain(const SweepArgs& A, const ProbDev& P, int64_t c,
             }
         }
     };
-    int s0 = 0;
-    for (; s0 + G <= L; s0 += G) round(s0, mine);  // full rounds
-    if (s0 < L) round(s0, mine && s0 + gl < L);    // the last, partial round
+    // The level's rounds, with the choices that hold for the whole level taken
+    // once: tracing or not, and whether every group of the warp holds a chain.
+    auto rounds = [&](auto trace_c) {
+        int s0 = 0;
+        if (__all_sync(kFull, mine)) {
+            for (; s0 + G <= L; s0 += G) round(s0, true, trace_c);  // full rounds
+        } else {
+            for (; s0 + G <= L; s0 += G) round(s0, mine, trace_c);
+        }
+        if (s0 < L) round(s0, mine && s0 + gl < L, trace_c);  // the last, partial round
+    };
+    if (trace_on) rounds(std::true_type{});
+    else rounds(std::false_type{});
     (void)gmask;
     if (COST != kRosenbrock) e = fmaf((float)nacc, kappa, sabs_acc * 1.2e-7f);
     // lane sums -> chain sums (log2 G tree levels: their rounding is bounded by log2(G) u sum|dS_lane|)
