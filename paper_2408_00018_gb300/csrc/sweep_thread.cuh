@@ -26,6 +26,7 @@
 // over those candidates (reduce.cu) is therefore exact.
 
 #pragma once
+#include <type_traits>
 #include <cfloat>
 #include <cmath>
 #include <math_constants.h>
@@ -354,7 +355,10 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
     uint32_t* mybits = tracing ? A.bits + ((size_t)level * (size_t)A.total_chains + (size_t)gc) * (size_t)A.words : nullptr;
     float dS = 0.0f, e = 0.0f;
     uint32_t nacc = 0;
-    if (active || PD) {
+    // The level's steps; trace_c is std::true_type when the level records its
+    // accept bits, so the untraced levels carry no per-step test for it.
+    auto run_steps = [&](auto trace_c) {
+        constexpr bool kTrace = decltype(trace_c)::value;
         uint32_t bw = 0;
         const int L = A.L;
         int s = 0;
@@ -375,7 +379,7 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
                 ++nacc;
                 if (COST == kAckley) { st.s1 = p.a; st.s2 = p.b; st.a = p.ap; }
             }
-            if (tracing) {
+            if (kTrace) {
                 bw |= (acc ? 1u : 0u) << (sidx & 31);
                 if ((sidx & 31) == 31 || sidx == L - 1) { mybits[sidx >> 5] = bw; bw = 0; }
             }
@@ -476,6 +480,10 @@ __device__ void sweep_tile(const SweepArgs& A, const ProbDev& P, const WorkItem&
             evaluate<COST, UB, UP>(C, st, p);
             commit(p, s);
         }
+    };
+    if (active || PD) {
+        if (tracing) run_steps(std::true_type{});
+        else run_steps(std::false_type{});
     }
 
     // ---- candidates for the FP64 argmin -------------------------------------
