@@ -516,6 +516,9 @@ sa_status sa_argmin_f64(const double* d_F, int64_t count, int64_t* d_index, doub
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before any
  *     stream capture.
+ *   - A device reset (cudaDeviceReset) destroys the array and the looked-up
+ *     address goes stale: a process that resets a device does not call this
+ *     function on that device again.
  *   - All calls share the array: calls whose kernels overlap on the GPU
  *     (other streams, other host threads) race and may return wrong results.
  *     Order such calls on one stream.

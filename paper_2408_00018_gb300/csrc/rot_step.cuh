@@ -257,7 +257,7 @@ __device__ __forceinline__ void rot_update(const ProbDev& P, float* yh, float* y
     if ((n & 1) == 0) {
         // coordinate pairs in packed arithmetic: lane for lane the operations below
         const f32x2_t dh2 = f2_splat(dh), dl2 = f2_splat(dl);
-        #pragma unroll 4
+        #pragma unroll 2
         for (int i = 2 * lane; i < n; i += 64) {
             const f32x2_t qh = f2_ld(qcol + i), ql = f2_ld(qlcol + i);
             const f32x2_t ph = f2_mul(dh2, qh);  // packed products are never merged into an FMA
